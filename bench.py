@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the spherical-grid projector: forward + adjoint rays/s on one GPU.
+
+Workload (paper scale): grid 100 r x 60 theta x 120 phi (log-spaced shells 3-25,
+seeded blob + exp(-r/4) density), 32 cone-beam views of 256^2 on a circular
+orbit of radius 60 (30 deg field of view) plus 32 parallel-beam views of 256^2
+at seeded random orientations: 4,194,304 rays. One step = F on every ray and
+F^T on every ray, each traversal done from scratch in-kernel (nothing cached).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank projects its own copy of the workload (weak
+scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+adjoint rays/s"
+UNIT = "rays/s"
+# FP32 operations per valid segment counted from the method's formulas (selection
+# of the next crossing, segment length, gather-accumulate, and the average
+# next-crossing update over the sphere / cone / half-plane mix of the workload);
+# the derivation is written out in the design notes.
+OPS_PER_SEGMENT = 15.0
+SMS, FP32_LANES_PER_SM = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(open(self.path)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax.append(float(row[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+
+def oracle_sample(wl, stride):
+    import oracle
+    parts = []
+    for v in wl.views:
+        if v.kind == "cone":
+            st, di = oracle.cone_rays(v.pos, v.shape[0], v.shape[1], v.fov_deg)
+        else:
+            st, di = oracle.parallel_rays(v.pos, v.shape[0], v.shape[1], v.size)
+        parts.append((st[::stride], di[::stride]))
+    return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
+
+
+def time_oracle(wl, stride):
+    import oracle
+    st, di = oracle_sample(wl, stride)
+    yv = np.ones(len(st))
+    t = time.perf_counter()
+    oracle.forward(wl.edges, st, di, wl.rho)
+    oracle.adjoint(wl.edges, st, di, yv)
+    dt = time.perf_counter() - t
+    return len(st), dt
+
+
+def cpu_baseline(wl, target_s=15.0):
+    import oracle
+    stride = 4096
+    n, dt = time_oracle(wl, stride)
+    stride = max(1, int(stride * dt / target_s))
+    n, dt = time_oracle(wl, stride)
+    return {"value": n / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"every {stride}th ray of each view set ({n} rays), forward + adjoint, FP64, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2608_16960_gb300 import workloads
+    import oracle
+    oracle.build()
+    wl = workloads.paper_scale()
+    # each step: a bounded sample sized so that the whole run takes a few minutes
+    n, dt = time_oracle(wl, 4096)
+    per_step_target = max(1.0, 120.0 / max(1, args.steps + args.warmup))
+    stride = max(1, int(4096 * dt / per_step_target))
+    st, di = oracle_sample(wl, stride)
+    yv = np.ones(len(st))
+    for _ in range(args.warmup):
+        oracle.forward(wl.edges, st, di, wl.rho)
+        oracle.adjoint(wl.edges, st, di, yv)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.forward(wl.edges, st, di, wl.rho)
+        oracle.adjoint(wl.edges, st, di, yv)
+    dt = time.perf_counter() - t
+    value = len(st) * args.steps / dt
+    sample = f"every {stride}th ray of each view set ({len(st)} rays) per step, forward + adjoint, FP64"
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": wl.describe(), "n_rays": wl.n_rays, "sample_rays": len(st)},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "gpu_launches": 0}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import ctypes
+
+    import torch
+
+    from paper_2608_16960_gb300 import _lib, synth, workloads
+    from paper_2608_16960_gb300.projector import Geometry, Grid, tsp_adjoint, tsp_count_segments, tsp_forward
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    L = _lib.load()
+
+    wl = workloads.paper_scale()
+    grid = Grid.from_edges(wl.edges)
+    geoms = [Geometry.cone(v.pos, v.shape, v.fov_deg) if v.kind == "cone" else Geometry.parallel(v.pos, v.shape, v.size)
+             for v in wl.views]
+    rho = torch.tensor(wl.rho, device="cuda")
+    ys = [torch.empty(g.det_shape, device="cuda") for g in geoms]
+    ws = [torch.tensor(synth.uniform_volume(g.det_shape, 100 + i), device="cuda") for i, g in enumerate(geoms)]
+    gs = [torch.empty(grid.shape, device="cuda") for _ in geoms]
+    n_rays = sum(g.n_rays for g in geoms)
+    segs = [int(tsp_count_segments(grid, g).sum().item()) for g in geoms]
+    n_segs = sum(segs)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")  # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+
+    def fwd(i):
+        st = L.tsp_forward_ex(grid.handle, geoms[i].handle, ctypes.c_void_p(rho.data_ptr()),
+                              ctypes.c_void_p(ys[i].data_ptr()), 1, None, sp)
+        _lib.check(st, "tsp_forward")
+
+    def adj(i):
+        st = L.tsp_adjoint_ex(grid.handle, geoms[i].handle, ctypes.c_void_p(ws[i].data_ptr()),
+                              ctypes.c_void_p(gs[i].data_ptr()), 1, 0, None, sp)
+        _lib.check(st, "tsp_adjoint")
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        for i in range(len(geoms)):
+            fwd(i)
+        if ev:
+            ev[1].record(stream)
+        for i in range(len(geoms)):
+            adj(i)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        step(evs[k])
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_fwd = sum(e[0].elapsed_time(e[1]) for e in evs)  # ms
+    t_adj = sum(e[1].elapsed_time(e[2]) for e in evs)
+    t_tot = t_fwd + t_adj
+    if dist:
+        t = torch.tensor([t_tot], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_tot = float(t.item())
+    value = world * n_rays * args.steps / (t_tot / 1e3)
+
+    # end to end through the public API: pinned host buffers, H2D + compute + D2H
+    e2e = None
+    if not args.no_e2e:
+        h_rho = torch.tensor(wl.rho).pin_memory()
+        h_ws = [w.cpu().pin_memory() for w in ws]
+        h_ys = [torch.empty(g.det_shape).pin_memory() for g in geoms]
+        h_gs = [torch.empty(grid.shape).pin_memory() for _ in geoms]
+
+        def e2e_step():
+            d_rho = h_rho.to("cuda", non_blocking=True)
+            d_ws = [h.to("cuda", non_blocking=True) for h in h_ws]
+            for i, g in enumerate(geoms):
+                h_ys[i].copy_(tsp_forward(grid, g, d_rho), non_blocking=True)
+            for i, g in enumerate(geoms):
+                h_gs[i].copy_(tsp_adjoint(grid, g, d_ws[i]), non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        for _ in range(2):
+            e2e_step()
+        ke = max(3, min(args.steps, 10))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(ke):
+            e2e_step()
+        e1.record()
+        torch.cuda.synchronize()
+        te = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        h2d = h_rho.numel() * 4 + sum(h.numel() * 4 for h in h_ws)
+        d2h = sum(h.numel() * 4 for h in h_ys) + sum(h.numel() * 4 for h in h_gs)
+        e2e = {"value": world * n_rays * ke / (te / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    peaks, peak_kind = measured_peaks()
+    # dominant kernel: whichever of the forward / adjoint traversals takes longer
+    dom = "forward" if t_fwd >= t_adj else "adjoint"
+    t_dom_launch = (max(t_fwd, t_adj) / args.steps) / len(geoms) / 1e3  # s per launch
+    seg_per_launch = n_segs / len(geoms)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12  # Tops/s
+    achieved = OPS_PER_SEGMENT * seg_per_launch / t_dom_launch / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s", "frac": achieved / peak_ops,
+                "traffic": None, "kernel": f"{dom}_kernel", "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz",
+                "ops_per_segment": OPS_PER_SEGMENT,
+                "l2_gbs": (4.0 if dom == "forward" else 8.0) * seg_per_launch / t_dom_launch / 1e9}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": wl.describe(), "n_rays": n_rays, "segments_per_step": 2 * n_segs,
+                      "mean_segments_per_ray": n_segs / n_rays, "l2": "flushed between steps (256 MB write)",
+                      "parallelism": f"replicas x{world}"},
+           "fwd_rays_per_s": world * n_rays * args.steps / (t_fwd / 1e3),
+           "adj_rays_per_s": world * n_rays * args.steps / (t_adj / 1e3),
+           "segments_per_s": world * 2 * n_segs * args.steps / (t_tot / 1e3),
+           "roofline": roofline, "clocks": clocks, "e2e": e2e,
+           "gpu_launches": 2 * len(geoms) * args.steps, "peaks": peak_kind}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

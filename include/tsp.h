@@ -1,0 +1,146 @@
+/*
+ * tsp.h - C ABI of the GB300 spherical-grid tomographic projector.
+ *
+ * The projector F maps a density rho, piecewise constant on a spherical grid,
+ * to line integrals y along rays (TomoSphero, Sec. 2.1, Eq. 3-5); its adjoint
+ * F^T scatters y * (segment length) back onto the voxels (Sec. 4.4).
+ *
+ * Conventions shared by every entry point
+ *  - Grid: radial shells r_0 < ... < r_Nr, polar cones theta_0 < ... < theta_Ne
+ *    (polar angle from +Z, in [0, pi]), azimuthal half-planes phi_0 < ... < phi_Na
+ *    (span <= 2 pi; a span of exactly 2 pi wraps, phi_Na being phi_0).
+ *    Bins are half-open [edge_k, edge_{k+1}). Density is zero outside the grid.
+ *  - rho: float32, C-order (batch, N_r, N_e, N_a); flat voxel = (ir*N_e + ie)*N_a + ia.
+ *  - y:   float32, (batch, n_views, H, W) for cone/parallel detectors,
+ *         (batch, n_rays) for free-form rays.
+ *  - All array pointers passed to projection calls are DEVICE pointers owned by
+ *    the caller (e.g. torch tensors). Handles own copies of the geometry.
+ *  - Calls run asynchronously on the given CUDA stream (NULL = legacy default
+ *    stream) on the current device, which must be the device the handles were
+ *    created on. No call synchronises the host except where stated.
+ *  - Errors are returned as tsp_status, never thrown. tsp_last_error() gives a
+ *    thread-local message for the last failure. A kernel that detects an
+ *    internal inconsistency sets a device error word instead of trapping;
+ *    tsp_device_status() reads and clears it.
+ */
+#ifndef TSP_H_
+#define TSP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tsp_grid_s* tsp_grid;
+typedef struct tsp_geom_s* tsp_geom;
+
+typedef enum {
+  TSP_OK = 0,
+  TSP_EINVAL = 1,     /* null pointer, size <= 0, out-of-range argument */
+  TSP_ENOTMONO = 2,   /* grid edges not strictly increasing */
+  TSP_ENOMEM = 3,     /* device or host allocation failed */
+  TSP_ECUDA = 4,      /* a CUDA runtime call failed (message has the CUDA error) */
+  TSP_ETIMEOUT = 5,   /* a bounded device wait gave up */
+  TSP_EDEVICE = 6,    /* a kernel set the device error word */
+  TSP_ENOTSUP = 7     /* size beyond a documented limit */
+} tsp_status;
+
+/* Limits of one grid: N_r, N_e <= 1024, N_a <= 2048, voxels < 2^31. */
+
+/*
+ * tsp_grid_create - spherical grid from its boundary locations (Sec. 2.2, 4.1;
+ * Fig. 2-4). Edges are host arrays of n_*_edges = N + 1 doubles, copied.
+ * r_edges >= 0; theta_edges within [0, pi]; phi span <= 2 pi. Grids that cover
+ * a wedge only (Fig. 3) are allowed. Returns TSP_ENOTMONO for non-increasing
+ * edges, TSP_EINVAL for other bad input. Synchronous (uploads small tables).
+ */
+tsp_status tsp_grid_create(const double* r_edges, int n_r_edges, const double* theta_edges,
+                           int n_theta_edges, const double* phi_edges, int n_phi_edges,
+                           tsp_grid* out);
+tsp_status tsp_grid_shape(tsp_grid grid, int* n_r, int* n_e, int* n_a);
+void tsp_grid_destroy(tsp_grid grid);
+
+/*
+ * tsp_geom_cone - cone-beam views (Sec. 4.2 ConeRectGeom, Sec. 4.3 collections):
+ * a pinhole detector at each pos (host, [n_views][3]) looking at look_at
+ * (host [n_views][3], NULL = origin), with up hint (NULL = +Z, +Y if parallel
+ * to the view axis). H x W pixel centres uniform in tangent space over the full
+ * field of view fov_h_deg x fov_w_deg (degrees). Row 0 is at +up, column 0 at
+ * -right (right = look x up). Ray i = (view*H + row)*W + col.
+ */
+tsp_status tsp_geom_cone(int n_views, const double* pos, const double* look_at, const double* up,
+                         int H, int W, double fov_h_deg, double fov_w_deg, tsp_geom* out);
+
+/*
+ * tsp_geom_parallel - parallel-beam views (Sec. 4.2 ParallelGeom): a detector
+ * plane through pos, perpendicular to the direction pos -> origin, of physical
+ * size size_h x size_w, H x W pixels; every ray runs along that direction.
+ */
+tsp_status tsp_geom_parallel(int n_views, const double* pos, const double* up, int H, int W,
+                             double size_h, double size_w, tsp_geom* out);
+
+/*
+ * tsp_geom_rays - free-form rays (Sec. 4.2 ViewGeom, Listing 4): DEVICE arrays
+ * starts[3][n_rays] and dirs[3][n_rays] (structure of arrays, float32).
+ * Directions need not be normalised; they are normalised in-kernel. A zero
+ * direction yields y = 0 for that ray. copy != 0 copies the arrays (synchronous);
+ * copy == 0 keeps the caller's pointers, which must outlive the handle.
+ */
+tsp_status tsp_geom_rays(int64_t n_rays, const float* starts, const float* dirs, int copy,
+                         tsp_geom* out);
+tsp_status tsp_geom_num_rays(tsp_geom geom, int64_t* n_rays);
+void tsp_geom_destroy(tsp_geom geom);
+
+/* Launch knobs (chosen by tsp_autotune or set by hand). */
+typedef struct {
+  int block_threads;   /* threads per block: 64, 128, 256 or 512 */
+  int warp_tile_w;     /* detector pixels per warp along a row: 4, 8, 16 or 32 */
+  int scatter;         /* adjoint: 0 = one atomic add per segment, 1 = warp-aggregated */
+} tsp_launch;
+
+/*
+ * tsp_forward - y = F rho (Eq. 5) for `batch` densities. rho: device float32
+ * (batch, N_r, N_e, N_a); y: device float32 (batch, n_rays), overwritten.
+ * Every segment of every ray is found in-kernel (Sec. 3.1-3.3) and gathered
+ * (Sec. 3.4); nothing is precomputed. launch may be NULL (defaults).
+ */
+tsp_status tsp_forward(tsp_grid grid, tsp_geom geom, const float* rho, float* y, int batch,
+                       void* stream);
+tsp_status tsp_forward_ex(tsp_grid grid, tsp_geom geom, const float* rho, float* y, int batch,
+                          const tsp_launch* launch, void* stream);
+
+/*
+ * tsp_adjoint - rho (+)= F^T y (adjoint of Eq. 5; Sec. 4.4). y: device float32
+ * (batch, n_rays); rho: device float32 (batch, N_r, N_e, N_a). accumulate == 0
+ * overwrites rho, otherwise adds to it. The traversal is bit-identical to
+ * tsp_forward's, so <F x, y> = <x, F^T y> up to float32 summation order.
+ */
+tsp_status tsp_adjoint(tsp_grid grid, tsp_geom geom, const float* y, float* rho, int batch,
+                       int accumulate, void* stream);
+tsp_status tsp_adjoint_ex(tsp_grid grid, tsp_geom geom, const float* y, float* rho, int batch,
+                          int accumulate, const tsp_launch* launch, void* stream);
+
+/*
+ * tsp_count_segments - counts[i] = number of valid segments of ray i (pieces
+ * of the ray inside the grid with an in-range voxel index: the non-zero rows
+ * of Table 2c). counts: device int32 [n_rays], overwritten.
+ */
+tsp_status tsp_count_segments(tsp_grid grid, tsp_geom geom, int* counts, void* stream);
+
+/*
+ * tsp_device_status - synchronises `stream`, then reads and clears the device
+ * error word (0 = no kernel reported an inconsistency).
+ */
+tsp_status tsp_device_status(void* stream, int* code);
+
+/* Thread-local message describing the last non-OK status of this thread. */
+const char* tsp_last_error(void);
+
+/* Library version, for the binding's load check. */
+int tsp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSP_H_ */

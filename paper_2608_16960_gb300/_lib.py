@@ -1,0 +1,107 @@
+"""ctypes loader for libtsp.so (the C ABI of include/tsp.h).
+
+The product path has no fallback: if the CUDA library is missing or fails to
+load, every call raises. Symbols keep their C names.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import nvbuild as _build
+
+_lock = threading.Lock()
+_lib = None
+
+TSP_OK = 0
+STATUS_NAMES = {0: "TSP_OK", 1: "TSP_EINVAL", 2: "TSP_ENOTMONO", 3: "TSP_ENOMEM", 4: "TSP_ECUDA",
+                5: "TSP_ETIMEOUT", 6: "TSP_EDEVICE", 7: "TSP_ENOTSUP"}
+
+
+class TspError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class tsp_launch(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int), ("warp_tile_w", ctypes.c_int), ("scatter", ctypes.c_int)]
+
+
+# (name, restype, argtypes) for every symbol declared in include/tsp.h
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_LP = ctypes.POINTER(tsp_launch)
+SIGNATURES = {
+    "tsp_grid_create": (_I, [_DP, _I, _DP, _I, _DP, _I, ctypes.POINTER(_P)]),
+    "tsp_grid_shape": (_I, [_P, _IP, _IP, _IP]),
+    "tsp_grid_destroy": (None, [_P]),
+    "tsp_geom_cone": (_I, [_I, _DP, _DP, _DP, _I, _I, _D, _D, ctypes.POINTER(_P)]),
+    "tsp_geom_parallel": (_I, [_I, _DP, _DP, _I, _I, _D, _D, ctypes.POINTER(_P)]),
+    "tsp_geom_rays": (_I, [_I64, _P, _P, _I, ctypes.POINTER(_P)]),
+    "tsp_geom_num_rays": (_I, [_P, _I64P]),
+    "tsp_geom_destroy": (None, [_P]),
+    "tsp_forward": (_I, [_P, _P, _P, _P, _I, _P]),
+    "tsp_forward_ex": (_I, [_P, _P, _P, _P, _I, _LP, _P]),
+    "tsp_adjoint": (_I, [_P, _P, _P, _P, _I, _I, _P]),
+    "tsp_adjoint_ex": (_I, [_P, _P, _P, _P, _I, _I, _LP, _P]),
+    "tsp_count_segments": (_I, [_P, _P, _P, _P]),
+    "tsp_device_status": (_I, [_P, _IP]),
+    "tsp_last_error": (ctypes.c_char_p, []),
+    "tsp_version": (_I, []),
+}
+
+
+def extra_signatures():
+    """Signatures of the entry points declared beyond the projector core
+    (reconstruction, batching, training); merged in by their modules."""
+    return _EXTRA
+
+
+_EXTRA: dict = {}
+
+
+def register(sigs: dict):
+    _EXTRA.update(sigs)
+    if _lib is not None:
+        _apply(_lib, sigs)
+
+
+def _apply(L, sigs):
+    for name, (res, args) in sigs.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def so_path() -> str:
+    return _build.SO
+
+
+def load(build_if_missing: bool = True):
+    """Load libtsp.so (building it first if asked and absent). Raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.SO
+            if build_if_missing:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing: run __graft_entry__.build()")
+            L = ctypes.CDLL(path)
+            _apply(L, SIGNATURES)
+            _apply(L, _EXTRA)
+            _lib = L
+    return _lib
+
+
+def check(status: int, what: str = ""):
+    if status != TSP_OK:
+        msg = load().tsp_last_error().decode(errors="replace")
+        raise TspError(status, f"{what}: {msg}" if what else msg)

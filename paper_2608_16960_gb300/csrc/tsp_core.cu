@@ -1,0 +1,374 @@
+// Handles, validation and error reporting of the C ABI (include/tsp.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "tsp_internal.h"
+
+namespace {
+thread_local std::string g_last_error;
+const double kPi = 3.14159265358979323846;
+const double kTwoPi = 2.0 * kPi;
+}  // namespace
+
+namespace tsp {
+
+tsp_status fail(tsp_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+tsp_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return TSP_ECUDA;
+}
+
+tsp_status check_device(int device) {
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != device)
+    return fail(TSP_EINVAL, "handle was created on device " + std::to_string(device) +
+                                " but the current device is " + std::to_string(cur));
+  return TSP_OK;
+}
+
+}  // namespace tsp
+
+using tsp::fail;
+
+extern "C" const char* tsp_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int tsp_version(void) { return 1; }
+
+static bool strictly_increasing(const double* v, int n) {
+  for (int i = 0; i + 1 < n; ++i)
+    if (!(v[i] < v[i + 1])) return false;
+  return true;
+}
+
+namespace tsp {
+
+// Shared-memory table of a grid (layout R2 | R2L | C | S2 | S2L | K2 | K2L | PC |
+// PS | PA | SEC; the *L arrays hold the float32 rounding residue of the
+// preceding high parts, computed in double). Pure host
+// arithmetic: radii squared, cosines of the polar edges, and the azimuth
+// half-planes with their sector-to-voxel map. Fills the grid's dimensions.
+void build_grid_table(const double* r_edges, int n_r_edges, const double* theta_edges, int n_theta_edges,
+                      const double* phi_edges, int n_phi_edges, std::vector<float>* table_out, tsp_grid_s* g) {
+  const int Nr = n_r_edges - 1, Ne = n_theta_edges - 1, Na = n_phi_edges - 1;
+  const double span = phi_edges[n_phi_edges - 1] - phi_edges[0];
+  g->Nr = Nr;
+  g->Ne = Ne;
+  g->Na = Na;
+  g->wrap = std::fabs(span - kTwoPi) <= 1e-9;
+  // Azimuth half-planes: the real boundaries (N_a distinct ones when the grid
+  // wraps), plus the gap sector of a wedge grid, plus virtual planes that split
+  // any sector wider than pi/2 (they keep the sector's voxel index on both
+  // sides), so that every sector is narrower than the half-turn a line sweeps.
+  std::vector<double> planes;
+  std::vector<int> sec;
+  const int nreal = g->wrap ? Na : Na + 1;
+  for (int k = 0; k < nreal; ++k) {
+    const double a0 = phi_edges[k];
+    const double a1 = (k + 1 < nreal) ? phi_edges[k + 1] : phi_edges[0] + kTwoPi;
+    const int vox = (k < Na) ? k : -1;
+    const double w = a1 - a0;
+    const int pieces = std::max(1, int(std::ceil(w / (0.5 * kPi) - 1e-12)));
+    for (int m = 0; m < pieces; ++m) {
+      planes.push_back(a0 + w * m / pieces);
+      sec.push_back(vox);
+    }
+  }
+  g->M = int(planes.size());
+  g->pa0 = float(planes[0]);
+  g->words = 2 * (Nr + 1) + 5 * (Ne + 1) + 4 * g->M;
+  std::vector<float>& table = *table_out;
+  table.assign(size_t(g->words), 0.0f);
+  float* R2 = table.data();
+  float* R2L = R2 + (Nr + 1);
+  float* C = R2L + (Nr + 1);
+  float* S2 = C + (Ne + 1);
+  float* S2L = S2 + (Ne + 1);
+  float* K2 = S2L + (Ne + 1);
+  float* K2L = K2 + (Ne + 1);
+  float* PC = K2L + (Ne + 1);
+  float* PS = PC + g->M;
+  float* PA = PS + g->M;
+  int* SEC = reinterpret_cast<int*>(PA + g->M);
+  auto split = [](double v, float* hi, float* lo) {
+    *hi = float(v);
+    *lo = float(v - double(*hi));
+  };
+  for (int k = 0; k <= Nr; ++k) split(r_edges[k] * r_edges[k], &R2[k], &R2L[k]);
+  for (int k = 0; k <= Ne; ++k) {
+    const double t = std::min(kPi, std::max(0.0, theta_edges[k]));
+    const double c = std::cos(t), sn = std::sin(t);
+    C[k] = float(c);
+    split(sn * sn, &S2[k], &S2L[k]);
+    split(c * c, &K2[k], &K2L[k]);
+  }
+  for (int j = 0; j < g->M; ++j) {
+    PC[j] = float(std::cos(planes[j]));
+    PS[j] = float(std::sin(planes[j]));
+    PA[j] = float(planes[j] - planes[0]);
+    SEC[j] = sec[j];
+  }
+}
+
+}  // namespace tsp
+
+extern "C" tsp_status tsp_grid_create(const double* r_edges, int n_r_edges, const double* theta_edges,
+                                      int n_theta_edges, const double* phi_edges, int n_phi_edges,
+                                      tsp_grid* out) {
+  if (!out) return fail(TSP_EINVAL, "tsp_grid_create: out is NULL");
+  *out = nullptr;
+  if (!r_edges || !theta_edges || !phi_edges) return fail(TSP_EINVAL, "tsp_grid_create: NULL edge array");
+  if (n_r_edges < 2 || n_theta_edges < 2 || n_phi_edges < 2)
+    return fail(TSP_EINVAL, "tsp_grid_create: each dimension needs at least 2 edges");
+  const int Nr = n_r_edges - 1, Ne = n_theta_edges - 1, Na = n_phi_edges - 1;
+  if (Nr > 1024 || Ne > 1024 || Na > 2048)
+    return fail(TSP_ENOTSUP, "tsp_grid_create: grid larger than 1024 x 1024 x 2048");
+  if (int64_t(Nr) * Ne * Na >= (int64_t(1) << 31))
+    return fail(TSP_ENOTSUP, "tsp_grid_create: more than 2^31 - 1 voxels");
+  for (int i = 0; i < n_r_edges; ++i)
+    if (!std::isfinite(r_edges[i])) return fail(TSP_EINVAL, "tsp_grid_create: non-finite radial edge");
+  for (int i = 0; i < n_theta_edges; ++i)
+    if (!std::isfinite(theta_edges[i])) return fail(TSP_EINVAL, "tsp_grid_create: non-finite polar edge");
+  for (int i = 0; i < n_phi_edges; ++i)
+    if (!std::isfinite(phi_edges[i])) return fail(TSP_EINVAL, "tsp_grid_create: non-finite azimuth edge");
+  if (!strictly_increasing(r_edges, n_r_edges) || !strictly_increasing(theta_edges, n_theta_edges) ||
+      !strictly_increasing(phi_edges, n_phi_edges))
+    return fail(TSP_ENOTMONO, "tsp_grid_create: edges must be strictly increasing");
+  if (r_edges[0] < 0) return fail(TSP_EINVAL, "tsp_grid_create: negative radius");
+  if (theta_edges[0] < -1e-9 || theta_edges[n_theta_edges - 1] > kPi + 1e-9)
+    return fail(TSP_EINVAL, "tsp_grid_create: polar edges must lie in [0, pi]");
+  const double span = phi_edges[n_phi_edges - 1] - phi_edges[0];
+  if (span > kTwoPi + 1e-9) return fail(TSP_EINVAL, "tsp_grid_create: azimuth span exceeds 2 pi");
+
+  tsp_grid g = new (std::nothrow) tsp_grid_s();
+  if (!g) return fail(TSP_ENOMEM, "tsp_grid_create: host allocation");
+  g->r.assign(r_edges, r_edges + n_r_edges);
+  g->th.assign(theta_edges, theta_edges + n_theta_edges);
+  g->ph.assign(phi_edges, phi_edges + n_phi_edges);
+  std::vector<float> table;
+  tsp::build_grid_table(r_edges, n_r_edges, theta_edges, n_theta_edges, phi_edges, n_phi_edges, &table, g);
+  if (g->words > 12288) {  // kernels stage the table in at most 48 KB of shared memory
+    delete g;
+    return fail(TSP_ENOTSUP, "tsp_grid_create: boundary tables exceed 48 KB (too many edges)");
+  }
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_table, sizeof(float) * table.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(g->d_table, table.data(), sizeof(float) * table.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    tsp_status st = tsp::cuda_fail(e, "tsp_grid_create: upload");
+    if (g->d_table) cudaFree(g->d_table);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_grid_shape(tsp_grid g, int* n_r, int* n_e, int* n_a) {
+  if (!g) return fail(TSP_EINVAL, "tsp_grid_shape: NULL grid");
+  if (n_r) *n_r = g->Nr;
+  if (n_e) *n_e = g->Ne;
+  if (n_a) *n_a = g->Na;
+  return TSP_OK;
+}
+
+extern "C" void tsp_grid_destroy(tsp_grid g) {
+  if (!g) return;
+  if (g->d_table) cudaFree(g->d_table);
+  delete g;
+}
+
+// ---------------------------------------------------------------------------
+// geometries
+// ---------------------------------------------------------------------------
+namespace {
+
+void cross3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+double norm3(const double a[3]) { return std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]); }
+
+// Detector frame: look toward look_at (origin by default), right = look x up_hint
+// (up_hint +Z, or +Y when +Z is along the view axis), up = right x look.
+bool view_frame(const double* pos, const double* look_at, const double* up_hint, double look[3],
+                double right[3], double up[3]) {
+  double d[3] = {-pos[0], -pos[1], -pos[2]};
+  if (look_at) {
+    d[0] += look_at[0];
+    d[1] += look_at[1];
+    d[2] += look_at[2];
+  }
+  const double dn = norm3(d);
+  if (!(dn > 0) || !std::isfinite(dn)) return false;
+  for (int i = 0; i < 3; ++i) look[i] = d[i] / dn;
+  double uh[3] = {0, 0, 1};
+  if (up_hint) std::memcpy(uh, up_hint, sizeof uh);
+  double rt[3];
+  cross3(look, uh, rt);
+  double s = norm3(rt);
+  if (s < 1e-9) {
+    const double alt[3] = {0, 1, 0};
+    cross3(look, alt, rt);
+    s = norm3(rt);
+  }
+  if (!(s > 0)) return false;
+  for (int i = 0; i < 3; ++i) right[i] = rt[i] / s;
+  cross3(right, look, up);
+  return true;
+}
+
+tsp_status upload_views(tsp_geom g) {
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_views, sizeof(ViewParams) * g->h_views.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(g->d_views, g->h_views.data(), sizeof(ViewParams) * g->h_views.size(),
+                   cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return tsp::cuda_fail(e, "geometry upload");
+  return TSP_OK;
+}
+
+}  // namespace
+
+extern "C" tsp_status tsp_geom_cone(int n_views, const double* pos, const double* look_at, const double* up,
+                                    int H, int W, double fov_h_deg, double fov_w_deg, tsp_geom* out) {
+  if (!out) return fail(TSP_EINVAL, "tsp_geom_cone: out is NULL");
+  *out = nullptr;
+  if (n_views <= 0 || H <= 0 || W <= 0 || !pos) return fail(TSP_EINVAL, "tsp_geom_cone: bad size or NULL pos");
+  if (H > 65535 * 8 || W > (1 << 20) || n_views > 65535)
+    return fail(TSP_ENOTSUP, "tsp_geom_cone: detector or view count too large");
+  if (!(fov_h_deg > 0 && fov_h_deg < 180) || !(fov_w_deg > 0 && fov_w_deg < 180))
+    return fail(TSP_EINVAL, "tsp_geom_cone: field of view must be in (0, 180) degrees");
+  tsp_geom g = new (std::nothrow) tsp_geom_s();
+  if (!g) return fail(TSP_ENOMEM, "tsp_geom_cone: host allocation");
+  g->kind = GEOM_CONE;
+  g->n_views = n_views;
+  g->H = H;
+  g->W = W;
+  g->n_rays = int64_t(n_views) * H * W;
+  const double th = std::tan(0.5 * fov_h_deg * kPi / 180.0), tw = std::tan(0.5 * fov_w_deg * kPi / 180.0);
+  g->h_views.resize(n_views);
+  for (int v = 0; v < n_views; ++v) {
+    double look[3], right[3], upv[3];
+    if (!view_frame(pos + 3 * v, look_at ? look_at + 3 * v : nullptr, up ? up + 3 * v : nullptr, look, right,
+                    upv)) {
+      delete g;
+      return fail(TSP_EINVAL, "tsp_geom_cone: degenerate view (pos equals look_at?)");
+    }
+    ViewParams& p = g->h_views[v];
+    for (int i = 0; i < 3; ++i) {
+      p.o[i] = float(pos[3 * v + i]);
+      p.a[i] = float(look[i]);
+      p.bu[i] = float(right[i] * tw);
+      p.bv[i] = float(upv[i] * th);
+    }
+  }
+  tsp_status st = upload_views(g);
+  if (st != TSP_OK) {
+    tsp_geom_destroy(g);
+    return st;
+  }
+  *out = g;
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_geom_parallel(int n_views, const double* pos, const double* up, int H, int W,
+                                        double size_h, double size_w, tsp_geom* out) {
+  if (!out) return fail(TSP_EINVAL, "tsp_geom_parallel: out is NULL");
+  *out = nullptr;
+  if (n_views <= 0 || H <= 0 || W <= 0 || !pos) return fail(TSP_EINVAL, "tsp_geom_parallel: bad size or NULL pos");
+  if (H > 65535 * 8 || W > (1 << 20) || n_views > 65535)
+    return fail(TSP_ENOTSUP, "tsp_geom_parallel: detector or view count too large");
+  if (!(size_h > 0) || !(size_w > 0)) return fail(TSP_EINVAL, "tsp_geom_parallel: detector size must be > 0");
+  tsp_geom g = new (std::nothrow) tsp_geom_s();
+  if (!g) return fail(TSP_ENOMEM, "tsp_geom_parallel: host allocation");
+  g->kind = GEOM_PARALLEL;
+  g->n_views = n_views;
+  g->H = H;
+  g->W = W;
+  g->n_rays = int64_t(n_views) * H * W;
+  g->h_views.resize(n_views);
+  for (int v = 0; v < n_views; ++v) {
+    double look[3], right[3], upv[3];
+    if (!view_frame(pos + 3 * v, nullptr, up ? up + 3 * v : nullptr, look, right, upv)) {
+      delete g;
+      return fail(TSP_EINVAL, "tsp_geom_parallel: degenerate view (pos at the origin?)");
+    }
+    ViewParams& p = g->h_views[v];
+    for (int i = 0; i < 3; ++i) {
+      p.o[i] = float(pos[3 * v + i]);
+      p.a[i] = float(look[i]);
+      p.bu[i] = float(right[i] * size_w);
+      p.bv[i] = float(upv[i] * size_h);
+    }
+  }
+  tsp_status st = upload_views(g);
+  if (st != TSP_OK) {
+    tsp_geom_destroy(g);
+    return st;
+  }
+  *out = g;
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_geom_rays(int64_t n_rays, const float* starts, const float* dirs, int copy,
+                                    tsp_geom* out) {
+  if (!out) return fail(TSP_EINVAL, "tsp_geom_rays: out is NULL");
+  *out = nullptr;
+  if (n_rays <= 0 || !starts || !dirs) return fail(TSP_EINVAL, "tsp_geom_rays: bad size or NULL array");
+  if (n_rays >= (int64_t(1) << 40)) return fail(TSP_ENOTSUP, "tsp_geom_rays: too many rays");
+  tsp_geom g = new (std::nothrow) tsp_geom_s();
+  if (!g) return fail(TSP_ENOMEM, "tsp_geom_rays: host allocation");
+  g->kind = GEOM_RAYS;
+  g->n_views = 1;
+  g->H = 1;
+  g->W = 0;
+  g->n_rays = n_rays;
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e != cudaSuccess) {
+    delete g;
+    return tsp::cuda_fail(e, "cudaGetDevice");
+  }
+  if (copy) {
+    e = cudaMalloc(&g->owned, sizeof(float) * 6 * size_t(n_rays));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g->owned, starts, sizeof(float) * 3 * size_t(n_rays), cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(g->owned + 3 * n_rays, dirs, sizeof(float) * 3 * size_t(n_rays), cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+      if (g->owned) cudaFree(g->owned);
+      delete g;
+      return tsp::cuda_fail(e, "tsp_geom_rays: copy");
+    }
+    g->starts = g->owned;
+    g->dirs = g->owned + 3 * n_rays;
+  } else {
+    g->starts = starts;
+    g->dirs = dirs;
+  }
+  *out = g;
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_geom_num_rays(tsp_geom g, int64_t* n) {
+  if (!g || !n) return fail(TSP_EINVAL, "tsp_geom_num_rays: NULL argument");
+  *n = g->n_rays;
+  return TSP_OK;
+}
+
+extern "C" void tsp_geom_destroy(tsp_geom g) {
+  if (!g) return;
+  if (g->d_views) cudaFree(g->d_views);
+  if (g->owned) cudaFree(g->owned);
+  delete g;
+}

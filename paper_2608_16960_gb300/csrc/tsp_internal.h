@@ -1,0 +1,90 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tsp.h"
+#include "tsp_trace.cuh"
+
+struct tsp_grid_s {
+  int Nr = 0, Ne = 0, Na = 0, M = 0;
+  bool wrap = false;
+  float pa0 = 0.0f;
+  int words = 0;
+  float* d_table = nullptr;  // R2 | C | PC | PS | PA | SEC
+  int device = 0;
+  std::vector<double> r, th, ph;
+  tsp::GridDesc desc() const {
+    tsp::GridDesc d;
+    d.table = d_table;
+    d.Nr = Nr;
+    d.Ne = Ne;
+    d.Na = Na;
+    d.M = M;
+    d.words = words;
+    d.pa0 = pa0;
+    return d;
+  }
+  int64_t voxels() const { return int64_t(Nr) * Ne * Na; }
+};
+
+enum GeomKind { GEOM_CONE = 0, GEOM_PARALLEL = 1, GEOM_RAYS = 2 };
+
+// Per-view parameters, float32 (rounded from host double arithmetic).
+// cone:     origin = o; dir(u,v) = a + u*bu + v*bv, u = 2(j+.5)/W - 1, v = 1 - 2(i+.5)/H
+// parallel: origin(u,v) = o + u*bu + v*bv, u = (j+.5)/W - .5, v = .5 - (i+.5)/H; dir = a
+struct ViewParams {
+  float o[3], a[3], bu[3], bv[3];
+};
+
+struct tsp_geom_s {
+  GeomKind kind = GEOM_CONE;
+  int n_views = 0, H = 0, W = 0;
+  int64_t n_rays = 0;
+  ViewParams* d_views = nullptr;
+  std::vector<ViewParams> h_views;
+  const float* starts = nullptr;  // [3][n] device (free-form rays)
+  const float* dirs = nullptr;
+  float* owned = nullptr;
+  int device = 0;
+};
+
+namespace tsp {
+
+tsp_status fail(tsp_status st, const std::string& msg);
+tsp_status cuda_fail(cudaError_t e, const char* what);
+tsp_status check_device(int device);
+
+// Host construction of a grid's shared-memory table (no CUDA calls).
+void build_grid_table(const double* r_edges, int n_r_edges, const double* theta_edges, int n_theta_edges,
+                      const double* phi_edges, int n_phi_edges, std::vector<float>* table, tsp_grid_s* g);
+
+// Device error word helpers (defined in tsp_project.cu).
+int* device_error_word();
+
+inline bool valid_launch(const tsp_launch& l) {
+  const int b = l.block_threads, w = l.warp_tile_w;
+  return (b == 64 || b == 128 || b == 256 || b == 512) && (w == 4 || w == 8 || w == 16 || w == 32) &&
+         (l.scatter == 0 || l.scatter == 1);
+}
+
+inline tsp_launch default_launch() {
+  tsp_launch l;
+  l.block_threads = 128;
+  l.warp_tile_w = 8;
+  l.scatter = 0;
+  return l;
+}
+
+}  // namespace tsp
+
+#define TSP_CUDA(call)                                     \
+  do {                                                     \
+    cudaError_t e__ = (call);                              \
+    if (e__ != cudaSuccess) return tsp::cuda_fail(e__, #call); \
+  } while (0)

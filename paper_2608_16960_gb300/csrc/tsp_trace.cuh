@@ -1,0 +1,450 @@
+// Per-ray traversal of a spherical grid (TomoSphero Sec. 3, steps 1-3, fused).
+//
+// The paper computes every crossing of a ray with every boundary (Sec. 3.1),
+// turns each into a region index by its crossing direction (Sec. 3.2,
+// Eq. 11-13), sorts them and forward-fills the voxel index (Sec. 3.3,
+// Table 2). Along a line, r(l) and the polar angle theta(l) are unimodal and
+// the azimuth phi(l) is monotone, so the sorted crossing list is a merge of at
+// most five monotone runs. This routine walks that merge lazily: for each
+// family (spheres, cones, half-planes) it keeps only the next crossing in the
+// direction the ray is moving, chosen from the two boundaries bounding the
+// current region. Each crossing sets one coordinate of the voxel index exactly
+// as Eq. 11-13 + forward fill do; a segment whose index is out of range (inside
+// the inner sphere, outside the outer sphere or outside a wedge) is skipped
+// (Table 2c). No buffers, no sort.
+//
+// Parameterisation: p(t) = q + t n with n the unit direction and q the point of
+// closest approach to the origin (q . n = 0, |q|^2 = b2). The start is t0 = x.n.
+//   sphere k:  t = -+ sqrt(R_k^2 - b2)                          (inbound / outbound)
+//   cone k (c = cos theta_k), with Q = q_z, w = Q^2 + b2 n_z^2, W = sqrt(w - c^2 b2):
+//     theta decreasing through it:  t = (b2 n_z c - Q W) / (Q c + n_z W)
+//     theta increasing through it:  t = (b2 n_z c + Q W) / (Q c - n_z W)
+//     (the roots of the cone quadratic of refs [28],[29], each tagged with its
+//      Eq. 12 direction; a non-positive denominator puts the root at infinity)
+//   half-plane j at azimuth psi_j: t = (q_y cos psi_j - q_x sin psi_j) / den_j,
+//     den_j = n_x sin psi_j - n_y cos psi_j, on the half-plane iff den_j m_z < 0
+//     where m_z = (q x n)_z (Eq. 13: the azimuth grows iff m_z > 0).
+// cos(theta) along the line peaks (Q > 0) or dips (Q < 0) once, at
+// t_e = b2 n_z / Q, with value sign(Q) sqrt(Q^2/b2 + n_z^2); before/after that
+// point theta moves monotonically, which fixes which cone comes next.
+//
+// Every choice is made from the current region, so a start index that is off
+// by one because the start lies within rounding of a boundary corrects itself
+// at the first crossing (that crossing is then "just behind" and fires at once).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace tsp {
+
+// Explicitly rounded arithmetic: the device build uses the round-to-nearest
+// intrinsics so no multiply-add is ever contracted implicitly; the host build
+// (used only to check the index logic on a CPU) maps them to plain operations.
+#if defined(__CUDA_ARCH__)
+#define TSP_HD __host__ __device__ __forceinline__
+#define T_MUL(a, b) __fmul_rn(a, b)
+#define T_ADD(a, b) __fadd_rn(a, b)
+#define T_SUB(a, b) __fsub_rn(a, b)
+#define T_SQRT(a) __fsqrt_rn(a)
+#define T_RCP(a) __frcp_rn(a)
+#define T_DIV(a, b) __fdividef(a, b)
+#else
+#define TSP_HD __host__ __device__ inline
+#define T_MUL(a, b) ((a) * (b))
+#define T_ADD(a, b) ((a) + (b))
+#define T_SUB(a, b) ((a) - (b))
+#define T_SQRT(a) sqrtf(a)
+#define T_RCP(a) (1.0f / (a))
+#define T_DIV(a, b) ((a) / (b))
+#endif
+
+// Grid tables as seen by a kernel (pointers into shared memory).
+struct TGrid {
+  const float* R2;  // [Nr+1] squared sphere radii (high part)
+  const float* R2L; // [Nr+1] low part: R_k^2 = R2 + R2L to ~2^-48
+  const float* C;   // [Ne+1] cos(theta_k), decreasing
+  const float* S2;  // [Ne+1] sin^2(theta_k), high part
+  const float* S2L; // [Ne+1] low part
+  const float* K2;  // [Ne+1] cos^2(theta_k), high part
+  const float* K2L; // [Ne+1] low part
+  const float* PC;  // [M] cos of half-plane azimuths
+  const float* PS;  // [M] sin of half-plane azimuths
+  const float* PA;  // [M] half-plane azimuth minus PA0, increasing in [0, 2 pi)
+  const int* SEC;   // [M] azimuth voxel index of the sector counter-clockwise of plane j (-1: outside)
+  int Nr, Ne, Na, M;
+  float pa0;
+};
+
+// Device-side description of a grid's table in global memory.
+struct GridDesc {
+  const float* table;  // R2 | R2L | C | S2 | S2L | K2 | K2L | PC | PS | PA | SEC (int bits)
+  int Nr, Ne, Na, M;
+  int words;           // table length in 32-bit words
+  float pa0;
+};
+
+TSP_HD TGrid tgrid_from_smem(const GridDesc& d, const float* s) {
+  TGrid g;
+  g.R2 = s;
+  g.R2L = s + (d.Nr + 1);
+  g.C = g.R2L + (d.Nr + 1);
+  g.S2 = g.C + (d.Ne + 1);
+  g.S2L = g.S2 + (d.Ne + 1);
+  g.K2 = g.S2L + (d.Ne + 1);
+  g.K2L = g.K2 + (d.Ne + 1);
+  g.PC = g.K2L + (d.Ne + 1);
+  g.PS = g.PC + d.M;
+  g.PA = g.PS + d.M;
+  g.SEC = reinterpret_cast<const int*>(g.PA + d.M);
+  g.Nr = d.Nr;
+  g.Ne = d.Ne;
+  g.Na = d.Na;
+  g.M = d.M;
+  g.pa0 = d.pa0;
+  return g;
+}
+
+// Cooperative copy of the grid table into shared memory (whole block).
+__device__ __forceinline__ void load_table(const GridDesc& d, float* s) {
+  for (int i = threadIdx.x; i < d.words; i += blockDim.x) s[i] = __ldg(d.table + i);
+  __syncthreads();
+}
+
+// ---- classification of one point (only at the ray's first in-grid point) ----
+
+// Radial region: number of k with R2[k] <= r2, minus one.
+TSP_HD int classify_r(const TGrid& G, float r2) {
+  int lo = 0, hi = G.Nr + 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (G.R2[mid] <= r2) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo - 1;
+}
+
+// Polar region of a point with z component pz and norm pn: number of k with
+// cos(theta_k) >= pz / pn (a prefix, the table decreasing), minus one.
+TSP_HD int classify_theta(const TGrid& G, float pz, float pn) {
+  int lo = 0, hi = G.Ne + 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (G.C[mid] * pn >= pz) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo - 1;
+}
+
+// Azimuth sector of a direction (px, py): the last plane j with PA[j] <= angle.
+TSP_HD int classify_sector(const TGrid& G, float px, float py) {
+  const float two_pi = 6.28318530717958647692f;
+  float a = atan2f(py, px) - G.pa0;
+  a = a - two_pi * floorf(a * (1.0f / two_pi));
+  int lo = 0, hi = G.M;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (G.PA[mid] <= a) lo = mid + 1;
+    else hi = mid;
+  }
+  int s = lo - 1;
+  return s < 0 ? G.M - 1 : s;
+}
+
+// ---- next-crossing rules per family ----
+
+TSP_HD int imin_(int a, int b) { return a < b ? a : b; }
+
+// ---- float-float (unevaluated sum hi + lo) arithmetic ----
+// Error-free products and sums (Dekker; Knuth's TwoSum; FMA-based TwoProduct,
+// as in Ogita, Rump and Oishi, "Accurate sum and dot product", SISC 2005).
+// Used once per ray for the impact parameter and per sphere/cone crossing for
+// the discriminant R^2 - b^2, whose cancellation near tangency float32 alone
+// cannot resolve.
+struct ff {
+  float hi, lo;
+};
+TSP_HD ff two_prod(float a, float b) {
+  const float p = T_MUL(a, b);
+  return ff{p, fmaf(a, b, -p)};
+}
+TSP_HD ff two_sum(float a, float b) {
+  const float s = T_ADD(a, b);
+  const float bb = T_SUB(s, a);
+  return ff{s, T_ADD(T_SUB(a, T_SUB(s, bb)), T_SUB(b, bb))};
+}
+TSP_HD ff ff_add(ff a, ff b) {
+  const ff s = two_sum(a.hi, b.hi);
+  return two_sum(s.hi, T_ADD(s.lo, T_ADD(a.lo, b.lo)));
+}
+TSP_HD ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+TSP_HD ff ff_mul(ff a, ff b) {
+  const ff p = two_prod(a.hi, b.hi);
+  return two_sum(p.hi, T_ADD(p.lo, T_ADD(T_MUL(a.hi, b.lo), T_MUL(a.lo, b.hi))));
+}
+TSP_HD ff ff_div(ff a, ff b) {
+  const float q1 = T_DIV(a.hi, b.hi);
+  const ff r = ff_add(a, ff_neg(ff_mul(ff{q1, 0.0f}, b)));
+  return two_sum(q1, T_DIV(r.hi, b.hi));
+}
+// a*d - b*c exactly rounded to float-float
+TSP_HD ff ff_cross(float a, float d, float b, float c) { return ff_add(two_prod(a, d), ff_neg(two_prod(b, c))); }
+
+struct RayState {
+  // line
+  float qx, qy, qz, nx, ny, nz, b2;
+  float b2lo;          // b2 + b2lo = squared impact parameter to ~2^-46
+  ff mxy2, mz2;        // |(x cross d)_xy|^2 and (x cross d)_z^2, exact to ~2^-46
+  float inv_dd;        // 1 / |d|^2
+  // radial
+  int ir, ir_next;
+  bool r_out;
+  float tr;
+  // polar
+  int ie, ie_next;
+  bool th_br2;   // past the extremum of theta
+  int th_mode;   // 0 walk, 1 no crossings, 2 one jump pending (line through the origin)
+  float th_sg, th_fe, th_te;
+  float tth;
+  // azimuth
+  int sec, sec_next;
+  int ph_mode;   // 0 walk, 1 no crossings, 2 one jump pending (line meets the z axis)
+  float mz;
+  float tph;
+};
+
+// R_k^2 - b^2 from the two-part table and impact parameter.
+TSP_HD float sphere_disc(const TGrid& G, const RayState& s, int k) {
+  return T_ADD(T_SUB(G.R2[k], s.b2), T_SUB(G.R2L[k], s.b2lo));
+}
+
+TSP_HD void radial_next(const TGrid& G, RayState& s) {
+  if (!s.r_out) {
+    const int k = s.ir;  // inner sphere of the current shell
+    const float dk = k >= 0 ? sphere_disc(G, s, k) : -1.0f;
+    if (dk > 0.0f) {
+      s.tr = -T_SQRT(dk);
+      s.ir_next = k - 1;
+      return;
+    }
+    s.r_out = true;  // passed the closest approach: from now on outward
+  }
+  const int k = s.ir + 1;  // outer sphere of the current shell
+  if (k <= G.Nr) {
+    s.tr = T_SQRT(fmaxf(sphere_disc(G, s, k), 0.0f));
+    s.ir_next = k;
+  } else {
+    s.tr = INFINITY;
+    s.ir_next = s.ir;
+  }
+}
+
+// W = sqrt(b2 sin^2 theta_k - m_z^2) = sqrt((|m_xy|^2 sin^2 - m_z^2 cos^2) / |d|^2),
+// m = x cross d, the difference taken in float-float (it cancels at tangency).
+TSP_HD float cone_w(const TGrid& G, const RayState& s, int k) {
+  const ff a = ff_mul(s.mxy2, ff{G.S2[k], G.S2L[k]});
+  const ff b = ff_mul(s.mz2, ff{G.K2[k], G.K2L[k]});
+  const float w2 = T_ADD(T_SUB(a.hi, b.hi), T_SUB(a.lo, b.lo));
+  return T_SQRT(fmaxf(T_MUL(w2, s.inv_dd), 0.0f));
+}
+
+TSP_HD void theta_next(const TGrid& G, RayState& s) {
+  if (s.th_mode != 0) {
+    s.tth = INFINITY;
+    return;
+  }
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool dec = s.th_br2 ? (s.th_sg < 0.0f) : (s.th_sg > 0.0f);
+    const float lim = s.th_br2 ? s.nz : s.th_fe;
+    if (dec) {  // theta decreasing: next is the cone at the region's small-theta side
+      const int k = s.ie;
+      if (k >= 0 && G.C[k] < lim) {
+        const float c = G.C[k];
+        const float W = cone_w(G, s, k);
+        const float num = T_SUB(T_MUL(T_MUL(s.b2, s.nz), c), T_MUL(s.qz, W));
+        const float den = T_ADD(T_MUL(s.qz, c), T_MUL(s.nz, W));
+        s.tth = den > 0.0f ? T_DIV(num, den) : (s.th_br2 ? INFINITY : -INFINITY);
+        s.ie_next = k - 1;
+        return;
+      }
+    } else {  // theta increasing: next is the cone at the region's large-theta side
+      const int k = s.ie + 1;
+      if (k <= G.Ne && G.C[k] > lim) {
+        const float c = G.C[k];
+        const float W = cone_w(G, s, k);
+        const float num = T_ADD(T_MUL(T_MUL(s.b2, s.nz), c), T_MUL(s.qz, W));
+        const float den = T_SUB(T_MUL(s.qz, c), T_MUL(s.nz, W));
+        s.tth = den > 0.0f ? T_DIV(num, den) : (s.th_br2 ? INFINITY : -INFINITY);
+        s.ie_next = k;
+        return;
+      }
+    }
+    if (s.th_br2) break;
+    s.th_br2 = true;  // no more crossings before the extremum: continue past it
+  }
+  s.tth = INFINITY;
+}
+
+TSP_HD void phi_next(const TGrid& G, RayState& s) {
+  if (s.ph_mode != 0) {
+    s.tph = INFINITY;
+    return;
+  }
+  const bool ccw = s.mz > 0.0f;
+  const int j = ccw ? (s.sec + 1 == G.M ? 0 : s.sec + 1) : s.sec;
+  const float pc = G.PC[j], ps = G.PS[j];
+  const float den = T_SUB(T_MUL(s.nx, ps), T_MUL(s.ny, pc));
+  if (ccw ? den < 0.0f : den > 0.0f) {
+    const float num = T_SUB(T_MUL(s.qy, pc), T_MUL(s.qx, ps));
+    s.tph = T_DIV(num, den);
+    s.sec_next = ccw ? j : (s.sec == 0 ? G.M - 1 : s.sec - 1);
+  } else {
+    s.tph = INFINITY;
+  }
+}
+
+// Trace one ray from start x along direction d (need not be unit).
+// op(voxel, dl) is called for every valid segment in order along the ray.
+// Returns false if the step cap was hit (an internal inconsistency).
+template <class Op>
+TSP_HD bool trace_ray(const TGrid& G, float xx, float xy, float xz, float dx,
+                                          float dy, float dz, Op& op) {
+  // Impact parameter of the exact input line, in float-float: m = x cross d,
+  // b^2 = |m|^2 / |d|^2. Float32 alone would leave R^2 - b^2 (and the cone
+  // discriminant) with an absolute error of an ulp of R^2 near tangency.
+  const ff mx = ff_cross(xy, dz, xz, dy);
+  const ff my = ff_cross(xz, dx, xx, dz);
+  const ff mzf = ff_cross(xx, dy, xy, dx);
+  const ff D = ff_add(ff_add(two_prod(dx, dx), two_prod(dy, dy)), two_prod(dz, dz));
+  if (!(D.hi > 0.0f) || !(D.hi < INFINITY)) return true;  // zero or non-finite direction: y = 0
+  RayState s;
+  s.mxy2 = ff_add(ff_mul(mx, mx), ff_mul(my, my));
+  s.mz2 = ff_mul(mzf, mzf);
+  const ff b2 = ff_div(ff_add(s.mxy2, s.mz2), D);
+  s.b2 = b2.hi;
+  s.b2lo = b2.lo;
+  s.inv_dd = T_RCP(D.hi);
+  s.mz = mzf.hi;  // only its sign is used: the azimuth grows along the ray iff m_z > 0 (Eq. 13)
+
+  const float inv = T_RCP(T_SQRT(D.hi));
+  s.nx = T_MUL(dx, inv);
+  s.ny = T_MUL(dy, inv);
+  s.nz = T_MUL(dz, inv);
+  const float t0 = T_ADD(T_ADD(T_MUL(xx, s.nx), T_MUL(xy, s.ny)), T_MUL(xz, s.nz));
+  // closest point q = (d x m) / |d|^2, from the float-float m: accurate to a few
+  // ulp of |q| itself (x - t0 n would carry an ulp of |x| instead)
+  const ff ex = ff_add(ff_mul(ff{dy, 0.0f}, mzf), ff_neg(ff_mul(ff{dz, 0.0f}, my)));
+  const ff ey = ff_add(ff_mul(ff{dz, 0.0f}, mx), ff_neg(ff_mul(ff{dx, 0.0f}, mzf)));
+  const ff ez = ff_add(ff_mul(ff{dx, 0.0f}, my), ff_neg(ff_mul(ff{dy, 0.0f}, mx)));
+  s.qx = T_MUL(ex.hi, s.inv_dd);
+  s.qy = T_MUL(ey.hi, s.inv_dd);
+  s.qz = T_MUL(ez.hi, s.inv_dd);
+
+  const float dout = sphere_disc(G, s, G.Nr);
+  if (!(dout > 0.0f)) return true;  // misses the outer sphere
+  const float sout = T_SQRT(dout);
+  if (!(t0 < sout)) return true;     // starts beyond the grid, moving away
+
+  float tcur;
+  if (t0 <= -sout) {  // enters through the outer sphere
+    tcur = -sout;
+    s.ir = G.Nr - 1;
+    s.r_out = false;
+  } else {            // starts inside the outer sphere
+    tcur = t0;
+    s.ir = imin_(classify_r(G, fmaf(t0, t0, s.b2)), G.Nr - 1);
+    s.r_out = t0 >= 0.0f;
+  }
+  const float px = fmaf(tcur, s.nx, s.qx), py = fmaf(tcur, s.ny, s.qy), pz = fmaf(tcur, s.nz, s.qz);
+  const float pn = T_SQRT(fmaf(tcur, tcur, s.b2));
+
+  // polar set-up
+  s.ie = classify_theta(G, pz, pn);
+  if (s.b2 == 0.0f) {              // through the origin: theta jumps there
+    s.th_mode = tcur < 0.0f ? 2 : 1;
+    if (tcur >= 0.0f) s.ie = classify_theta(G, s.nz, 1.0f);  // at or past the apex: the direction's bin
+  } else if (s.qz != 0.0f) {
+    s.th_mode = 0;
+    s.th_sg = s.qz > 0.0f ? 1.0f : -1.0f;
+    // |cos theta| at the extremum: sqrt(|m_xy|^2 / |m|^2)
+    const float rho2 = fminf(T_DIV(s.mxy2.hi, T_ADD(s.mxy2.hi, s.mz2.hi)), 1.0f);
+    s.th_fe = s.th_sg * T_SQRT(rho2);
+    s.th_te = T_DIV(T_MUL(s.b2, s.nz), s.qz);
+    s.th_br2 = !(tcur < s.th_te);
+  } else if (s.nz != 0.0f) {       // q in the plane z = 0: cos(theta) monotone
+    s.th_mode = 0;
+    s.th_sg = s.nz > 0.0f ? 1.0f : -1.0f;
+    s.th_fe = s.nz;
+    s.th_te = INFINITY;
+    s.th_br2 = false;
+  } else {                         // horizontal line in the plane z = 0
+    s.th_mode = 1;
+  }
+
+  // azimuth set-up
+  s.sec = classify_sector(G, px, py);
+  float t_ax = INFINITY;
+  int sec_ax = 0;
+  if (s.mz != 0.0f) {
+    s.ph_mode = 0;
+  } else {
+    const float nxy = fmaf(s.nx, s.nx, T_MUL(s.ny, s.ny));
+    if (nxy > 0.0f) {  // the line meets the z axis: azimuth jumps by pi there
+      t_ax = -T_DIV(fmaf(s.qx, s.nx, T_MUL(s.qy, s.ny)), nxy);
+      s.ph_mode = t_ax > tcur ? 2 : 1;
+      sec_ax = classify_sector(G, s.nx, s.ny);
+      if (t_ax <= tcur) s.sec = sec_ax;  // at or past the axis: the direction's azimuth
+    } else {
+      s.ph_mode = 1;  // vertical line: constant azimuth
+    }
+  }
+
+  radial_next(G, s);
+  s.tr = fmaxf(s.tr, tcur);
+  if (s.th_mode == 2) {
+    s.tth = 0.0f;
+    s.ie_next = classify_theta(G, s.nz, 1.0f);
+  } else {
+    theta_next(G, s);
+    s.tth = fmaxf(s.tth, tcur);
+  }
+  if (s.ph_mode == 2) {
+    s.tph = t_ax;
+    s.sec_next = sec_ax;
+  } else {
+    phi_next(G, s);
+    s.tph = fmaxf(s.tph, tcur);
+  }
+
+  const int cap = 2 * (G.Nr + G.Ne + 2) + G.M + 8;
+#pragma unroll 1
+  for (int it = 0; it < cap; ++it) {
+    const float tn = fminf(s.tr, fminf(s.tth, s.tph));
+    const int ia = G.SEC[s.sec];
+    if ((unsigned)s.ir < (unsigned)G.Nr && (unsigned)s.ie < (unsigned)G.Ne && ia >= 0) {
+      op((s.ir * G.Ne + s.ie) * G.Na + ia, T_SUB(tn, tcur));
+    }
+    tcur = tn;
+    if (s.tr <= s.tth && s.tr <= s.tph) {
+      s.ir = s.ir_next;
+      if (s.ir >= G.Nr) return true;  // left through the outer sphere
+      radial_next(G, s);
+      s.tr = fmaxf(s.tr, tcur);
+    } else if (s.tth <= s.tph) {
+      s.ie = s.ie_next;
+      if (s.th_mode == 2) s.th_mode = 1;
+      theta_next(G, s);
+      s.tth = fmaxf(s.tth, tcur);
+    } else {
+      s.sec = s.sec_next;
+      if (s.ph_mode == 2) s.ph_mode = 1;
+      phi_next(G, s);
+      s.tph = fmaxf(s.tph, tcur);
+    }
+  }
+  return false;
+}
+
+}  // namespace tsp

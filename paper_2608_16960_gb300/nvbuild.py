@@ -1,0 +1,75 @@
+"""Build the CUDA library libtsp.so in-tree for sm_103a (GB300) with nvcc.
+
+Each .cu under csrc/ compiles to an object in parallel; the objects link into
+one shared library with the CUDA runtime linked statically. No torch headers
+are involved: the library's ABI is plain C (include/tsp.h).
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import glob
+import os
+import shutil
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+SO = os.path.join(BUILD, "libtsp.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Translation units whose traversal must round identically in every kernel:
+# no implicit multiply-add contraction (explicit fmaf only).
+NO_FMAD = {"tsp_project.cu", "tsp_sirt.cu", "tsp_batch.cu", "tsp_segments.cu", "tsp_noalloc.cu"}
+
+
+def nvcc() -> str:
+    p = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(p):
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libtsp.so")
+    return p
+
+
+def _deps():
+    return sorted(glob.glob(os.path.join(CSRC, "*")) + [os.path.join(ROOT, "include", "tsp.h")])
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
+    os.makedirs(BUILD, exist_ok=True)
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    newest = max(os.path.getmtime(p) for p in _deps())
+    if not force and os.path.exists(SO) and os.path.getmtime(SO) >= newest:
+        return SO
+    cc = nvcc()
+
+    def compile_one(src):
+        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        cmd = [cc, "-c", src, "-o", obj, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+               "-I", os.path.join(ROOT, "include"), "-I", CSRC] + ARCH
+        if os.path.basename(src) in NO_FMAD:
+            cmd.append("-fmad=false")
+        if ptxas_v:
+            cmd += ["-Xptxas", "-v"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
+        return obj, r.stderr
+
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        results = list(ex.map(compile_one, srcs))
+    if verbose or ptxas_v:
+        for _, err in results:
+            if err:
+                print(err)
+    tmp = SO + f".{os.getpid()}.tmp"
+    cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH + ["-lcuda"] * 0
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stderr}")
+    os.replace(tmp, SO)
+    return SO
+
+
+if __name__ == "__main__":
+    import sys
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv))

@@ -1,0 +1,238 @@
+"""Python binding of the projector: grid and geometry handles, F, F^T, and the
+autograd function whose backward is the hand-written adjoint.
+
+Argument marshalling only: shapes and pointers are checked here, every step
+of the projection runs in libtsp.so (include/tsp.h). Torch provides device
+memory and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, tsp_launch
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream(t: torch.Tensor):
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Grid:
+    """Spherical grid (Sec. 2.2, 4.1): N_r+1 shells, N_e+1 polar cones, N_a+1 half-planes.
+
+    Mirrors tsp_grid_create. The handle lives on the current CUDA device."""
+
+    def __init__(self, r_edges, theta_edges, phi_edges):
+        L = _lib.load()
+        self.r = np.ascontiguousarray(r_edges, dtype=np.float64)
+        self.theta = np.ascontiguousarray(theta_edges, dtype=np.float64)
+        self.phi = np.ascontiguousarray(phi_edges, dtype=np.float64)
+        h = ctypes.c_void_p()
+        check(L.tsp_grid_create(_dptr(self.r), len(self.r), _dptr(self.theta), len(self.theta), _dptr(self.phi),
+                                len(self.phi), ctypes.byref(h)), "tsp_grid_create")
+        self.handle = h
+        self.device = torch.cuda.current_device()
+        self.shape = (len(self.r) - 1, len(self.theta) - 1, len(self.phi) - 1)
+
+    @classmethod
+    def from_edges(cls, edges):
+        return cls(edges.r, edges.theta, edges.phi)
+
+    @classmethod
+    def uniform(cls, shape, size_r=(0.0, 1.0)):
+        """Uniform grid of the given shape out to size_r (Listing 1)."""
+        nr, ne, na = shape
+        return cls(np.linspace(size_r[0], size_r[1], nr + 1), np.linspace(0, math.pi, ne + 1),
+                   np.linspace(0, 2 * math.pi, na + 1))
+
+    @property
+    def voxels(self):
+        return int(np.prod(self.shape))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _lib.load(build_if_missing=False).tsp_grid_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+class Geometry:
+    """View geometry handle: cone (ConeRectGeom), parallel (ParallelGeom) or
+    free-form rays (ViewGeom), Sec. 4.2. A collection of equal-shape views
+    (Sec. 4.3) is one handle with n_views > 1."""
+
+    def __init__(self, handle, kind, det_shape, n_rays, keep=None):
+        self.handle = handle
+        self.kind = kind
+        self.det_shape = det_shape  # (n_views, H, W) or (n_rays,)
+        self.n_rays = n_rays
+        self._keep = keep
+        self.device = torch.cuda.current_device()
+
+    @classmethod
+    def cone(cls, pos, shape, fov_deg, look_at=None, up=None):
+        """Pinhole detector at each pos looking at look_at (default origin);
+        shape (H, W) pixels; fov_deg scalar or (fov_h, fov_w), full angles."""
+        L = _lib.load()
+        pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+        nv = pos.shape[0]
+        H, W = shape
+        fh, fw = (fov_deg, fov_deg) if np.isscalar(fov_deg) else fov_deg
+        la = None if look_at is None else np.ascontiguousarray(np.asarray(look_at, np.float64).reshape(nv, 3))
+        uh = None if up is None else np.ascontiguousarray(np.asarray(up, np.float64).reshape(nv, 3))
+        h = ctypes.c_void_p()
+        check(L.tsp_geom_cone(nv, _dptr(pos), _dptr(la) if la is not None else None,
+                              _dptr(uh) if uh is not None else None, H, W, float(fh), float(fw), ctypes.byref(h)),
+              "tsp_geom_cone")
+        return cls(h, "cone", (nv, H, W), nv * H * W)
+
+    @classmethod
+    def parallel(cls, pos, shape, size, up=None):
+        L = _lib.load()
+        pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+        nv = pos.shape[0]
+        H, W = shape
+        sh, sw = (size, size) if np.isscalar(size) else size
+        uh = None if up is None else np.ascontiguousarray(np.asarray(up, np.float64).reshape(nv, 3))
+        h = ctypes.c_void_p()
+        check(L.tsp_geom_parallel(nv, _dptr(pos), _dptr(uh) if uh is not None else None, H, W, float(sh), float(sw),
+                                  ctypes.byref(h)), "tsp_geom_parallel")
+        return cls(h, "parallel", (nv, H, W), nv * H * W)
+
+    @classmethod
+    def rays(cls, starts: torch.Tensor, dirs: torch.Tensor, copy: bool = True):
+        """Free-form rays; starts and dirs are CUDA float32 (3, n) tensors."""
+        L = _lib.load()
+        for t, nm in ((starts, "starts"), (dirs, "dirs")):
+            _require_cuda(t, nm)
+            if t.dim() != 2 or t.shape[0] != 3:
+                raise ValueError(f"{nm} must have shape (3, n)")
+        n = starts.shape[1]
+        if dirs.shape[1] != n:
+            raise ValueError("starts and dirs differ in length")
+        h = ctypes.c_void_p()
+        check(L.tsp_geom_rays(n, ctypes.c_void_p(starts.data_ptr()), ctypes.c_void_p(dirs.data_ptr()), int(copy),
+                              ctypes.byref(h)), "tsp_geom_rays")
+        return cls(h, "rays", (n,), n, keep=None if copy else (starts, dirs))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _lib.load(build_if_missing=False).tsp_geom_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def _launch_ptr(launch):
+    if launch is None:
+        return None
+    if isinstance(launch, tsp_launch):
+        return ctypes.byref(launch)
+    return ctypes.byref(tsp_launch(*launch))
+
+
+def tsp_forward(grid: Grid, geom: Geometry, rho: torch.Tensor, launch=None) -> torch.Tensor:
+    """y = F rho (Eq. 5). rho: (N_r, N_e, N_a) or (B, N_r, N_e, N_a) CUDA float32.
+    Returns y shaped like the detector: (B?,) + det_shape."""
+    _require_cuda(rho, "rho")
+    batched = rho.dim() == 4
+    if tuple(rho.shape[-3:]) != grid.shape or rho.dim() not in (3, 4):
+        raise ValueError(f"rho shape {tuple(rho.shape)} does not match grid {grid.shape}")
+    B = rho.shape[0] if batched else 1
+    y = torch.empty((B,) + geom.det_shape, device=rho.device, dtype=torch.float32)
+    L = _lib.load()
+    check(L.tsp_forward_ex(grid.handle, geom.handle, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                           B, _launch_ptr(launch), _stream(rho)), "tsp_forward")
+    return y if batched else y[0]
+
+
+def tsp_adjoint(grid: Grid, geom: Geometry, y: torch.Tensor, out: torch.Tensor | None = None,
+                accumulate: bool = False, launch=None) -> torch.Tensor:
+    """F^T y (adjoint of Eq. 5). y: det_shape or (B,) + det_shape."""
+    _require_cuda(y, "y")
+    nd = len(geom.det_shape)
+    batched = y.dim() == nd + 1
+    if tuple(y.shape[-nd:]) != geom.det_shape:
+        raise ValueError(f"y shape {tuple(y.shape)} does not match geometry {geom.det_shape}")
+    B = y.shape[0] if batched else 1
+    if out is None:
+        out = torch.empty((B,) + grid.shape, device=y.device, dtype=torch.float32)
+        accumulate = False
+    else:
+        _require_cuda(out, "out")
+        if out.numel() != B * grid.voxels:
+            raise ValueError("out has the wrong size")
+    L = _lib.load()
+    check(L.tsp_adjoint_ex(grid.handle, geom.handle, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                           B, int(accumulate), _launch_ptr(launch), _stream(y)), "tsp_adjoint")
+    if batched:
+        return out.view((B,) + grid.shape)
+    return out.view(grid.shape)
+
+
+def tsp_count_segments(grid: Grid, geom: Geometry) -> torch.Tensor:
+    """Valid segments per ray (int32, det_shape)."""
+    L = _lib.load()
+    counts = torch.empty(geom.det_shape, dtype=torch.int32, device=torch.device("cuda", geom.device))
+    check(L.tsp_count_segments(grid.handle, geom.handle, ctypes.c_void_p(counts.data_ptr()), _stream(counts)),
+          "tsp_count_segments")
+    return counts
+
+
+def tsp_device_status(device_tensor: torch.Tensor | None = None) -> int:
+    L = _lib.load()
+    code = ctypes.c_int(0)
+    st = torch.cuda.current_stream().cuda_stream
+    L.tsp_device_status(ctypes.c_void_p(st), ctypes.byref(code))
+    return code.value
+
+
+class ProjectorFn(torch.autograd.Function):
+    """Autograd function: forward = tsp_forward, backward = tsp_adjoint (the
+    hand-written F^T), so parametric models (Eq. 7, Listing 8) differentiate
+    through the projector."""
+
+    @staticmethod
+    def forward(ctx, rho, grid, geom, launch=None):
+        ctx.grid, ctx.geom, ctx.launch = grid, geom, launch
+        return tsp_forward(grid, geom, rho.contiguous(), launch)
+
+    @staticmethod
+    def backward(ctx, gy):
+        g = tsp_adjoint(ctx.grid, ctx.geom, gy.contiguous(), launch=ctx.launch)
+        return g, None, None, None
+
+
+class Operator:
+    """Operator(grid, geom): callable F with autograd (Sec. 4.4, Listing 6)."""
+
+    def __init__(self, grid: Grid, geom: Geometry, launch=None):
+        self.grid, self.geom, self.launch = grid, geom, launch
+
+    def __call__(self, rho: torch.Tensor) -> torch.Tensor:
+        return ProjectorFn.apply(rho, self.grid, self.geom, self.launch)
+
+    def T(self, y: torch.Tensor) -> torch.Tensor:
+        return tsp_adjoint(self.grid, self.geom, y, launch=self.launch)
