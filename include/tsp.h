@@ -26,6 +26,7 @@
 #ifndef TSP_H_
 #define TSP_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -127,6 +128,27 @@ tsp_status tsp_adjoint_ex(tsp_grid grid, tsp_geom geom, const float* y, float* r
  * of Table 2c). counts: device int32 [n_rays], overwritten.
  */
 tsp_status tsp_count_segments(tsp_grid grid, tsp_geom geom, int* counts, void* stream);
+
+/*
+ * SIRT - simultaneous iterative reconstruction (the paper cites it among the
+ * algorithms its operator serves, Sec. 1 ref. [10]; standard definition):
+ *   R = 1 / (F 1), C = 1 / (F^T 1)  (0 where the sum is 0)
+ *   x <- x + C * F^T( R * (y - F x) )   repeated n_iter times.
+ * y: device float32 (n_rays) measurements; x: device float32 (N_r, N_e, N_a),
+ * the starting point on entry and the result on exit.
+ * workspace: caller-owned DEVICE scratch of at least tsp_sirt_workspace_bytes()
+ * bytes, 256-byte aligned; it holds R, C, the residual and the back-projection.
+ * flags: TSP_SIRT_NONNEG clamps x at 0 after every update;
+ * TSP_SIRT_REUSE_WEIGHTS skips recomputing R and C, which a previous call with
+ * the same grid, geometry and workspace left in the workspace.
+ * Enqueues 3 kernels per iteration (plus 3 for the weights and 2 memsets) on
+ * `stream`; no host synchronisation.
+ */
+#define TSP_SIRT_NONNEG 1
+#define TSP_SIRT_REUSE_WEIGHTS 2
+tsp_status tsp_sirt_workspace_bytes(tsp_grid grid, tsp_geom geom, size_t* bytes);
+tsp_status tsp_sirt(tsp_grid grid, tsp_geom geom, const float* y, float* x, int n_iter, int flags,
+                    void* workspace, size_t workspace_bytes, const tsp_launch* launch, void* stream);
 
 /*
  * tsp_device_status - synchronises `stream`, then reads and clears the device

@@ -15,6 +15,8 @@ _lock = threading.Lock()
 _lib = None
 
 TSP_OK = 0
+TSP_SIRT_NONNEG = 1
+TSP_SIRT_REUSE_WEIGHTS = 2
 STATUS_NAMES = {0: "TSP_OK", 1: "TSP_EINVAL", 2: "TSP_ENOTMONO", 3: "TSP_ENOMEM", 4: "TSP_ECUDA",
                 5: "TSP_ETIMEOUT", 6: "TSP_EDEVICE", 7: "TSP_ENOTSUP"}
 
@@ -52,6 +54,8 @@ SIGNATURES = {
     "tsp_adjoint": (_I, [_P, _P, _P, _P, _I, _I, _P]),
     "tsp_adjoint_ex": (_I, [_P, _P, _P, _P, _I, _I, _LP, _P]),
     "tsp_count_segments": (_I, [_P, _P, _P, _P]),
+    "tsp_sirt_workspace_bytes": (_I, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
+    "tsp_sirt": (_I, [_P, _P, _P, _P, _I, _I, _P, ctypes.c_size_t, _LP, _P]),
     "tsp_device_status": (_I, [_P, _IP]),
     "tsp_last_error": (ctypes.c_char_p, []),
     "tsp_version": (_I, []),

@@ -34,9 +34,31 @@ tsp_status check_device(int device) {
   return TSP_OK;
 }
 
+std::vector<error_reader>& reader_list() {
+  static std::vector<error_reader> v;
+  return v;
+}
+
+void register_error_reader(error_reader r) { reader_list().push_back(r); }
+
+const std::vector<error_reader>& error_readers() { return reader_list(); }
+
 }  // namespace tsp
 
 using tsp::fail;
+
+extern "C" tsp_status tsp_device_status(void* stream, int* code) {
+  if (!code) return fail(TSP_EINVAL, "tsp_device_status: NULL code");
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  for (tsp::error_reader r : tsp::error_readers()) {
+    cudaError_t e = r(&v, cs);
+    if (e != cudaSuccess) return tsp::cuda_fail(e, "tsp_device_status");
+  }
+  *code = v;
+  if (v != 0) return fail(TSP_EDEVICE, "a kernel set the device error word: " + std::to_string(v));
+  return TSP_OK;
+}
 
 extern "C" const char* tsp_last_error(void) { return g_last_error.c_str(); }
 
@@ -197,6 +219,11 @@ void cross3(const double a[3], const double b[3], double o[3]) {
   o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
+tsp::ff split_ff(double v) {
+  const float hi = float(v);
+  return tsp::ff{hi, float(v - double(hi))};
+}
+
 double norm3(const double a[3]) { return std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]); }
 
 // Detector frame: look toward look_at (origin by default), right = look x up_hint
@@ -267,10 +294,10 @@ extern "C" tsp_status tsp_geom_cone(int n_views, const double* pos, const double
     }
     ViewParams& p = g->h_views[v];
     for (int i = 0; i < 3; ++i) {
-      p.o[i] = float(pos[3 * v + i]);
-      p.a[i] = float(look[i]);
-      p.bu[i] = float(right[i] * tw);
-      p.bv[i] = float(upv[i] * th);
+      p.o[i] = split_ff(pos[3 * v + i]);
+      p.a[i] = split_ff(look[i]);
+      p.bu[i] = split_ff(right[i] * tw);
+      p.bv[i] = split_ff(upv[i] * th);
     }
   }
   tsp_status st = upload_views(g);
@@ -306,10 +333,10 @@ extern "C" tsp_status tsp_geom_parallel(int n_views, const double* pos, const do
     }
     ViewParams& p = g->h_views[v];
     for (int i = 0; i < 3; ++i) {
-      p.o[i] = float(pos[3 * v + i]);
-      p.a[i] = float(look[i]);
-      p.bu[i] = float(right[i] * size_w);
-      p.bv[i] = float(upv[i] * size_h);
+      p.o[i] = split_ff(pos[3 * v + i]);
+      p.a[i] = split_ff(look[i]);
+      p.bu[i] = split_ff(right[i] * size_w);
+      p.bv[i] = split_ff(upv[i] * size_h);
     }
   }
   tsp_status st = upload_views(g);

@@ -35,11 +35,11 @@ struct tsp_grid_s {
 
 enum GeomKind { GEOM_CONE = 0, GEOM_PARALLEL = 1, GEOM_RAYS = 2 };
 
-// Per-view parameters, float32 (rounded from host double arithmetic).
+// Per-view parameters as float-float pairs split from host double arithmetic.
 // cone:     origin = o; dir(u,v) = a + u*bu + v*bv, u = 2(j+.5)/W - 1, v = 1 - 2(i+.5)/H
 // parallel: origin(u,v) = o + u*bu + v*bv, u = (j+.5)/W - .5, v = .5 - (i+.5)/H; dir = a
 struct ViewParams {
-  float o[3], a[3], bu[3], bv[3];
+  tsp::ff o[3], a[3], bu[3], bv[3];
 };
 
 struct tsp_geom_s {
@@ -64,8 +64,15 @@ tsp_status check_device(int device);
 void build_grid_table(const double* r_edges, int n_r_edges, const double* theta_edges, int n_theta_edges,
                       const double* phi_edges, int n_phi_edges, std::vector<float>* table, tsp_grid_s* g);
 
-// Device error word helpers (defined in tsp_project.cu).
-int* device_error_word();
+// SIRT enqueue shared by the single and batched entry points (tsp_sirt.cu).
+tsp_status sirt_enqueue(tsp_grid grid, tsp_geom geom, const float* y, float* x, int n_iter, int flags, void* ws,
+                        const tsp_launch& l, cudaStream_t st);
+size_t sirt_workspace_bytes(const tsp_grid_s* grid, const tsp_geom_s* geom);
+
+// Readers of the per-translation-unit device error words (tsp_core.cu).
+typedef cudaError_t (*error_reader)(int* out, cudaStream_t st);
+void register_error_reader(error_reader r);
+const std::vector<error_reader>& error_readers();
 
 inline bool valid_launch(const tsp_launch& l) {
   const int b = l.block_threads, w = l.warp_tile_w;

@@ -1,0 +1,234 @@
+// Generic per-ray traversal kernel: one thread per ray, the grid table staged
+// in shared memory, a per-segment operation supplied as a functor.
+//
+//   struct Op {
+//     __device__ bool begin(int64_t ray);          // false: skip this ray
+//     __device__ void operator()(int voxel, float dl);
+//     __device__ void end(int64_t ray);
+//   };
+//
+// Every kernel of the library that walks rays instantiates this template, so
+// all of them see bit-identical segments (same code, -fmad=false).
+#pragma once
+
+#include "tsp_internal.h"
+
+// Device error word of this translation unit (device variables are not shared
+// across translation units without relocatable device code). A kernel that
+// detects an internal inconsistency ORs a bit into it instead of trapping; the
+// host reads and clears every unit's word through the registered readers.
+static __device__ int g_tsp_error_word;
+
+namespace tsp {
+
+static cudaError_t take_unit_error(int* out, cudaStream_t st) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_tsp_error_word, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const int zero = 0;
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_tsp_error_word, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  *out |= v;
+  return e;
+}
+
+namespace {
+struct UnitErrorRegistrar {
+  UnitErrorRegistrar() { register_error_reader(&take_unit_error); }
+};
+UnitErrorRegistrar unit_error_registrar;
+}  // namespace
+
+struct GeomArgs {
+  const ViewParams* views;
+  const float* starts;
+  const float* dirs;
+  int H, W;
+  int64_t n_rays;
+};
+
+inline GeomArgs geom_args(const tsp_geom_s* g) {
+  GeomArgs a;
+  a.views = g->d_views;
+  a.starts = g->starts;
+  a.dirs = g->dirs;
+  a.H = g->H;
+  a.W = g->W;
+  a.n_rays = g->n_rays;
+  return a;
+}
+
+// num / den for small integers, as float-float (the remainder is exact).
+__device__ __forceinline__ ff ratio_ff(int num, int den) {
+  const float n = float(num), d = float(den);
+  const float hi = __fdiv_rn(n, d);
+  return ff{hi, __fdiv_rn(fmaf(-hi, d, n), d)};
+}
+
+// Ray of a detector pixel (cone or parallel view) or of a free-form ray, as
+// float-float start x and direction d.
+template <int GK>
+__device__ __forceinline__ void ray_geometry(const GeomArgs& ga, int view, int row, int col, int64_t ray, ff x[3],
+                                             ff d[3]) {
+  if (GK == GEOM_RAYS) {
+    const int64_t n = ga.n_rays;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      x[i] = ff{__ldg(ga.starts + i * n + ray), 0.0f};
+      d[i] = ff{__ldg(ga.dirs + i * n + ray), 0.0f};
+    }
+    return;
+  }
+  const ViewParams& p = ga.views[view];
+  const bool cone = GK == GEOM_CONE;
+  const ff u = ratio_ff(2 * col + 1 - ga.W, cone ? ga.W : 2 * ga.W);
+  const ff v = ratio_ff(ga.H - 2 * row - 1, cone ? ga.H : 2 * ga.H);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const ff off = ff_add(ff_mul(u, p.bu[i]), ff_mul(v, p.bv[i]));
+    if (cone) {
+      x[i] = p.o[i];
+      d[i] = ff_add(p.a[i], off);
+    } else {
+      x[i] = ff_add(p.o[i], off);
+      d[i] = p.a[i];
+    }
+  }
+}
+
+// Map this thread to a ray: detector geometries tile a warp over tw x (32/tw)
+// pixels and stack the block's warps vertically; free-form rays are linear.
+template <int GK>
+__device__ __forceinline__ bool ray_of_thread(const GeomArgs& ga, int tw, int64_t& ray, ff x[3], ff d[3]) {
+  if (GK == GEOM_RAYS) {
+    ray = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (ray >= ga.n_rays) return false;
+    ray_geometry<GK>(ga, 0, 0, 0, ray, x, d);
+    return true;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int th = 32 / tw, bh = blockDim.x / tw;
+  const int col = blockIdx.x * tw + (lane % tw);
+  const int row = blockIdx.y * bh + warp * th + lane / tw;
+  if (col >= ga.W || row >= ga.H) return false;
+  const int view = blockIdx.z;
+  ray = (int64_t(view) * ga.H + row) * ga.W + col;
+  ray_geometry<GK>(ga, view, row, col, ray, x, d);
+  return true;
+}
+
+template <int GK, class Op>
+__global__ void __launch_bounds__(512) trace_kernel(GridDesc gd, GeomArgs ga, Op op, int tw) {
+  extern __shared__ float smem[];
+  load_table(gd, smem);
+  const TGrid G = tgrid_from_smem(gd, smem);
+  int64_t ray;
+  ff x[3], d[3];
+  if (!ray_of_thread<GK>(ga, tw, ray, x, d)) return;
+  if (!op.begin(ray)) return;
+  if (!trace_ray(G, x, d, op)) atomicOr(&g_tsp_error_word, 1);
+  op.end(ray);
+}
+
+struct LaunchShape {
+  dim3 grid, block;
+  size_t smem;
+};
+
+inline LaunchShape shape_for(const tsp_grid_s* grid, const tsp_geom_s* geom, const tsp_launch& l) {
+  LaunchShape s;
+  s.block = dim3(l.block_threads);
+  s.smem = sizeof(float) * size_t(grid->words);
+  if (geom->kind == GEOM_RAYS) {
+    s.grid = dim3(unsigned((geom->n_rays + l.block_threads - 1) / l.block_threads));
+  } else {
+    const int bh = l.block_threads / l.warp_tile_w;
+    s.grid = dim3((geom->W + l.warp_tile_w - 1) / l.warp_tile_w, (geom->H + bh - 1) / bh, geom->n_views);
+  }
+  return s;
+}
+
+// Launch trace_kernel for the geometry kind of `geom`.
+template <class Op>
+void launch_trace(const tsp_grid_s* grid, const tsp_geom_s* geom, const tsp_launch& l, const Op& op,
+                  cudaStream_t st) {
+  const LaunchShape s = shape_for(grid, geom, l);
+  const GridDesc gd = grid->desc();
+  const GeomArgs ga = geom_args(geom);
+  if (geom->kind == GEOM_CONE) trace_kernel<GEOM_CONE, Op><<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w);
+  else if (geom->kind == GEOM_PARALLEL)
+    trace_kernel<GEOM_PARALLEL, Op><<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w);
+  else trace_kernel<GEOM_RAYS, Op><<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w);
+}
+
+// Validation shared by the entry points that launch traversals.
+inline tsp_status check_trace_args(tsp_grid grid, tsp_geom geom, const void* a, const void* b, int batch,
+                                   const tsp_launch* l, const char* who) {
+  if (!grid || !geom) return fail(TSP_EINVAL, std::string(who) + ": NULL handle");
+  if (!a || !b) return fail(TSP_EINVAL, std::string(who) + ": NULL array");
+  if (batch <= 0) return fail(TSP_EINVAL, std::string(who) + ": batch must be >= 1");
+  if (l && !valid_launch(*l)) return fail(TSP_EINVAL, std::string(who) + ": invalid launch knobs");
+  tsp_status st = check_device(grid->device);
+  if (st != TSP_OK) return st;
+  st = check_device(geom->device);
+  if (st != TSP_OK) return st;
+  const tsp_launch lc = l ? *l : default_launch();
+  const LaunchShape s = shape_for(grid, geom, lc);
+  if (s.grid.y > 65535u || s.grid.z > 65535u || s.grid.x > 2147483647u)
+    return fail(TSP_ENOTSUP, std::string(who) + ": detector too large for one launch");
+  return TSP_OK;
+}
+
+// ---- per-segment operations shared across translation units ----
+
+// y[b] = sum rho[b][v] dl  (Eq. 5), optionally followed by an epilogue.
+template <int NB>
+struct GatherOp {
+  const float* __restrict__ rho;
+  float* __restrict__ y;
+  int64_t V, n_rays;
+  int nb;
+  float acc[NB];
+  __device__ __forceinline__ bool begin(int64_t) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) acc[b] = 0.0f;
+    return true;
+  }
+  __device__ __forceinline__ void operator()(int v, float dl) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (b < nb) acc[b] = fmaf(__ldg(rho + b * V + v), dl, acc[b]);
+  }
+  __device__ __forceinline__ void end(int64_t ray) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (b < nb) y[b * n_rays + ray] = acc[b];
+  }
+};
+
+// g[b][v] += w[b] dl with one atomic add per segment (adjoint of Eq. 5).
+template <int NB>
+struct ScatterOp {
+  const float* __restrict__ y;
+  float* __restrict__ g;
+  int64_t V, n_rays;
+  int nb;
+  float w[NB];
+  __device__ __forceinline__ bool begin(int64_t ray) {
+    bool any = false;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      w[b] = b < nb ? __ldg(y + b * n_rays + ray) : 0.0f;
+      any |= w[b] != 0.0f;
+    }
+    return any;
+  }
+  __device__ __forceinline__ void operator()(int v, float dl) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (b < nb && w[b] != 0.0f) atomicAdd(g + b * V + v, __fmul_rn(w[b], dl));
+  }
+  __device__ __forceinline__ void end(int64_t) {}
+};
+
+}  // namespace tsp

@@ -309,15 +309,18 @@ TSP_HD void phi_next(const TGrid& G, RayState& s) {
 // op(voxel, dl) is called for every valid segment in order along the ray.
 // Returns false if the step cap was hit (an internal inconsistency).
 template <class Op>
-TSP_HD bool trace_ray(const TGrid& G, float xx, float xy, float xz, float dx,
-                                          float dy, float dz, Op& op) {
-  // Impact parameter of the exact input line, in float-float: m = x cross d,
+TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d[3], Op& op) {
+  const float xx = x[0].hi, xy = x[1].hi, xz = x[2].hi;
+  const float dx = d[0].hi, dy = d[1].hi, dz = d[2].hi;
+  // The line arrives as float-float start and direction (exact for float32
+  // inputs; carrying the rounding residue of detector-generated rays).
+  // Impact parameter of that line, in float-float: m = x cross d,
   // b^2 = |m|^2 / |d|^2. Float32 alone would leave R^2 - b^2 (and the cone
   // discriminant) with an absolute error of an ulp of R^2 near tangency.
-  const ff mx = ff_cross(xy, dz, xz, dy);
-  const ff my = ff_cross(xz, dx, xx, dz);
-  const ff mzf = ff_cross(xx, dy, xy, dx);
-  const ff D = ff_add(ff_add(two_prod(dx, dx), two_prod(dy, dy)), two_prod(dz, dz));
+  const ff mx = ff_add(ff_mul(x[1], d[2]), ff_neg(ff_mul(x[2], d[1])));
+  const ff my = ff_add(ff_mul(x[2], d[0]), ff_neg(ff_mul(x[0], d[2])));
+  const ff mzf = ff_add(ff_mul(x[0], d[1]), ff_neg(ff_mul(x[1], d[0])));
+  const ff D = ff_add(ff_add(ff_mul(d[0], d[0]), ff_mul(d[1], d[1])), ff_mul(d[2], d[2]));
   if (!(D.hi > 0.0f) || !(D.hi < INFINITY)) return true;  // zero or non-finite direction: y = 0
   RayState s;
   s.mxy2 = ff_add(ff_mul(mx, mx), ff_mul(my, my));
@@ -335,9 +338,9 @@ TSP_HD bool trace_ray(const TGrid& G, float xx, float xy, float xz, float dx,
   const float t0 = T_ADD(T_ADD(T_MUL(xx, s.nx), T_MUL(xy, s.ny)), T_MUL(xz, s.nz));
   // closest point q = (d x m) / |d|^2, from the float-float m: accurate to a few
   // ulp of |q| itself (x - t0 n would carry an ulp of |x| instead)
-  const ff ex = ff_add(ff_mul(ff{dy, 0.0f}, mzf), ff_neg(ff_mul(ff{dz, 0.0f}, my)));
-  const ff ey = ff_add(ff_mul(ff{dz, 0.0f}, mx), ff_neg(ff_mul(ff{dx, 0.0f}, mzf)));
-  const ff ez = ff_add(ff_mul(ff{dx, 0.0f}, my), ff_neg(ff_mul(ff{dy, 0.0f}, mx)));
+  const ff ex = ff_add(ff_mul(d[1], mzf), ff_neg(ff_mul(d[2], my)));
+  const ff ey = ff_add(ff_mul(d[2], mx), ff_neg(ff_mul(d[0], mzf)));
+  const ff ez = ff_add(ff_mul(d[0], my), ff_neg(ff_mul(d[1], mx)));
   s.qx = T_MUL(ex.hi, s.inv_dd);
   s.qy = T_MUL(ey.hi, s.inv_dd);
   s.qz = T_MUL(ez.hi, s.inv_dd);

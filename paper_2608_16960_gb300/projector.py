@@ -192,6 +192,34 @@ def tsp_adjoint(grid: Grid, geom: Geometry, y: torch.Tensor, out: torch.Tensor |
     return out.view(grid.shape)
 
 
+def sirt_workspace(grid: Grid, geom: Geometry) -> torch.Tensor:
+    """Device scratch for tsp_sirt (R, C, residual, back-projection)."""
+    L = _lib.load()
+    n = ctypes.c_size_t()
+    check(L.tsp_sirt_workspace_bytes(grid.handle, geom.handle, ctypes.byref(n)), "tsp_sirt_workspace_bytes")
+    return torch.empty(n.value, dtype=torch.uint8, device=torch.device("cuda", geom.device))
+
+
+def tsp_sirt(grid: Grid, geom: Geometry, y: torch.Tensor, x: torch.Tensor, n_iter: int, nonneg: bool = False,
+             workspace: torch.Tensor | None = None, reuse_weights: bool = False, launch=None) -> torch.Tensor:
+    """n_iter SIRT updates of x (in place) toward measurements y; returns x."""
+    _require_cuda(y, "y")
+    _require_cuda(x, "x")
+    if tuple(x.shape[-3:]) != grid.shape or x.numel() != grid.voxels:
+        raise ValueError("x must have the grid's shape")
+    if y.numel() != geom.n_rays:
+        raise ValueError("y must hold one value per ray")
+    ws = sirt_workspace(grid, geom) if workspace is None else workspace
+    if reuse_weights and workspace is None:
+        raise ValueError("reuse_weights needs the workspace of an earlier call")
+    flags = (_lib.TSP_SIRT_NONNEG if nonneg else 0) | (_lib.TSP_SIRT_REUSE_WEIGHTS if reuse_weights else 0)
+    L = _lib.load()
+    check(L.tsp_sirt(grid.handle, geom.handle, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                     int(n_iter), flags, ctypes.c_void_p(ws.data_ptr()), ws.numel(), _launch_ptr(launch),
+                     _stream(x)), "tsp_sirt")
+    return x
+
+
 def tsp_count_segments(grid: Grid, geom: Geometry) -> torch.Tensor:
     """Valid segments per ray (int32, det_shape)."""
     L = _lib.load()
