@@ -188,6 +188,13 @@ TSP_HD ff ff_div(ff a, ff b) {
   const ff r = ff_add(a, ff_neg(ff_mul(ff{q1, 0.0f}, b)));
   return two_sum(q1, T_DIV(r.hi, b.hi));
 }
+TSP_HD ff ff_sqrt(ff a) {
+  const float r = T_SQRT(a.hi);
+  if (!(r > 0.0f)) return ff{0.0f, 0.0f};
+  const ff r2 = two_prod(r, r);
+  const float e = T_ADD(T_SUB(T_SUB(a.hi, r2.hi), r2.lo), a.lo);
+  return two_sum(r, T_DIV(e, T_ADD(r, r)));
+}
 // a*d - b*c exactly rounded to float-float
 TSP_HD ff ff_cross(float a, float d, float b, float c) { return ff_add(two_prod(a, d), ff_neg(two_prod(b, c))); }
 
@@ -195,8 +202,7 @@ struct RayState {
   // line
   float qx, qy, qz, nx, ny, nz, b2;
   float b2lo;          // b2 + b2lo = squared impact parameter to ~2^-46
-  ff mxy2, mz2;        // |(x cross d)_xy|^2 and (x cross d)_z^2, exact to ~2^-46
-  float inv_dd;        // 1 / |d|^2
+  ff mxy2, mz2;        // |(q cross n)_xy|^2 and (q cross n)_z^2 in float-float
   // radial
   int ir, ir_next;
   bool r_out;
@@ -240,13 +246,13 @@ TSP_HD void radial_next(const TGrid& G, RayState& s) {
   }
 }
 
-// W = sqrt(b2 sin^2 theta_k - m_z^2) = sqrt((|m_xy|^2 sin^2 - m_z^2 cos^2) / |d|^2),
-// m = x cross d, the difference taken in float-float (it cancels at tangency).
+// W = sqrt(b2 sin^2 theta_k - m_z^2) = sqrt(|m_xy|^2 sin^2 - m_z^2 cos^2) with
+// m = q x n, the difference taken in float-float (it cancels at tangency).
 TSP_HD float cone_w(const TGrid& G, const RayState& s, int k) {
   const ff a = ff_mul(s.mxy2, ff{G.S2[k], G.S2L[k]});
   const ff b = ff_mul(s.mz2, ff{G.K2[k], G.K2L[k]});
   const float w2 = T_ADD(T_SUB(a.hi, b.hi), T_SUB(a.lo, b.lo));
-  return T_SQRT(fmaxf(T_MUL(w2, s.inv_dd), 0.0f));
+  return T_SQRT(fmaxf(w2, 0.0f));
 }
 
 TSP_HD void theta_next(const TGrid& G, RayState& s) {
@@ -314,36 +320,41 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d[3], Op& op) {
   const float dx = d[0].hi, dy = d[1].hi, dz = d[2].hi;
   // The line arrives as float-float start and direction (exact for float32
   // inputs; carrying the rounding residue of detector-generated rays).
-  // Impact parameter of that line, in float-float: m = x cross d,
-  // b^2 = |m|^2 / |d|^2. Float32 alone would leave R^2 - b^2 (and the cone
-  // discriminant) with an absolute error of an ulp of R^2 near tangency.
+  // Its closest point to the origin, q = (d x (x x d)) / |d|^2, is formed in
+  // float-float: accurate to ~2^-46 |x| absolute, where x - (x.n) n in float32
+  // would carry an ulp of |x|. Every other quantity is then derived from
+  // (q, n) alone, n the unit direction (float-float; its float32 part drives
+  // the crossing formulas), so spheres, cones and half-planes all see the same
+  // line: m = q x n, b^2 = |m_xy|^2 + m_z^2. Near
+  // tangency R^2 - b^2 and the cone discriminant cancel; both are formed from
+  // these float-float parts.
   const ff mx = ff_add(ff_mul(x[1], d[2]), ff_neg(ff_mul(x[2], d[1])));
   const ff my = ff_add(ff_mul(x[2], d[0]), ff_neg(ff_mul(x[0], d[2])));
   const ff mzf = ff_add(ff_mul(x[0], d[1]), ff_neg(ff_mul(x[1], d[0])));
   const ff D = ff_add(ff_add(ff_mul(d[0], d[0]), ff_mul(d[1], d[1])), ff_mul(d[2], d[2]));
   if (!(D.hi > 0.0f) || !(D.hi < INFINITY)) return true;  // zero or non-finite direction: y = 0
+  const ff qxf = ff_div(ff_add(ff_mul(d[1], mzf), ff_neg(ff_mul(d[2], my))), D);
+  const ff qyf = ff_div(ff_add(ff_mul(d[2], mx), ff_neg(ff_mul(d[0], mzf))), D);
+  const ff qzf = ff_div(ff_add(ff_mul(d[0], my), ff_neg(ff_mul(d[1], mx))), D);
   RayState s;
-  s.mxy2 = ff_add(ff_mul(mx, mx), ff_mul(my, my));
-  s.mz2 = ff_mul(mzf, mzf);
-  const ff b2 = ff_div(ff_add(s.mxy2, s.mz2), D);
+  const ff dn = ff_sqrt(D);
+  const ff nxf = ff_div(d[0], dn), nyf = ff_div(d[1], dn), nzf = ff_div(d[2], dn);  // unit to ~2^-44
+  s.nx = nxf.hi;
+  s.ny = nyf.hi;
+  s.nz = nzf.hi;
+  const ff mnx = ff_add(ff_mul(qyf, nzf), ff_neg(ff_mul(qzf, nyf)));
+  const ff mny = ff_add(ff_mul(qzf, nxf), ff_neg(ff_mul(qxf, nzf)));
+  const ff mnz = ff_add(ff_mul(qxf, nyf), ff_neg(ff_mul(qyf, nxf)));
+  s.mxy2 = ff_add(ff_mul(mnx, mnx), ff_mul(mny, mny));
+  s.mz2 = ff_mul(mnz, mnz);
+  const ff b2 = ff_add(s.mxy2, s.mz2);
   s.b2 = b2.hi;
   s.b2lo = b2.lo;
-  s.inv_dd = T_RCP(D.hi);
-  s.mz = mzf.hi;  // only its sign is used: the azimuth grows along the ray iff m_z > 0 (Eq. 13)
-
-  const float inv = T_RCP(T_SQRT(D.hi));
-  s.nx = T_MUL(dx, inv);
-  s.ny = T_MUL(dy, inv);
-  s.nz = T_MUL(dz, inv);
+  s.mz = mnz.hi;  // only its sign is used: the azimuth grows along the ray iff m_z > 0 (Eq. 13)
+  s.qx = qxf.hi;
+  s.qy = qyf.hi;
+  s.qz = qzf.hi;
   const float t0 = T_ADD(T_ADD(T_MUL(xx, s.nx), T_MUL(xy, s.ny)), T_MUL(xz, s.nz));
-  // closest point q = (d x m) / |d|^2, from the float-float m: accurate to a few
-  // ulp of |q| itself (x - t0 n would carry an ulp of |x| instead)
-  const ff ex = ff_add(ff_mul(d[1], mzf), ff_neg(ff_mul(d[2], my)));
-  const ff ey = ff_add(ff_mul(d[2], mx), ff_neg(ff_mul(d[0], mzf)));
-  const ff ez = ff_add(ff_mul(d[0], my), ff_neg(ff_mul(d[1], mx)));
-  s.qx = T_MUL(ex.hi, s.inv_dd);
-  s.qy = T_MUL(ey.hi, s.inv_dd);
-  s.qz = T_MUL(ez.hi, s.inv_dd);
 
   const float dout = sphere_disc(G, s, G.Nr);
   if (!(dout > 0.0f)) return true;  // misses the outer sphere
