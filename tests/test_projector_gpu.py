@@ -229,7 +229,11 @@ def test_paper_scale_forward_sampled(paper_scale):
 
 def test_paper_scale_adjoint_sparse_rays(paper_scale):
     """Full-size adjoint with y non-zero on every 509th ray only, so the oracle
-    can compute the exact volume from those rays."""
+    can compute the exact volume from those rays. Each voxel is then fed by one
+    or two segments, so a segment whose end is a boundary crossed at a grazing
+    angle alpha shows the float32 position error (~1e-6 at r ~ 20) amplified by
+    1 / sin(alpha) undiluted: normwise 1e-4 and per voxel 1e-3 bound it; the
+    per-voxel 1e-4 bar applies to dense back-projections (next test)."""
     wl, grid, geoms = paper_scale
     for v, g in zip(wl.views, geoms):
         idx = np.arange(0, v.n_rays, 509)
@@ -238,7 +242,21 @@ def test_paper_scale_adjoint_sparse_rays(paper_scale):
         out = tsp_adjoint(grid, g, torch.tensor(yv.reshape(g.det_shape), device=DEV)).cpu().numpy()
         st, di = oracle_rays(v)
         ref = oracle.adjoint(wl.edges, st[idx], di[idx], yv[idx].astype(np.float64))
-        parity(out, ref, what=f"adjoint {v.kind}")
+        parity(out, ref, rel=1e-3, what=f"sparse adjoint {v.kind}")
+        assert np.linalg.norm(out - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
+def test_paper_scale_adjoint_dense_views(paper_scale):
+    """Full-size grid, every ray of two whole views non-zero: per-voxel 1e-4."""
+    wl, grid, geoms = paper_scale
+    for v in wl.views:
+        sub = type(v)(v.kind, v.pos[:2], v.shape, v.fov_deg, v.size)
+        g = Geometry.cone(sub.pos, sub.shape, sub.fov_deg) if v.kind == "cone" else Geometry.parallel(sub.pos, sub.shape, sub.size)
+        yv = synth.uniform_volume(g.det_shape, 73)
+        out = tsp_adjoint(grid, g, torch.tensor(yv, device=DEV)).cpu().numpy()
+        st, di = oracle_rays(sub)
+        ref = oracle.adjoint(wl.edges, st, di, yv.reshape(-1).astype(np.float64))
+        parity(out, ref, what=f"dense adjoint {v.kind}")
 
 
 def test_paper_scale_adjoint_identity(paper_scale):
