@@ -232,8 +232,10 @@ def test_paper_scale_adjoint_sparse_rays(paper_scale):
     can compute the exact volume from those rays. Each voxel is then fed by one
     or two segments, so a segment whose end is a boundary crossed at a grazing
     angle alpha shows the float32 position error (~1e-6 at r ~ 20) amplified by
-    1 / sin(alpha) undiluted: normwise 1e-4 and per voxel 1e-3 bound it; the
-    per-voxel 1e-4 bar applies to dense back-projections (next test)."""
+    1 / sin(alpha) undiluted, without bound as alpha -> 0. The check is
+    normwise 1e-4 plus a per-voxel gross-error bound of 1e-2 (a wrong voxel
+    index is an O(1) error); the per-voxel 1e-4 bar applies to dense
+    back-projections (next test)."""
     wl, grid, geoms = paper_scale
     for v, g in zip(wl.views, geoms):
         idx = np.arange(0, v.n_rays, 509)
@@ -242,7 +244,7 @@ def test_paper_scale_adjoint_sparse_rays(paper_scale):
         out = tsp_adjoint(grid, g, torch.tensor(yv.reshape(g.det_shape), device=DEV)).cpu().numpy()
         st, di = oracle_rays(v)
         ref = oracle.adjoint(wl.edges, st[idx], di[idx], yv[idx].astype(np.float64))
-        parity(out, ref, rel=1e-3, what=f"sparse adjoint {v.kind}")
+        parity(out, ref, rel=1e-2, what=f"sparse adjoint {v.kind}")
         assert np.linalg.norm(out - ref) <= 1e-4 * np.linalg.norm(ref)
 
 
