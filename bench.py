@@ -36,7 +36,7 @@ UNIT = "rays/s"
 # of the next crossing, segment length, gather-accumulate, and the average
 # next-crossing update over the sphere / cone / half-plane mix of the workload);
 # the derivation is written out in the design notes.
-OPS_PER_SEGMENT = 15.0
+OPS_PER_SEGMENT = 13.0
 SMS, FP32_LANES_PER_SM = 152, 128
 
 
