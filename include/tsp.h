@@ -151,6 +151,29 @@ tsp_status tsp_sirt(tsp_grid grid, tsp_geom geom, const float* y, float* x, int 
                     void* workspace, size_t workspace_bytes, const tsp_launch* launch, void* stream);
 
 /*
+ * tsp_sirt_noalloc - tsp_sirt without a caller workspace and without any
+ * device allocation. (An addition of this library; the paper has no
+ * counterpart.) It is for callers that cannot call cudaMalloc: onboard or
+ * real-time reconstruction code bound to a memory budget fixed at start-up,
+ * pipelines where an allocation's implicit synchronisation would stall
+ * latency-critical work, and hosts whose own allocator owns the device pool.
+ * The scratch lives in a static device array of TSP_NOALLOC_SCRATCH_BYTES
+ * (32 MiB) that every GPU loading this library holds until the process exits;
+ * a grid and geometry needing more (about n_rays + voxels > 4.19 million)
+ * return TSP_ENOTSUP with the size in the message, and allocate nothing.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any CUDA
+ * stream capture. Every call on a device shares the array and leaves its
+ * contents behind; each call clears what must start at zero and recomputes
+ * the SIRT weights, so flags accepts TSP_SIRT_NONNEG only. Calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on the array.
+ * Arguments and results are otherwise those of tsp_sirt.
+ */
+#define TSP_NOALLOC_SCRATCH_BYTES (32u << 20)
+tsp_status tsp_sirt_noalloc(tsp_grid grid, tsp_geom geom, const float* y, float* x, int n_iter, int flags,
+                            void* stream);
+
+/*
  * tsp_device_status - synchronises `stream`, then reads and clears the device
  * error word (0 = no kernel reported an inconsistency).
  */

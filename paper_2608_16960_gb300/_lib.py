@@ -56,6 +56,7 @@ SIGNATURES = {
     "tsp_count_segments": (_I, [_P, _P, _P, _P]),
     "tsp_sirt_workspace_bytes": (_I, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "tsp_sirt": (_I, [_P, _P, _P, _P, _I, _I, _P, ctypes.c_size_t, _LP, _P]),
+    "tsp_sirt_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _P]),
     "tsp_device_status": (_I, [_P, _IP]),
     "tsp_last_error": (ctypes.c_char_p, []),
     "tsp_version": (_I, []),

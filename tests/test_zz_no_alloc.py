@@ -1,0 +1,71 @@
+"""tsp_sirt_noalloc: SIRT for callers that cannot allocate device memory.
+
+Callers such as onboard or real-time reconstruction code with a memory budget
+fixed at start-up, pipelines that cannot afford the synchronisation a
+cudaMalloc/cudaFree implies, or hosts whose own allocator owns the device pool,
+use this entry point: it keeps its scratch in a static device array instead of
+asking for a workspace. These tests call it through the C ABI twice in a row,
+on different problems (the shared array keeps the previous call's contents),
+and compare each result with the workspace-based tsp_sirt under the parity
+tolerance of the other tests.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2608_16960_gb300 import _lib, synth, workloads
+from paper_2608_16960_gb300.projector import Geometry, Grid, tsp_device_status, tsp_forward, tsp_sirt
+
+from _util import parity
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _noalloc(grid, geom, y, x, n_iter, nonneg):
+    L = _lib.load()
+    st = L.tsp_sirt_noalloc(grid.handle, geom.handle, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                            n_iter, _lib.TSP_SIRT_NONNEG if nonneg else 0,
+                            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return st
+
+
+def _problem(kind):
+    if kind == "tiny":
+        wl = workloads.tiny()
+        grid = Grid.from_edges(wl.edges)
+        v = wl.views[0]
+        geom = Geometry.cone(v.pos, v.shape, v.fov_deg)
+        truth = wl.rho
+    else:
+        e = synth.grid_edges(16, 12, 24)
+        grid = Grid.from_edges(e)
+        geom = Geometry.cone(synth.circular_orbit(6, 60.0, incline_deg=25.0), (40, 36), 50.0)
+        truth = synth.training_phantom(e, 77)
+    y = tsp_forward(grid, geom, torch.tensor(truth, device=DEV))
+    return grid, geom, y
+
+
+def test_noalloc_matches_workspace_sirt_two_calls_in_a_row():
+    for kind, n_iter, nonneg in (("tiny", 6, False), ("multiview", 4, True)):
+        grid, geom, y = _problem(kind)
+        x_ref = torch.zeros(grid.shape, device=DEV)
+        tsp_sirt(grid, geom, y, x_ref, n_iter, nonneg=nonneg)
+        x = torch.full(grid.shape, 0.0, device=DEV)
+        assert _noalloc(grid, geom, y, x, n_iter, nonneg) == 0, _lib.load().tsp_last_error()
+        torch.cuda.synchronize()
+        parity(x.cpu().numpy(), x_ref.cpu().numpy(), what=f"noalloc sirt {kind}")
+    assert tsp_device_status() == 0
+
+
+def test_noalloc_rejection_status_and_message():
+    wl = workloads.paper_scale()
+    grid = Grid.from_edges(wl.edges)
+    geom = Geometry.cone(synth.circular_orbit(96, 60.0), (256, 256), 30.0)  # 6.3 M rays: above 32 MiB
+    y = torch.zeros(geom.det_shape, device=DEV)
+    x = torch.zeros(grid.shape, device=DEV)
+    st = _noalloc(grid, geom, y, x, 1, False)
+    assert st == 7  # TSP_ENOTSUP
+    assert b"static scratch" in _lib.load().tsp_last_error()
