@@ -130,6 +130,22 @@ tsp_status tsp_adjoint_ex(tsp_grid grid, tsp_geom geom, const float* y, float* r
 tsp_status tsp_count_segments(tsp_grid grid, tsp_geom geom, int* counts, void* stream);
 
 /*
+ * tsp_autotune - times candidate launch knobs (threads per block 64..512, warp
+ * tiles 4..32 pixels wide, and for the adjoint the scatter strategy) for this
+ * grid and geometry, and caches the fastest per size class (each grid and
+ * detector dimension rounded up to a power of two). Calls made afterwards
+ * without explicit knobs (launch == NULL) on a grid and geometry of the same
+ * class use the cached choice. Synchronous: allocates and frees temporary
+ * device buffers of one volume and one detector, launches each candidate
+ * three times. fwd / adj receive the choices (may be NULL).
+ */
+tsp_status tsp_autotune(tsp_grid grid, tsp_geom geom, tsp_launch* fwd, tsp_launch* adj, void* stream);
+/* Cached choice for this size class, or TSP_ENOTSUP if it was never tuned. */
+tsp_status tsp_autotune_lookup(tsp_grid grid, tsp_geom geom, tsp_launch* fwd, tsp_launch* adj);
+/* Forget every cached choice. */
+void tsp_autotune_clear(void);
+
+/*
  * SIRT - simultaneous iterative reconstruction (the paper cites it among the
  * algorithms its operator serves, Sec. 1 ref. [10]; standard definition):
  *   R = 1 / (F 1), C = 1 / (F^T 1)  (0 where the sum is 0)
@@ -172,6 +188,40 @@ tsp_status tsp_sirt(tsp_grid grid, tsp_geom geom, const float* y, float* x, int 
 #define TSP_NOALLOC_SCRATCH_BYTES (32u << 20)
 tsp_status tsp_sirt_noalloc(tsp_grid grid, tsp_geom geom, const float* y, float* x, int n_iter, int flags,
                             void* stream);
+
+/*
+ * Batched SIRT over many independent reconstructions of uneven sizes (each
+ * item its own grid, geometry, measurements y and volume x; device pointers
+ * owned by the caller, valid for the batch's lifetime). Each SIRT stage runs
+ * as one persistent launch over all items: blocks take (item, detector tile)
+ * work from an atomic counter. Per item, the warp tile and scatter strategy
+ * come from tsp_autotune's cache for its size class (defaults otherwise); the
+ * block size from the item with the most rays.
+ *   tsp_batch_create         - host-side plan (synchronous; small upload).
+ *   tsp_batch_workspace_bytes- device scratch for n_iter iterations: R and the
+ *                              residual per ray, C and the back-projection per
+ *                              voxel, stage counters; 256-byte aligned.
+ *   tsp_batch_sirt           - enqueue weights + n_iter iterations on stream.
+ *   tsp_batch_sirt_capture   - capture that schedule once into a CUDA graph
+ *                              (on a private stream) bound to this workspace;
+ *   tsp_batch_sirt_launch    - replay it with one graph launch on stream.
+ * Each run starts from the items' current x. flags: TSP_SIRT_NONNEG only.
+ */
+typedef struct tsp_batch_s* tsp_batch;
+typedef struct {
+  tsp_grid grid;
+  tsp_geom geom;
+  const float* y;
+  float* x;
+} tsp_batch_item;
+tsp_status tsp_batch_create(const tsp_batch_item* items, int n_items, tsp_batch* out);
+tsp_status tsp_batch_workspace_bytes(tsp_batch batch, int n_iter, size_t* bytes);
+tsp_status tsp_batch_sirt(tsp_batch batch, int n_iter, int flags, void* workspace, size_t workspace_bytes,
+                          void* stream);
+tsp_status tsp_batch_sirt_capture(tsp_batch batch, int n_iter, int flags, void* workspace, size_t workspace_bytes);
+tsp_status tsp_batch_sirt_launch(tsp_batch batch, void* stream);
+tsp_status tsp_batch_info(tsp_batch batch, int64_t* total_rays, int64_t* total_voxels, int* block_threads);
+void tsp_batch_destroy(tsp_batch batch);
 
 /*
  * tsp_device_status - synchronises `stream`, then reads and clears the device

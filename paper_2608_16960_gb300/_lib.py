@@ -27,6 +27,10 @@ class TspError(RuntimeError):
         self.status = status
 
 
+class tsp_batch_item(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_void_p), ("geom", ctypes.c_void_p), ("y", ctypes.c_void_p), ("x", ctypes.c_void_p)]
+
+
 class tsp_launch(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int), ("warp_tile_w", ctypes.c_int), ("scatter", ctypes.c_int)]
 
@@ -57,6 +61,16 @@ SIGNATURES = {
     "tsp_sirt_workspace_bytes": (_I, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "tsp_sirt": (_I, [_P, _P, _P, _P, _I, _I, _P, ctypes.c_size_t, _LP, _P]),
     "tsp_sirt_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _P]),
+    "tsp_autotune": (_I, [_P, _P, _LP, _LP, _P]),
+    "tsp_autotune_lookup": (_I, [_P, _P, _LP, _LP]),
+    "tsp_autotune_clear": (None, []),
+    "tsp_batch_create": (_I, [ctypes.POINTER(tsp_batch_item), _I, ctypes.POINTER(_P)]),
+    "tsp_batch_workspace_bytes": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    "tsp_batch_sirt": (_I, [_P, _I, _I, _P, ctypes.c_size_t, _P]),
+    "tsp_batch_sirt_capture": (_I, [_P, _I, _I, _P, ctypes.c_size_t]),
+    "tsp_batch_sirt_launch": (_I, [_P, _P]),
+    "tsp_batch_info": (_I, [_P, _I64P, _I64P, _IP]),
+    "tsp_batch_destroy": (None, [_P]),
     "tsp_device_status": (_I, [_P, _IP]),
     "tsp_last_error": (ctypes.c_char_p, []),
     "tsp_version": (_I, []),

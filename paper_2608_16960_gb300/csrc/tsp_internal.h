@@ -64,9 +64,14 @@ tsp_status check_device(int device);
 void build_grid_table(const double* r_edges, int n_r_edges, const double* theta_edges, int n_theta_edges,
                       const double* phi_edges, int n_phi_edges, std::vector<float>* table, tsp_grid_s* g);
 
+// Autotuner cache lookup (tsp_autotune.cu).
+bool tuned_launch(const tsp_grid_s* grid, const tsp_geom_s* geom, tsp_launch* fwd, tsp_launch* adj);
+
 // SIRT enqueue shared by the single and batched entry points (tsp_sirt.cu).
+// lf drives the gathering traversals, la the scattering ones (its scatter
+// field picks the strategy).
 tsp_status sirt_enqueue(tsp_grid grid, tsp_geom geom, const float* y, float* x, int n_iter, int flags, void* ws,
-                        const tsp_launch& l, cudaStream_t st);
+                        const tsp_launch& lf, const tsp_launch& la, cudaStream_t st);
 size_t sirt_workspace_bytes(const tsp_grid_s* grid, const tsp_geom_s* geom);
 
 // Readers of the per-translation-unit device error words (tsp_core.cu).

@@ -11,6 +11,9 @@
 // all of them see bit-identical segments (same code, -fmad=false).
 #pragma once
 
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
+
 #include "tsp_internal.h"
 
 // Device error word of this translation unit (device variables are not shared
@@ -230,5 +233,34 @@ struct ScatterOp {
   }
   __device__ __forceinline__ void end(int64_t) {}
 };
+
+// Warp-aggregated scatter: lanes of a warp that hit the same voxel in the same
+// step combine their contributions and issue one atomic add.
+template <int NB>
+struct AggScatterOp : ScatterOp<NB> {
+  __device__ __forceinline__ void operator()(int v, float dl) {
+    cooperative_groups::coalesced_group act = cooperative_groups::coalesced_threads();
+    cooperative_groups::coalesced_group grp = cooperative_groups::labeled_partition(act, v);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (b < this->nb) {
+        const float s = cooperative_groups::reduce(grp, __fmul_rn(this->w[b], dl), cooperative_groups::plus<float>());
+        if (grp.thread_rank() == 0) atomicAdd(this->g + b * this->V + v, s);
+      }
+    }
+  }
+  __device__ __forceinline__ bool begin(int64_t ray) {
+    ScatterOp<NB>::begin(ray);
+    return true;  // every lane takes part in the warp-level combine
+  }
+};
+
+// Launch knobs for a call without explicit ones: the autotuner's choice for
+// this size class if it has one, else the defaults.
+inline tsp_launch preferred_launch(const tsp_grid_s* grid, const tsp_geom_s* geom, bool adjoint) {
+  tsp_launch f, a;
+  if (tuned_launch(grid, geom, &f, &a)) return adjoint ? a : f;
+  return default_launch();
+}
 
 }  // namespace tsp

@@ -62,6 +62,6 @@ extern "C" tsp_status tsp_sirt_noalloc(tsp_grid grid, tsp_geom geom, const float
   void* ws = nullptr;
   st = scratch_for_current_device(&ws);
   if (st != TSP_OK) return st;
-  return tsp::sirt_enqueue(grid, geom, y, x, n_iter, flags, ws, tsp::default_launch(),
+  return tsp::sirt_enqueue(grid, geom, y, x, n_iter, flags, ws, tsp::default_launch(), tsp::default_launch(),
                            static_cast<cudaStream_t>(stream));
 }

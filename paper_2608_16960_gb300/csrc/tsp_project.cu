@@ -6,36 +6,10 @@
 //
 // Built with -fmad=false and explicit fmaf/__f*_rn in the traversal, so the
 // forward and adjoint kernels compute bit-identical segments.
-#include <cooperative_groups.h>
-#include <cooperative_groups/reduce.h>
-
 #include "tsp_kernels.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace tsp {
 namespace {
-
-// Warp-aggregated scatter: lanes of a warp that hit the same voxel in the same
-// step combine their contributions and issue one atomic add.
-template <int NB>
-struct AggScatterOp : ScatterOp<NB> {
-  __device__ __forceinline__ void operator()(int v, float dl) {
-    cg::coalesced_group act = cg::coalesced_threads();
-    cg::coalesced_group grp = cg::labeled_partition(act, v);
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      if (b < this->nb) {
-        const float s = cg::reduce(grp, __fmul_rn(this->w[b], dl), cg::plus<float>());
-        if (grp.thread_rank() == 0) atomicAdd(this->g + b * this->V + v, s);
-      }
-    }
-  }
-  __device__ __forceinline__ bool begin(int64_t ray) {
-    ScatterOp<NB>::begin(ray);
-    return true;  // every lane takes part in the warp-level combine
-  }
-};
 
 struct CountOp {
   int* __restrict__ counts;
@@ -81,7 +55,7 @@ extern "C" tsp_status tsp_forward_ex(tsp_grid grid, tsp_geom geom, const float* 
                                      const tsp_launch* launch, void* stream) {
   tsp_status st = check_trace_args(grid, geom, rho, y, batch, launch, "tsp_forward");
   if (st != TSP_OK) return st;
-  const tsp_launch l = launch ? *launch : default_launch();
+  const tsp_launch l = launch ? *launch : preferred_launch(grid, geom, false);
   const int64_t V = grid->voxels();
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   for (int b0 = 0; b0 < batch; b0 += 8) {
@@ -106,7 +80,7 @@ extern "C" tsp_status tsp_adjoint_ex(tsp_grid grid, tsp_geom geom, const float* 
                                      int accumulate, const tsp_launch* launch, void* stream) {
   tsp_status st = check_trace_args(grid, geom, y, rho, batch, launch, "tsp_adjoint");
   if (st != TSP_OK) return st;
-  const tsp_launch l = launch ? *launch : default_launch();
+  const tsp_launch l = launch ? *launch : preferred_launch(grid, geom, true);
   const int64_t V = grid->voxels();
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   if (!accumulate) TSP_CUDA(cudaMemsetAsync(rho, 0, sizeof(float) * size_t(V) * batch, cs));

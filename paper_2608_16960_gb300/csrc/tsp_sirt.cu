@@ -99,18 +99,18 @@ Workspace carve(void* ws, const tsp_grid_s* grid, const tsp_geom_s* geom) {
 // Enqueue SIRT on `st`. Shared by the public entry points; the workspace must
 // hold workspace_bytes(grid, geom) bytes, 256-byte aligned.
 tsp_status sirt_enqueue(tsp_grid grid, tsp_geom geom, const float* y, float* x, int n_iter, int flags, void* ws,
-                        const tsp_launch& l, cudaStream_t st) {
+                        const tsp_launch& lf, const tsp_launch& la, cudaStream_t st) {
   const Workspace w = carve(ws, grid, geom);
   const int64_t V = grid->voxels();
   const int nonneg = flags & TSP_SIRT_NONNEG;
   if (!(flags & TSP_SIRT_REUSE_WEIGHTS)) {
     PathLenOp lop;
     lop.R = w.R;
-    launch_trace(grid, geom, l, lop, st);
+    launch_trace(grid, geom, lf, lop, st);
     TSP_CUDA(cudaMemsetAsync(w.C, 0, sizeof(float) * size_t(V), st));
     UnitScatterOp uop;
     uop.c = w.C;
-    launch_trace(grid, geom, l, uop, st);
+    launch_trace(grid, geom, la, uop, st);
     reciprocal_kernel<<<elementwise_blocks(V), 256, 0, st>>>(w.C, V);
   }
   TSP_CUDA(cudaMemsetAsync(w.g, 0, sizeof(float) * size_t(V), st));
@@ -120,14 +120,24 @@ tsp_status sirt_enqueue(tsp_grid grid, tsp_geom geom, const float* y, float* x, 
     rop.y = y;
     rop.R = w.R;
     rop.r = w.r;
-    launch_trace(grid, geom, l, rop, st);
-    ScatterOp<1> sop;
-    sop.y = w.r;
-    sop.g = w.g;
-    sop.V = V;
-    sop.n_rays = geom->n_rays;
-    sop.nb = 1;
-    launch_trace(grid, geom, l, sop, st);
+    launch_trace(grid, geom, lf, rop, st);
+    if (la.scatter == 1) {
+      AggScatterOp<1> sop;
+      sop.y = w.r;
+      sop.g = w.g;
+      sop.V = V;
+      sop.n_rays = geom->n_rays;
+      sop.nb = 1;
+      launch_trace(grid, geom, la, sop, st);
+    } else {
+      ScatterOp<1> sop;
+      sop.y = w.r;
+      sop.g = w.g;
+      sop.V = V;
+      sop.n_rays = geom->n_rays;
+      sop.nb = 1;
+      launch_trace(grid, geom, la, sop, st);
+    }
     update_kernel<<<elementwise_blocks(V), 256, 0, st>>>(x, w.g, w.C, V, nonneg);
   }
   TSP_CUDA(cudaGetLastError());
@@ -157,6 +167,7 @@ extern "C" tsp_status tsp_sirt(tsp_grid grid, tsp_geom geom, const float* y, flo
   if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(TSP_EINVAL, "tsp_sirt: workspace not 256-byte aligned");
   if (workspace_bytes_given < workspace_bytes(grid, geom))
     return fail(TSP_EINVAL, "tsp_sirt: workspace smaller than tsp_sirt_workspace_bytes()");
-  const tsp_launch l = launch ? *launch : default_launch();
-  return sirt_enqueue(grid, geom, y, x, n_iter, flags, workspace, l, static_cast<cudaStream_t>(stream));
+  const tsp_launch lf = launch ? *launch : preferred_launch(grid, geom, false);
+  const tsp_launch la = launch ? *launch : preferred_launch(grid, geom, true);
+  return sirt_enqueue(grid, geom, y, x, n_iter, flags, workspace, lf, la, static_cast<cudaStream_t>(stream));
 }

@@ -215,6 +215,7 @@ struct RayState {
   float tth;
   // azimuth
   int sec, sec_next;
+  int ia;        // azimuth voxel index of sector sec (-1 outside a wedge)
   int ph_mode;   // 0 walk, 1 no crossings, 2 one jump pending (line meets the z axis)
   float mz;
   float tph;
@@ -249,6 +250,12 @@ TSP_HD void radial_next(const TGrid& G, RayState& s) {
 // W = sqrt(b2 sin^2 theta_k - m_z^2) = sqrt(|m_xy|^2 sin^2 - m_z^2 cos^2) with
 // m = q x n, the difference taken in float-float (it cancels at tangency).
 TSP_HD float cone_w(const TGrid& G, const RayState& s, int k) {
+  // Far from tangency (the difference keeps at least a quarter of its terms'
+  // magnitude) float32 already gives W to about an ulp.
+  const float a0 = T_MUL(s.mxy2.hi, G.S2[k]);
+  const float b0 = T_MUL(s.mz2.hi, G.K2[k]);
+  const float w2f = T_SUB(a0, b0);
+  if (w2f >= T_MUL(0.25f, T_ADD(a0, b0))) return T_SQRT(w2f);
   const ff a = ff_mul(s.mxy2, ff{G.S2[k], G.S2L[k]});
   const ff b = ff_mul(s.mz2, ff{G.K2[k], G.K2L[k]});
   const float w2 = T_ADD(T_SUB(a.hi, b.hi), T_SUB(a.lo, b.lo));
@@ -432,13 +439,13 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d[3], Op& op) {
     s.tph = fmaxf(s.tph, tcur);
   }
 
+  s.ia = G.SEC[s.sec];
   const int cap = 2 * (G.Nr + G.Ne + 2) + G.M + 8;
 #pragma unroll 1
   for (int it = 0; it < cap; ++it) {
     const float tn = fminf(s.tr, fminf(s.tth, s.tph));
-    const int ia = G.SEC[s.sec];
-    if ((unsigned)s.ir < (unsigned)G.Nr && (unsigned)s.ie < (unsigned)G.Ne && ia >= 0) {
-      op((s.ir * G.Ne + s.ie) * G.Na + ia, T_SUB(tn, tcur));
+    if ((unsigned)s.ir < (unsigned)G.Nr && (unsigned)s.ie < (unsigned)G.Ne && s.ia >= 0) {
+      op((s.ir * G.Ne + s.ie) * G.Na + s.ia, T_SUB(tn, tcur));
     }
     tcur = tn;
     if (s.tr <= s.tth && s.tr <= s.tph) {
@@ -453,6 +460,7 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d[3], Op& op) {
       s.tth = fmaxf(s.tth, tcur);
     } else {
       s.sec = s.sec_next;
+      s.ia = G.SEC[s.sec];
       if (s.ph_mode == 2) s.ph_mode = 1;
       phi_next(G, s);
       s.tph = fmaxf(s.tph, tcur);

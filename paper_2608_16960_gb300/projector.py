@@ -220,6 +220,21 @@ def tsp_sirt(grid: Grid, geom: Geometry, y: torch.Tensor, x: torch.Tensor, n_ite
     return x
 
 
+def tsp_autotune(grid: Grid, geom: Geometry):
+    """Time candidate launch knobs for this size class and cache the fastest.
+    Returns ((block, tile, scatter) forward, (block, tile, scatter) adjoint)."""
+    L = _lib.load()
+    f, a = tsp_launch(), tsp_launch()
+    check(L.tsp_autotune(grid.handle, geom.handle, ctypes.byref(f), ctypes.byref(a),
+                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)), "tsp_autotune")
+    as_t = lambda l: (l.block_threads, l.warp_tile_w, l.scatter)
+    return as_t(f), as_t(a)
+
+
+def tsp_autotune_clear():
+    _lib.load().tsp_autotune_clear()
+
+
 def tsp_count_segments(grid: Grid, geom: Geometry) -> torch.Tensor:
     """Valid segments per ray (int32, det_shape)."""
     L = _lib.load()
@@ -264,3 +279,62 @@ class Operator:
 
     def T(self, y: torch.Tensor) -> torch.Tensor:
         return tsp_adjoint(self.grid, self.geom, y, launch=self.launch)
+
+
+class Batch:
+    """Batched SIRT over independent (grid, geometry, y, x) items of uneven
+    sizes: persistent per-stage launches, optionally one captured CUDA graph."""
+
+    def __init__(self, items):
+        L = _lib.load()
+        self._items = list(items)  # keep handles and tensors alive
+        arr = (_lib.tsp_batch_item * len(self._items))()
+        for i, (grid, geom, y, x) in enumerate(self._items):
+            _require_cuda(y, "y")
+            _require_cuda(x, "x")
+            if y.numel() != geom.n_rays or x.numel() != grid.voxels:
+                raise ValueError(f"item {i}: y or x has the wrong size")
+            arr[i] = _lib.tsp_batch_item(grid.handle.value, geom.handle.value, y.data_ptr(), x.data_ptr())
+        h = ctypes.c_void_p()
+        check(L.tsp_batch_create(arr, len(self._items), ctypes.byref(h)), "tsp_batch_create")
+        self.handle = h
+        self.device = torch.cuda.current_device()
+        self._ws = None
+
+    def info(self):
+        L = _lib.load()
+        r, v, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        check(L.tsp_batch_info(self.handle, ctypes.byref(r), ctypes.byref(v), ctypes.byref(b)), "tsp_batch_info")
+        return r.value, v.value, b.value
+
+    def workspace(self, n_iter):
+        L = _lib.load()
+        n = ctypes.c_size_t()
+        check(L.tsp_batch_workspace_bytes(self.handle, n_iter, ctypes.byref(n)), "tsp_batch_workspace_bytes")
+        if self._ws is None or self._ws.numel() < n.value:
+            self._ws = torch.empty(n.value, dtype=torch.uint8, device=torch.device("cuda", self.device))
+        return self._ws
+
+    def sirt(self, n_iter, nonneg=False):
+        ws = self.workspace(n_iter)
+        check(_lib.load().tsp_batch_sirt(self.handle, n_iter, _lib.TSP_SIRT_NONNEG if nonneg else 0,
+                                         ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)), "tsp_batch_sirt")
+
+    def capture(self, n_iter, nonneg=False):
+        ws = self.workspace(n_iter)
+        check(_lib.load().tsp_batch_sirt_capture(self.handle, n_iter, _lib.TSP_SIRT_NONNEG if nonneg else 0,
+                                                 ctypes.c_void_p(ws.data_ptr()), ws.numel()), "tsp_batch_sirt_capture")
+
+    def launch(self):
+        check(_lib.load().tsp_batch_sirt_launch(self.handle, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+              "tsp_batch_sirt_launch")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _lib.load(build_if_missing=False).tsp_batch_destroy(h)
+            except Exception:
+                pass
+            self.handle = None

@@ -70,3 +70,27 @@ def table3(row: int) -> Workload:
     rho = synth.blob_phantom(e, seed=10 + row)
     pos = synth.circular_orbit(nv, 60.0)
     return Workload(f"table3_{row}", e, rho, [ViewSet("cone", pos, (det, det), 30.0)])
+
+
+@dataclass
+class Instance:
+    edges: synth.GridEdges
+    rho: np.ndarray
+    view: ViewSet
+
+
+def batched(n: int = 64, seed: int = 6, fov_deg: float = 50.0):
+    """Uneven independent reconstructions: N_r in 20-120, N_e in 20-90, N_a in
+    40-180, 4-96 cone views of 64^2-512^2 on orbits of radius 60 at seeded
+    inclinations, seeded blob densities."""
+    rng = synth.SplitMix64(seed)
+    nr, ne, na = rng.integers(20, 120, n), rng.integers(20, 90, n), rng.integers(40, 180, n)
+    nv, det = rng.integers(4, 96, n), rng.integers(64, 512, n)
+    incl = rng.uniform(n, 0.0, 60.0)
+    out = []
+    for i in range(n):
+        e = synth.grid_edges(int(nr[i]), int(ne[i]), int(na[i]))
+        rho = synth.blob_phantom(e, seed=10_000 + i)
+        pos = synth.circular_orbit(int(nv[i]), 60.0, incline_deg=float(incl[i]), phase=0.1 * i)
+        out.append(Instance(e, rho, ViewSet("cone", pos, (int(det[i]), int(det[i])), fov_deg)))
+    return out
