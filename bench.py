@@ -48,10 +48,12 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["paper_scale", "batched"], default="paper_scale",
+    ap.add_argument("--workload", choices=["paper_scale", "batched", "differentiation"], default="paper_scale",
                     help="batched: 64 uneven SIRT reconstructions in one captured graph (not the headline metric)")
     ap.add_argument("--iters", type=int, default=50, help="SIRT iterations of the batched workload")
     ap.add_argument("--autotune", action="store_true", help="autotune launch knobs before timing")
+    ap.add_argument("--adam-steps", type=int, default=500, help="Adam steps of the differentiation workload")
+    ap.add_argument("--lr", type=float, default=1e-2, help="Adam learning rate of the differentiation workload")
     return ap.parse_args()
 
 
@@ -402,12 +404,75 @@ def run_batched(args):
     print(json.dumps(out), flush=True)
 
 
+def run_differentiation(args):
+    """500 Adam steps on ||y - F M(c)||^2 with M the SH x B-spline model; one step =
+    render, forward, loss, adjoint, render adjoint, Adam (all library kernels)."""
+    import torch
+
+    from paper_2608_16960_gb300 import synth, workloads
+    from paper_2608_16960_gb300.model import Adam, SHBSpline, squared_error
+    from paper_2608_16960_gb300.projector import Geometry, Grid, Operator, tsp_autotune
+
+    torch.cuda.set_device(0)
+    w = workloads.differentiation()
+    grid = Grid.from_edges(w.edges)
+    geom = Geometry.cone(w.view.pos, w.view.shape, w.view.fov_deg)
+    tuned = tsp_autotune(grid, geom)
+    model = SHBSpline(w.edges, w.n_basis, w.L)
+    op = Operator(grid, geom)
+    with torch.no_grad():
+        y_clean = op(model.render(torch.tensor(w.coeffs, device="cuda")))
+        sigma = w.noise_frac * float(y_clean.max())
+        noise = torch.tensor(synth.SplitMix64(w.noise_seed).normal(geom.n_rays).reshape(geom.det_shape) * sigma,
+                             device="cuda", dtype=torch.float32)
+        y = y_clean + noise
+    c = torch.zeros_like(torch.tensor(w.coeffs, device="cuda")).requires_grad_(True)
+    opt = Adam([c], lr=args.lr)
+
+    def step():
+        opt.zero_grad()
+        loss = squared_error(op(model.render(c)), y)
+        loss.backward()
+        opt.step()
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    with torch.no_grad():
+        c.zero_()
+    opt = Adam([c], lr=args.lr)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    first = None
+    e0.record()
+    for i in range(args.adam_steps):
+        loss = step()
+        if i == 0:
+            first = loss.detach().clone()
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    ct = torch.tensor(w.coeffs, device="cuda")
+    rel = float(torch.linalg.norm(c.detach() - ct) / torch.linalg.norm(ct))
+    noise_floor = float((noise.double() ** 2).sum())
+    out = {"metric": "differentiable reconstruction Adam steps/s", "value": args.adam_steps / t, "unit": "steps/s",
+           "ms_per_step": 1e3 * t / args.adam_steps, "steps": args.adam_steps, "dtype": "f32", "data": "synthetic",
+           "rays_per_s_fwd_adj": geom.n_rays * args.adam_steps / t,
+           "config": {"workload": "SH L<=8 x 20 B-splines on 128x64x128, 64 cone views 512^2, 1% noise",
+                      "lr": args.lr, "launch_fwd_adj": tuned},
+           "loss_first": float(first), "loss_last": float(loss), "noise_energy": noise_floor,
+           "coeff_rel_error": rel}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "differentiation":
+        run_differentiation(args)
     else:
         run_ours(args)
 

@@ -224,6 +224,43 @@ tsp_status tsp_batch_info(tsp_batch batch, int64_t* total_rays, int64_t* total_v
 void tsp_batch_destroy(tsp_batch batch);
 
 /*
+ * Parametric density model for reconstructions that differentiate through F
+ * (Sec. 4.5 Eq. 7 and Listing 8; Sec. 6 Eq. 10 uses spherical harmonics per
+ * shell): rho[ir][ie][ia] = sum_j sum_q B[ir][j] c[j][q] Y[ie,ia][q] with B the
+ * n_basis_r clamped cubic B-splines on [r_min, r_max] (uniform interior knots)
+ * and Y the real orthonormal spherical harmonics of degree <= L, q = l^2+l+m.
+ * Bases are evaluated on the host (double) at the given voxel-centre
+ * coordinates (host arrays) and kept on the device as float32 tables.
+ * coeffs / grad_coeffs: device float32 [n_basis_r][(L+1)^2]; rho / grad_rho:
+ * device float32 (N_r, N_e, N_a). The handle owns a small scratch buffer, so
+ * render calls on one handle must not overlap on the GPU.
+ * tsp_shbs_tables copies the float32 tables to host arrays (either may be
+ * NULL): B [N_r][n_basis_r], Yt [(L+1)^2][N_e*N_a].
+ */
+typedef struct tsp_shbs_s* tsp_shbs;
+tsp_status tsp_shbs_create(int n_basis_r, int L, const double* r_centres, int n_r, const double* theta_centres,
+                           int n_e, const double* phi_centres, int n_a, double r_min, double r_max, tsp_shbs* out);
+tsp_status tsp_shbs_tables(tsp_shbs model, float* B, float* Yt);
+tsp_status tsp_shbs_render(tsp_shbs model, const float* coeffs, float* rho, void* stream);
+tsp_status tsp_shbs_render_adjoint(tsp_shbs model, const float* grad_rho, float* grad_coeffs, void* stream);
+void tsp_shbs_destroy(tsp_shbs model);
+
+/*
+ * tsp_adam - one Adam step (Kingma and Ba 2015) on n float32 device values:
+ * g' = g + weight_decay * p; m = b1 m + (1-b1) g'; v = b2 v + (1-b2) g'^2;
+ * p -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). step >= 1.
+ */
+tsp_status tsp_adam(float* params, const float* grads, float* m, float* v, int64_t n, float lr, float beta1,
+                    float beta2, float eps, float weight_decay, int step, void* stream);
+
+/*
+ * tsp_sq_residual - squared-error loss of Eq. 6: loss += sum (yhat - y)^2
+ * (device double, accumulated: zero it first) and, if grad != NULL,
+ * grad = 2 (yhat - y) (device float32, n values).
+ */
+tsp_status tsp_sq_residual(const float* yhat, const float* y, int64_t n, float* grad, double* loss, void* stream);
+
+/*
  * tsp_device_status - synchronises `stream`, then reads and clears the device
  * error word (0 = no kernel reported an inconsistency).
  */

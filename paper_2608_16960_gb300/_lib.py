@@ -71,6 +71,14 @@ SIGNATURES = {
     "tsp_batch_sirt_launch": (_I, [_P, _P]),
     "tsp_batch_info": (_I, [_P, _I64P, _I64P, _IP]),
     "tsp_batch_destroy": (None, [_P]),
+    "tsp_shbs_create": (_I, [_I, _I, _DP, _I, _DP, _I, _DP, _I, _D, _D, ctypes.POINTER(_P)]),
+    "tsp_shbs_tables": (_I, [_P, _P, _P]),
+    "tsp_shbs_render": (_I, [_P, _P, _P, _P]),
+    "tsp_shbs_render_adjoint": (_I, [_P, _P, _P, _P]),
+    "tsp_shbs_destroy": (None, [_P]),
+    "tsp_adam": (_I, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                      ctypes.c_float, _I, _P]),
+    "tsp_sq_residual": (_I, [_P, _P, _I64, _P, _P, _P]),
     "tsp_device_status": (_I, [_P, _IP]),
     "tsp_last_error": (ctypes.c_char_p, []),
     "tsp_version": (_I, []),

@@ -1,0 +1,133 @@
+"""Parametric density model and optimisation pieces for reconstructions that
+differentiate through the projector (Sec. 4.5 Eq. 6-7, Listing 7-8; Sec. 6).
+
+SHBSpline: rho = B(r) c Y(theta, phi)^T with radial cubic B-splines and real
+spherical harmonics, rendered and back-propagated by library kernels
+(tsp_shbs_*). SquaredError: sum (yhat - y)^2 with its gradient from
+tsp_sq_residual. Adam: tsp_adam. Torch only chains them (autograd plumbing)
+and holds the memory.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+from .projector import _require_cuda, _stream
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class SHBSpline:
+    """n_basis_r radial cubic B-splines x real spherical harmonics of degree <= L
+    on a grid's voxel centres (arithmetic midpoints of the edges)."""
+
+    def __init__(self, edges, n_basis_r: int = 20, L: int = 8):
+        L_ = _lib.load()
+        rc = np.ascontiguousarray(0.5 * (edges.r[:-1] + edges.r[1:]), dtype=np.float64)
+        tc = np.ascontiguousarray(0.5 * (edges.theta[:-1] + edges.theta[1:]), dtype=np.float64)
+        pc = np.ascontiguousarray(0.5 * (edges.phi[:-1] + edges.phi[1:]), dtype=np.float64)
+        h = ctypes.c_void_p()
+        check(L_.tsp_shbs_create(n_basis_r, L, _dp(rc), len(rc), _dp(tc), len(tc), _dp(pc), len(pc),
+                                 float(edges.r[0]), float(edges.r[-1]), ctypes.byref(h)), "tsp_shbs_create")
+        self.handle = h
+        self.n_basis_r, self.L = n_basis_r, L
+        self.nq = (L + 1) ** 2
+        self.shape = (len(rc), len(tc), len(pc))
+        self.coeff_shape = (n_basis_r, self.nq)
+
+    def tables(self):
+        B = np.zeros((self.shape[0], self.n_basis_r), np.float32)
+        Yt = np.zeros((self.nq, self.shape[1] * self.shape[2]), np.float32)
+        check(_lib.load().tsp_shbs_tables(self.handle, ctypes.c_void_p(B.ctypes.data), ctypes.c_void_p(Yt.ctypes.data)),
+              "tsp_shbs_tables")
+        return B, Yt
+
+    def render(self, coeffs: torch.Tensor) -> torch.Tensor:
+        return ShbsRenderFn.apply(coeffs, self)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _lib.load(build_if_missing=False).tsp_shbs_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+class ShbsRenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, coeffs, model):
+        _require_cuda(coeffs, "coeffs")
+        if tuple(coeffs.shape) != model.coeff_shape:
+            raise ValueError(f"coeffs must have shape {model.coeff_shape}")
+        ctx.model = model
+        rho = torch.empty(model.shape, device=coeffs.device)
+        check(_lib.load().tsp_shbs_render(model.handle, ctypes.c_void_p(coeffs.data_ptr()),
+                                          ctypes.c_void_p(rho.data_ptr()), _stream(coeffs)), "tsp_shbs_render")
+        return rho
+
+    @staticmethod
+    def backward(ctx, g):
+        g = g.contiguous()
+        gc = torch.empty(ctx.model.coeff_shape, device=g.device)
+        check(_lib.load().tsp_shbs_render_adjoint(ctx.model.handle, ctypes.c_void_p(g.data_ptr()),
+                                                  ctypes.c_void_p(gc.data_ptr()), _stream(g)), "tsp_shbs_render_adjoint")
+        return gc, None
+
+
+class SquaredErrorFn(torch.autograd.Function):
+    """sum (yhat - y)^2 (Eq. 6) with the gradient 2 (yhat - y) from one kernel."""
+
+    @staticmethod
+    def forward(ctx, yhat, y):
+        yhat, y = yhat.contiguous(), y.contiguous()
+        _require_cuda(yhat, "yhat")
+        grad = torch.empty_like(yhat)
+        loss = torch.zeros((), dtype=torch.float64, device=yhat.device)
+        check(_lib.load().tsp_sq_residual(ctypes.c_void_p(yhat.data_ptr()), ctypes.c_void_p(y.data_ptr()), yhat.numel(),
+                                          ctypes.c_void_p(grad.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                                          _stream(yhat)), "tsp_sq_residual")
+        ctx.save_for_backward(grad)
+        return loss
+
+    @staticmethod
+    def backward(ctx, gl):
+        (grad,) = ctx.saved_tensors
+        return grad * gl.to(grad.dtype), None
+
+
+def squared_error(yhat, y):
+    return SquaredErrorFn.apply(yhat, y)
+
+
+class Adam:
+    """Adam over a list of float32 CUDA parameters, stepped by tsp_adam."""
+
+    def __init__(self, params, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, weight_decay=0.0):
+        self.params = list(params)
+        self.lr, self.betas, self.eps, self.wd = lr, betas, eps, weight_decay
+        self.m = [torch.zeros_like(p) for p in self.params]
+        self.v = [torch.zeros_like(p) for p in self.params]
+        self.t = 0
+
+    def zero_grad(self):
+        for p in self.params:
+            p.grad = None
+
+    def step(self):
+        self.t += 1
+        L = _lib.load()
+        for p, m, v in zip(self.params, self.m, self.v):
+            if p.grad is None:
+                continue
+            g = p.grad.contiguous()
+            check(L.tsp_adam(ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(m.data_ptr()),
+                             ctypes.c_void_p(v.data_ptr()), p.numel(), self.lr, self.betas[0], self.betas[1], self.eps,
+                             self.wd, self.t, _stream(p)), "tsp_adam")

@@ -94,3 +94,35 @@ def batched(n: int = 64, seed: int = 6, fov_deg: float = 50.0):
         pos = synth.circular_orbit(int(nv[i]), 60.0, incline_deg=float(incl[i]), phase=0.1 * i)
         out.append(Instance(e, rho, ViewSet("cone", pos, (int(det[i]), int(det[i])), fov_deg)))
     return out
+
+
+@dataclass
+class Differentiation:
+    edges: synth.GridEdges
+    view: ViewSet
+    n_basis: int
+    L: int
+    coeffs: np.ndarray     # true model coefficients (n_basis, (L+1)^2)
+    noise_seed: int
+    noise_frac: float
+
+
+def differentiation(shape=(128, 64, 128), n_views=64, det=512, n_basis=20, L=8) -> Differentiation:
+    """SH (L <= 8) x 20 radial cubic B-splines rendered on a 128 x 64 x 128 grid;
+    64 cone views of 512^2 (50 deg) from an orbit of radius 60 inclined 30 deg;
+    Gaussian noise of 1% of the peak. True coefficients: an exp(-r/4) radial
+    profile in the l = 0 term (its B-spline coefficients at the knot averages),
+    seeded higher-degree terms of 20% relative size, decaying with l."""
+    e = synth.grid_edges(*shape)
+    rng = synth.SplitMix64(4)
+    nq = (L + 1) ** 2
+    k = 3
+    n_int = n_basis - k - 1
+    knots = np.concatenate([[3.0] * (k + 1), 3.0 + 22.0 * np.arange(1, n_int + 1) / (n_int + 1), [25.0] * (k + 1)])
+    greville = np.array([knots[j + 1:j + k + 1].mean() for j in range(n_basis)])
+    c = np.zeros((n_basis, nq))
+    c[:, 0] = np.exp(-greville / 4.0) * 2.0 * np.sqrt(np.pi)
+    ell = np.floor(np.sqrt(np.arange(nq))).astype(int)
+    c[:, 1:] = 0.2 * c[:, :1] * rng.normal(n_basis * (nq - 1)).reshape(n_basis, nq - 1) / (ell[1:] + 1.0)
+    pos = synth.circular_orbit(n_views, 60.0, incline_deg=30.0, phase=float(synth.SplitMix64(5).uniform(1)[0]))
+    return Differentiation(e, ViewSet("cone", pos, (det, det), 50.0), n_basis, L, c.astype(np.float32), 44, 0.01)
