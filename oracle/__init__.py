@@ -66,6 +66,9 @@ def lib():
                 L.oracle_conv3d_fwd.argtypes = conv + [fp, fp, fp, dp]
                 L.oracle_conv3d_dgrad.argtypes = conv + [fp, fp, dp]
                 L.oracle_conv3d_wgrad.argtypes = conv + [fp, fp, dp, dp]
+                L.oracle_conv3d_fwd_f64.argtypes = conv + [dp, dp, dp, dp]
+                L.oracle_conv3d_dgrad_f64.argtypes = conv + [dp, dp, dp]
+                L.oracle_conv3d_wgrad_f64.argtypes = conv + [dp, dp, dp, dp]
             _lib = L
     return _lib
 
