@@ -261,6 +261,41 @@ tsp_status tsp_adam(float* params, const float* grads, float* m, float* v, int64
 tsp_status tsp_sq_residual(const float* yhat, const float* y, int64_t n, float* grad, double* loss, void* stream);
 
 /*
+ * Learned warm start: a residual 3D convolutional network on the spherical grid
+ * (3x3x3 kernels; zero padding in r and theta, periodic in phi):
+ *   h1 = relu(conv(a; w1) + b1)                  1 -> 32 channels
+ *   h_k = h_{k-1} + relu(conv(h_{k-1}; wk) + bk)  32 -> 32, k = 2..5 (tensor cores)
+ *   out = a + conv(h5; w6) + b6                  32 -> 1
+ * bfloat16 weights and activations, float32 accumulation, float32 master
+ * weights updated by Adam. (The paper has no network; it names learned and
+ * physics-informed uses of the differentiable operator, Sec. 4.5.)
+ * Parameters (float32, flat): w1 [27][32][1], b1 [32], w2..w5 [27][32][32],
+ * b2..b5 [32], w6 [27][1][32], b6 [1]; tap = (dr+1)*9 + (de+1)*3 + (da+1).
+ * Volumes a, target, out: device float32 [batch][N_r][N_e][N_a].
+ * tsp_net_create allocates the parameters, Adam moments and the activations
+ * of max_batch samples (about 224 bytes per voxel and sample); N_a must be a
+ * multiple of 32 in [32, 192]. Calls on one net must not overlap on the GPU.
+ *   tsp_net_forward   - out = net(a).
+ *   tsp_net_loss_grad - mean squared error against target and its gradient
+ *                       w.r.t. every parameter (kept in the net; synchronous if
+ *                       loss != NULL, which receives the loss).
+ *   tsp_net_adam      - one Adam step of the parameters with those gradients.
+ *   tsp_net_activation- copy h_{layer+1} (bfloat16 [batch][V][32], layer 0..4)
+ *                       or out (layer 5) to a host buffer (synchronous).
+ */
+typedef struct tsp_net_s* tsp_net;
+tsp_status tsp_net_create(int n_r, int n_e, int n_a, int max_batch, tsp_net* out);
+void tsp_net_destroy(tsp_net net);
+tsp_status tsp_net_num_params(tsp_net net, size_t* count);
+tsp_status tsp_net_set_params(tsp_net net, const float* host_params, size_t count);
+tsp_status tsp_net_get_params(tsp_net net, float* host_params, size_t count);
+tsp_status tsp_net_get_grads(tsp_net net, float* host_grads, size_t count);
+tsp_status tsp_net_forward(tsp_net net, const float* a, int batch, float* out, void* stream);
+tsp_status tsp_net_loss_grad(tsp_net net, const float* a, const float* target, int batch, double* loss, void* stream);
+tsp_status tsp_net_adam(tsp_net net, float lr, float beta1, float beta2, float eps, float weight_decay, void* stream);
+tsp_status tsp_net_activation(tsp_net net, int layer, int batch, void* host);
+
+/*
  * tsp_device_status - synchronises `stream`, then reads and clears the device
  * error word (0 = no kernel reported an inconsistency).
  */

@@ -79,6 +79,16 @@ SIGNATURES = {
     "tsp_adam": (_I, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                       ctypes.c_float, _I, _P]),
     "tsp_sq_residual": (_I, [_P, _P, _I64, _P, _P, _P]),
+    "tsp_net_create": (_I, [_I, _I, _I, _I, ctypes.POINTER(_P)]),
+    "tsp_net_destroy": (None, [_P]),
+    "tsp_net_num_params": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "tsp_net_set_params": (_I, [_P, _P, ctypes.c_size_t]),
+    "tsp_net_get_params": (_I, [_P, _P, ctypes.c_size_t]),
+    "tsp_net_get_grads": (_I, [_P, _P, ctypes.c_size_t]),
+    "tsp_net_forward": (_I, [_P, _P, _I, _P, _P]),
+    "tsp_net_loss_grad": (_I, [_P, _P, _P, _I, ctypes.POINTER(ctypes.c_double), _P]),
+    "tsp_net_adam": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
+    "tsp_net_activation": (_I, [_P, _I, _I, _P]),
     "tsp_device_status": (_I, [_P, _IP]),
     "tsp_last_error": (ctypes.c_char_p, []),
     "tsp_version": (_I, []),

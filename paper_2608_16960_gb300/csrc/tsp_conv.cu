@@ -1,0 +1,849 @@
+// Learned warm start: a residual 3D convolutional network on the spherical grid
+// (3x3x3 kernels, zero padding in r and theta, periodic in phi), bfloat16
+// weights and activations, float32 accumulation, trained by its own kernels.
+//
+//   h1 = relu(conv(a; w1) + b1)                   1 -> 32   CUDA cores
+//   h_k = h_{k-1} + relu(conv(h_{k-1}; wk) + bk)  32 -> 32  tensor cores (k = 2..5)
+//   out = a + conv(h5; w6) + b6                   32 -> 1   CUDA cores
+//
+// The 32 -> 32 layers are implicit GEMMs (M = voxels, N = 32, K = 27 taps x 32)
+// on mma.sync m16n8k16 BF16 tensor cores: a CTA covers four theta-rows of one
+// shell; its shared-memory slab holds the 3 x 6 neighbouring rows with the
+// periodic phi halo, and ldmatrix takes each lane's own (shifted) voxel row, so
+// every tap is the same GEMM on a shifted view. dgrad is the same kernel with
+// the mirrored, transposed kernel; wgrad uses ldmatrix.trans on both operands.
+// Shared-memory rows (64 bytes = 32 channels) are XOR-swizzled in 16-byte
+// chunks so that eight consecutive rows hit disjoint banks.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <vector>
+
+#include "tsp_internal.h"
+
+struct tsp_net_s;
+
+namespace tsp {
+namespace {
+
+constexpr int CH = 32;
+constexpr int TR = 4;  // theta-rows per forward/dgrad CTA (one per warp pair)
+
+struct Dims {
+  int B, Nr, Ne, Na;
+  int64_t V;  // voxels per sample
+};
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ int64_t nbr(const Dims& d, int r, int e, int a, int dr, int de, int da) {
+  const int rr = r + dr, ee = e + de;
+  if (rr < 0 || rr >= d.Nr || ee < 0 || ee >= d.Ne) return -1;
+  int aa = a + da;
+  aa = aa < 0 ? aa + d.Na : (aa >= d.Na ? aa - d.Na : aa);
+  return (int64_t(rr) * d.Ne + ee) * d.Na + aa;
+}
+
+__device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t chunk) {
+  return row * 64u + ((chunk ^ ((row >> 1) & 3u)) << 4);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void mma16816(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------------------------
+// 32 -> 32 implicit GEMM: MODE 0 forward (bias, ReLU, residual, mask, bf16
+// out), MODE 1 dgrad (accumulate into float32 G).
+// ---------------------------------------------------------------------------
+template <int MODE, int MT>
+__global__ void __launch_bounds__(256) conv32_kernel(Dims d, const bf16* __restrict__ X, const bf16* __restrict__ W,
+                                                     const float* __restrict__ bias, const bf16* __restrict__ Xres,
+                                                     bf16* __restrict__ Y, uint32_t* __restrict__ mask,
+                                                     float* __restrict__ G) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int Na = d.Na, cols = Na + 2;
+  const int slab_rows = 3 * (TR + 2) * cols;
+  unsigned char* s_x = smem;
+  unsigned char* s_w = smem + size_t(slab_rows) * 64;
+  const int b = blockIdx.z, r = blockIdx.y, e0 = blockIdx.x * TR;
+  const bf16* Xb = X + size_t(b) * d.V * CH;
+
+  // weights: 27 x 32 rows of 64 bytes
+  for (int i = threadIdx.x; i < 27 * 32 * 4; i += blockDim.x) {
+    const int row = i >> 2, ch = i & 3;
+    cp_async16(s_w + swz(row, ch), W + size_t(row) * CH + ch * 8);
+  }
+  // input slab: (dr, theta row, phi with halo) x 4 chunks, zeros outside in r/theta
+  for (int i = threadIdx.x; i < slab_rows * 4; i += blockDim.x) {
+    const int cell = i >> 2, ch = i & 3;
+    const int c = cell % cols, rowj = (cell / cols) % (TR + 2), dri = cell / (cols * (TR + 2));
+    const int rr = r + dri - 1, ee = e0 + rowj - 1;
+    unsigned char* dst = s_x + swz(cell, ch);
+    if (rr < 0 || rr >= d.Nr || ee < 0 || ee >= d.Ne) {
+      *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+    } else {
+      int aa = c - 1;
+      aa = aa < 0 ? aa + Na : (aa >= Na ? aa - Na : aa);
+      const int64_t v = (int64_t(rr) * d.Ne + ee) * Na + aa;
+      cp_async16(dst, Xb + v * CH + ch * 8);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row_l = warp >> 1, half = warp & 1;
+  const int phi0 = half * (Na >> 1);
+  float acc[MT][4][4];
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.0f;
+
+  const uint32_t sx = static_cast<uint32_t>(__cvta_generic_to_shared(s_x));
+  const uint32_t sw = static_cast<uint32_t>(__cvta_generic_to_shared(s_w));
+  const int mat = lane >> 3, rr8 = lane & 7;
+#pragma unroll 1
+  for (int tap = 0; tap < 27; ++tap) {
+    const int dri = tap / 9, dei = (tap / 3) % 3, dai = tap % 3;
+    const int base_row = (dri * (TR + 2) + row_l + dei) * cols + dai;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      uint32_t bfr[4][2];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const uint32_t wrow = tap * 32 + p * 16 + rr8 + 8 * (mat >> 1);
+        uint32_t q0, q1, q2, q3;
+        ldsm_x4(sw + swz(wrow, 2 * kk + (mat & 1)), q0, q1, q2, q3);
+        bfr[2 * p][0] = q0;
+        bfr[2 * p][1] = q1;
+        bfr[2 * p + 1][0] = q2;
+        bfr[2 * p + 1][1] = q3;
+      }
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        const uint32_t arow = base_row + phi0 + mt * 16 + rr8 + 8 * (mat & 1);
+        uint32_t a[4];
+        ldsm_x4(sx + swz(arow, 2 * kk + (mat >> 1)), a[0], a[1], a[2], a[3]);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) mma16816(acc[mt][nt], a, bfr[nt][0], bfr[nt][1]);
+      }
+    }
+  }
+
+  const int e = e0 + row_l;
+  if (e >= d.Ne) return;
+  const int g = lane >> 2, t = lane & 3;
+  const size_t rowbase = ((size_t(b) * d.Nr + r) * d.Ne + e) * Na;
+#pragma unroll
+  for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const size_t vox = rowbase + phi0 + mt * 16 + g + 8 * hh;
+      uint32_t bits = 0;
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int co = nt * 8 + 2 * t;
+        const float z0 = acc[mt][nt][2 * hh], z1 = acc[mt][nt][2 * hh + 1];
+        if (MODE == 0) {
+          const float y0 = z0 + bias[co], y1 = z1 + bias[co + 1];
+          bits |= (y0 > 0.0f ? 1u : 0u) << co;
+          bits |= (y1 > 0.0f ? 1u : 0u) << (co + 1);
+          const __nv_bfloat162 xr = *reinterpret_cast<const __nv_bfloat162*>(Xres + vox * CH + co);
+          const float o0 = __bfloat162float(xr.x) + fmaxf(y0, 0.0f);
+          const float o1 = __bfloat162float(xr.y) + fmaxf(y1, 0.0f);
+          *reinterpret_cast<__nv_bfloat162*>(Y + vox * CH + co) = __floats2bfloat162_rn(o0, o1);
+        } else {
+          float2* gp = reinterpret_cast<float2*>(G + vox * CH + co);
+          float2 gv = *gp;
+          gv.x += z0;
+          gv.y += z1;
+          *gp = gv;
+        }
+      }
+      if (MODE == 0) {
+        bits |= __shfl_xor_sync(0xffffffffu, bits, 1);
+        bits |= __shfl_xor_sync(0xffffffffu, bits, 2);
+        if (t == 0) mask[vox] = bits;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 32 -> 32 weight gradient: dW[tap][co][ci] += sum_v Gz[v][co] H[v + d_tap][ci].
+// 9 warps, warp w owns taps 3w..3w+2; a CTA walks `rows` consecutive phi-rows.
+// ---------------------------------------------------------------------------
+template <int NA>
+__global__ void __launch_bounds__(288) wgrad32_kernel(Dims d, const bf16* __restrict__ Gz, const bf16* __restrict__ H,
+                                                      float* __restrict__ dW, int rows_per_cta) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int cols = NA + 2;
+  unsigned char* s_h = smem;                         // 9 rows x cols
+  unsigned char* s_g = smem + size_t(9) * cols * 64;  // NA rows
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mat = lane >> 3, rr8 = lane & 7;
+  float acc[3][2][4][4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[a][i][j][k] = 0.0f;
+  const uint32_t sh = static_cast<uint32_t>(__cvta_generic_to_shared(s_h));
+  const uint32_t sg = static_cast<uint32_t>(__cvta_generic_to_shared(s_g));
+  const int64_t total_rows = int64_t(d.B) * d.Nr * d.Ne;
+  const int64_t row0 = int64_t(blockIdx.x) * rows_per_cta;
+  for (int64_t R = row0; R < row0 + rows_per_cta && R < total_rows; ++R) {
+    const int b = int(R / (int64_t(d.Nr) * d.Ne));
+    const int r = int((R / d.Ne) % d.Nr), e = int(R % d.Ne);
+    const bf16* Hb = H + size_t(b) * d.V * CH;
+    const bf16* Gb = Gz + size_t(b) * d.V * CH;
+    __syncthreads();  // previous row's operands are no longer read
+    for (int i = threadIdx.x; i < 9 * cols * 4; i += blockDim.x) {
+      const int cell = i >> 2, ch = i & 3;
+      const int c = cell % cols, j = cell / cols;
+      const int rr = r + j / 3 - 1, ee = e + j % 3 - 1;
+      unsigned char* dst = s_h + swz(cell, ch);
+      if (rr < 0 || rr >= d.Nr || ee < 0 || ee >= d.Ne) {
+        *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+      } else {
+        int aa = c - 1;
+        aa = aa < 0 ? aa + NA : (aa >= NA ? aa - NA : aa);
+        cp_async16(dst, Hb + ((int64_t(rr) * d.Ne + ee) * NA + aa) * CH + ch * 8);
+      }
+    }
+    const int64_t gbase = (int64_t(r) * d.Ne + e) * NA;
+    for (int i = threadIdx.x; i < NA * 4; i += blockDim.x) {
+      const int v = i >> 2, ch = i & 3;
+      cp_async16(s_g + swz(v, ch), Gb + (gbase + v) * CH + ch * 8);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+#pragma unroll 1
+    for (int k0 = 0; k0 < NA; k0 += 16) {
+      // A = Gz^T (co x v): two m16 tiles (co 0-15, 16-31)
+      uint32_t a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const uint32_t v = k0 + rr8 + 8 * (mat >> 1);
+        ldsm_x4_t(sg + swz(v, 2 * mt + (mat & 1)), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+      }
+#pragma unroll
+      for (int tt = 0; tt < 3; ++tt) {
+        const int tap = warp * 3 + tt;
+        const int dri = tap / 9, dei = (tap / 3) % 3, dai = tap % 3;
+        const int hrow = (dri * 3 + dei) * cols + dai;  // slab column = phi + dai
+        uint32_t bfr[4][2];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          // B (v x ci) for n-tiles 2p, 2p+1: rows v, chunks 2p + (mat >> 1)
+          const uint32_t v = hrow + k0 + rr8 + 8 * (mat & 1);
+          uint32_t q0, q1, q2, q3;
+          ldsm_x4_t(sh + swz(v, 2 * p + (mat >> 1)), q0, q1, q2, q3);
+          bfr[2 * p][0] = q0;
+          bfr[2 * p][1] = q1;
+          bfr[2 * p + 1][0] = q2;
+          bfr[2 * p + 1][1] = q3;
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) mma16816(acc[tt][mt][nt], a[mt], bfr[nt][0], bfr[nt][1]);
+      }
+    }
+  }
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int tt = 0; tt < 3; ++tt) {
+    const int tap = warp * 3 + tt;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int co = mt * 16 + g, ci = nt * 8 + 2 * t;
+        float* base = dW + (size_t(tap) * CH + co) * CH + ci;
+        atomicAdd(base, acc[tt][mt][nt][0]);
+        atomicAdd(base + 1, acc[tt][mt][nt][1]);
+        atomicAdd(base + 8 * CH, acc[tt][mt][nt][2]);
+        atomicAdd(base + 8 * CH + 1, acc[tt][mt][nt][3]);
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core layers and element-wise pieces
+// ---------------------------------------------------------------------------
+__global__ void to_bf16_kernel(const float* __restrict__ x, bf16* __restrict__ y, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// Weight preparation from the float32 masters: bf16 tensors for the tensor-core
+// layers (forward [tap][co][ci], dgrad [tap'][ci][co] with tap' the mirrored tap)
+// and bf16-rounded float copies for the CUDA-core layers.
+__global__ void prep_weights_kernel(const float* __restrict__ w, bf16* __restrict__ wf, bf16* __restrict__ wd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 27 * CH * CH) return;
+  const int tap = i / (CH * CH), co = (i / CH) % CH, ci = i % CH;
+  const bf16 v = __float2bfloat16_rn(w[i]);
+  wf[i] = v;
+  wd[(size_t(26 - tap) * CH + ci) * CH + co] = v;
+}
+
+__global__ void round_bf16_kernel(const float* __restrict__ w, float* __restrict__ out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __bfloat162float(__float2bfloat16_rn(w[i]));
+}
+
+// h1 = relu(conv(a; w1) + b1), a has one channel.
+__global__ void conv_in_fwd_kernel(Dims d, const bf16* __restrict__ a, const float* __restrict__ w1r,
+                                   const float* __restrict__ b1, bf16* __restrict__ h1, uint32_t* __restrict__ mask) {
+  __shared__ float sw[27 * CH];
+  __shared__ float sb[CH];
+  for (int i = threadIdx.x; i < 27 * CH; i += blockDim.x) sw[i] = w1r[i];
+  if (threadIdx.x < CH) sb[threadIdx.x] = b1[threadIdx.x];
+  __syncthreads();
+  const int64_t gi = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gi >= int64_t(d.B) * d.V) return;
+  const int b = int(gi / d.V);
+  const int64_t v = gi - int64_t(b) * d.V;
+  const int a_ = int(v % d.Na), e = int((v / d.Na) % d.Ne), r = int(v / (int64_t(d.Na) * d.Ne));
+  float an[27];
+#pragma unroll
+  for (int tap = 0; tap < 27; ++tap) {
+    const int64_t q = nbr(d, r, e, a_, tap / 9 - 1, (tap / 3) % 3 - 1, tap % 3 - 1);
+    an[tap] = q < 0 ? 0.0f : __bfloat162float(a[int64_t(b) * d.V + q]);
+  }
+  uint32_t bits = 0;
+  __nv_bfloat162 out[CH / 2];
+#pragma unroll
+  for (int co = 0; co < CH; co += 2) {
+    float z0 = sb[co], z1 = sb[co + 1];
+#pragma unroll
+    for (int tap = 0; tap < 27; ++tap) {
+      z0 = fmaf(sw[tap * CH + co], an[tap], z0);
+      z1 = fmaf(sw[tap * CH + co + 1], an[tap], z1);
+    }
+    bits |= (z0 > 0.0f ? 1u : 0u) << co;
+    bits |= (z1 > 0.0f ? 1u : 0u) << (co + 1);
+    out[co / 2] = __floats2bfloat162_rn(fmaxf(z0, 0.0f), fmaxf(z1, 0.0f));
+  }
+  uint4* dst = reinterpret_cast<uint4*>(h1 + gi * CH);
+  const uint4* src = reinterpret_cast<const uint4*>(out);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) dst[j] = src[j];
+  mask[gi] = bits;
+}
+
+// out = a + b6 + conv(h5; w6)
+__global__ void conv_out_fwd_kernel(Dims d, const bf16* __restrict__ h, const float* __restrict__ w6r,
+                                    const float* __restrict__ b6p, const bf16* __restrict__ a, float* __restrict__ out) {
+  __shared__ float sw[27 * CH];
+  for (int i = threadIdx.x; i < 27 * CH; i += blockDim.x) sw[i] = w6r[i];
+  __syncthreads();
+  const int64_t gi = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gi >= int64_t(d.B) * d.V) return;
+  const int b = int(gi / d.V);
+  const int64_t v = gi - int64_t(b) * d.V;
+  const int a_ = int(v % d.Na), e = int((v / d.Na) % d.Ne), r = int(v / (int64_t(d.Na) * d.Ne));
+  float acc = __ldg(b6p);
+#pragma unroll 1
+  for (int tap = 0; tap < 27; ++tap) {
+    const int64_t q = nbr(d, r, e, a_, tap / 9 - 1, (tap / 3) % 3 - 1, tap % 3 - 1);
+    if (q < 0) continue;
+    const uint4* src = reinterpret_cast<const uint4*>(h + (int64_t(b) * d.V + q) * CH);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint4 u = __ldg(src + j);
+      const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 f = __bfloat1622float2(p[k]);
+        acc = fmaf(sw[tap * CH + j * 8 + 2 * k], f.x, acc);
+        acc = fmaf(sw[tap * CH + j * 8 + 2 * k + 1], f.y, acc);
+      }
+    }
+  }
+  out[gi] = __bfloat162float(a[gi]) + acc;
+}
+
+// g_out = 2 (out - target) / n; loss += sum (out - target)^2 / n (double).
+__global__ void mse_kernel(const float* __restrict__ out, const float* __restrict__ tgt, int64_t n,
+                           float* __restrict__ g, double* __restrict__ loss) {
+  double acc = 0.0;
+  const double inv = 1.0 / double(n);
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const float diff = out[i] - tgt[i];
+    g[i] = float(2.0 * inv * double(diff));
+    acc += double(diff) * double(diff) * inv;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) atomicAdd(loss, v);
+  }
+}
+
+// Output layer backward, input side: g_h[v][ci] = sum_tap w6[tap][ci] g_out[v - d_tap].
+__global__ void conv_out_dgrad_kernel(Dims d, const float* __restrict__ gout, const float* __restrict__ w6r,
+                                      float* __restrict__ gh) {
+  __shared__ float sw[27 * CH];
+  for (int i = threadIdx.x; i < 27 * CH; i += blockDim.x) sw[i] = w6r[i];
+  __syncthreads();
+  const int64_t gi = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gi >= int64_t(d.B) * d.V) return;
+  const int b = int(gi / d.V);
+  const int64_t v = gi - int64_t(b) * d.V;
+  const int a_ = int(v % d.Na), e = int((v / d.Na) % d.Ne), r = int(v / (int64_t(d.Na) * d.Ne));
+  float acc[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) acc[c] = 0.0f;
+#pragma unroll 1
+  for (int tap = 0; tap < 27; ++tap) {
+    const int64_t q = nbr(d, r, e, a_, 1 - tap / 9, 1 - (tap / 3) % 3, 1 - tap % 3);
+    if (q < 0) continue;
+    const float gv = gout[int64_t(b) * d.V + q];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) acc[c] = fmaf(sw[tap * CH + c], gv, acc[c]);
+  }
+  float4* dst = reinterpret_cast<float4*>(gh + gi * CH);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) dst[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
+}
+
+// Weight gradient of a one-sided layer (one channel on one side, 32 on the other):
+//   mode 0 (output layer): dw[tap][ci] += sum_v g1[v] X32[v + d][ci],  db += sum g1
+//   mode 1 (input layer):  dw[tap][co] += sum_v (gh[v][co] if mask) a1[v + d], db[co] += sum
+// grid (27 taps, chunks); each thread keeps 32 partial sums, then block reduction.
+template <int MODE>
+__global__ void thin_wgrad_kernel(Dims d, const float* __restrict__ g1, const bf16* __restrict__ X32,
+                                  const float* __restrict__ gh, const uint32_t* __restrict__ mask,
+                                  const bf16* __restrict__ a1, float* __restrict__ dw, float* __restrict__ db) {
+  const int tap = blockIdx.y;
+  const int dr = tap / 9 - 1, de = (tap / 3) % 3 - 1, da = tap % 3 - 1;
+  float acc[CH], accb[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) acc[c] = accb[c] = 0.0f;
+  const int64_t n = int64_t(d.B) * d.V;
+  for (int64_t gi = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; gi < n; gi += int64_t(gridDim.x) * blockDim.x) {
+    const int b = int(gi / d.V);
+    const int64_t v = gi - int64_t(b) * d.V;
+    const int a_ = int(v % d.Na), e = int((v / d.Na) % d.Ne), r = int(v / (int64_t(d.Na) * d.Ne));
+    const int64_t q = nbr(d, r, e, a_, dr, de, da);
+    if (MODE == 0) {
+      const float gv = g1[gi];
+      if (tap == 0) accb[0] += gv;
+      if (q < 0 || gv == 0.0f) continue;
+      const uint4* src = reinterpret_cast<const uint4*>(X32 + (int64_t(b) * d.V + q) * CH);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint4 u = __ldg(src + j);
+        const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float2 f = __bfloat1622float2(p[k]);
+          acc[j * 8 + 2 * k] = fmaf(gv, f.x, acc[j * 8 + 2 * k]);
+          acc[j * 8 + 2 * k + 1] = fmaf(gv, f.y, acc[j * 8 + 2 * k + 1]);
+        }
+      }
+    } else {
+      const uint32_t m = mask[gi];
+      const float av = q < 0 ? 0.0f : __bfloat162float(a1[int64_t(b) * d.V + q]);
+      const float4* gp = reinterpret_cast<const float4*>(gh + gi * CH);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float4 gv = __ldg(gp + j);
+        const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = 4 * j + k;
+          const float gz = (m >> c) & 1u ? gg[k] : 0.0f;
+          acc[c] = fmaf(gz, av, acc[c]);
+          if (tap == 0) accb[c] += gz;
+        }
+      }
+    }
+  }
+  __shared__ float red[CH][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    float v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    float vb = accb[c];
+    for (int o = 16; o > 0; o >>= 1) vb += __shfl_down_sync(0xffffffffu, vb, o);
+    if (lane == 0) {
+      atomicAdd(dw + tap * CH + c, v);
+      if (tap == 0 && (MODE == 1 || c == 0)) atomicAdd(db + c, vb);
+    }
+  }
+  (void)red;
+  (void)warp;
+}
+
+// g_z = bf16(g_h where the forward pre-activation was positive, else 0)
+__global__ void gate_kernel(const float* __restrict__ gh, const uint32_t* __restrict__ mask, bf16* __restrict__ gz,
+                            int64_t nvox) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= nvox * CH) return;
+  const int64_t v = i >> 5;
+  const int c = int(i & 31);
+  gz[i] = __float2bfloat16_rn(((mask[v] >> c) & 1u) ? gh[i] : 0.0f);
+}
+
+// db[c] += sum_v gz[v][c]
+__global__ void colsum32_kernel(const bf16* __restrict__ gz, int64_t nvox, float* __restrict__ db) {
+  const int c = threadIdx.x & 31;
+  float acc = 0.0f;
+  for (int64_t v = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); v < nvox;
+       v += int64_t(gridDim.x) * (blockDim.x >> 5))
+    acc += __bfloat162float(gz[v * CH + c]);
+  __shared__ float part[32][33];
+  part[threadIdx.x >> 5][c] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float s = 0.0f;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) s += part[w][threadIdx.x];
+    atomicAdd(db + threadIdx.x, s);
+  }
+}
+
+int blocks_for(int64_t n, int threads) { return int(std::min<int64_t>((n + threads - 1) / threads, 1 << 30)); }
+
+}  // namespace
+}  // namespace tsp
+
+using namespace tsp;
+
+// Parameter layout (float32, flat): w1 [27][32][1], b1 [32], w2..w5 [27][32][32],
+// b2..b5 [32], w6 [27][1][32], b6 [1].
+struct tsp_net_s {
+  Dims d{};
+  int max_batch = 0;
+  int device = 0;
+  size_t n_params = 0;
+  size_t off_w[6], off_b[6];
+  float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
+  bf16 *wf[4] = {nullptr, nullptr, nullptr, nullptr}, *wd[4] = {nullptr, nullptr, nullptr, nullptr};
+  float *w1r = nullptr, *w6r = nullptr;
+  bf16* a16 = nullptr;
+  bf16* h[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  uint32_t* mask[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  float *out = nullptr, *gout = nullptr, *gh = nullptr;
+  bf16* gz = nullptr;
+  double* loss = nullptr;
+  std::vector<void*> allocs;
+  int adam_step = 0;
+};
+
+namespace {
+
+size_t fwd_smem(int Na) { return size_t(3 * (TR + 2) * (Na + 2)) * 64 + size_t(27 * 32) * 64; }
+size_t wgrad_smem(int Na) { return size_t(9 * (Na + 2)) * 64 + size_t(Na) * 64; }
+
+template <class T>
+tsp_status net_alloc(tsp_net n, T** p, size_t count) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count);
+  if (e != cudaSuccess) return cuda_fail(e, "tsp_net_create: allocation");
+  n->allocs.push_back(*p);
+  return TSP_OK;
+}
+
+template <int MT>
+tsp_status set_attrs(int Na) {
+  TSP_CUDA(cudaFuncSetAttribute(conv32_kernel<0, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwd_smem(Na))));
+  TSP_CUDA(cudaFuncSetAttribute(conv32_kernel<1, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwd_smem(Na))));
+  return TSP_OK;
+}
+
+template <int MT>
+void launch_conv32(int mode, const Dims& d, int B, const bf16* X, const bf16* W, const float* bias, const bf16* Xres,
+                   bf16* Y, uint32_t* mask, float* G, cudaStream_t st) {
+  Dims db = d;
+  db.B = B;
+  dim3 grid((d.Ne + TR - 1) / TR, d.Nr, B);
+  if (mode == 0) conv32_kernel<0, MT><<<grid, 256, fwd_smem(d.Na), st>>>(db, X, W, bias, Xres, Y, mask, G);
+  else conv32_kernel<1, MT><<<grid, 256, fwd_smem(d.Na), st>>>(db, X, W, bias, Xres, Y, mask, G);
+}
+
+void conv32(int mode, const Dims& d, int B, const bf16* X, const bf16* W, const float* bias, const bf16* Xres, bf16* Y,
+            uint32_t* mask, float* G, cudaStream_t st) {
+  switch (d.Na / 32) {
+    case 1: launch_conv32<1>(mode, d, B, X, W, bias, Xres, Y, mask, G, st); break;
+    case 2: launch_conv32<2>(mode, d, B, X, W, bias, Xres, Y, mask, G, st); break;
+    case 3: launch_conv32<3>(mode, d, B, X, W, bias, Xres, Y, mask, G, st); break;
+    case 4: launch_conv32<4>(mode, d, B, X, W, bias, Xres, Y, mask, G, st); break;
+    case 5: launch_conv32<5>(mode, d, B, X, W, bias, Xres, Y, mask, G, st); break;
+    default: launch_conv32<6>(mode, d, B, X, W, bias, Xres, Y, mask, G, st); break;
+  }
+}
+
+template <int NA>
+void launch_wgrad(const Dims& d, int B, const bf16* Gz, const bf16* H, float* dW, cudaStream_t st) {
+  Dims db = d;
+  db.B = B;
+  const int64_t rows = int64_t(B) * d.Nr * d.Ne;
+  const int rows_per = int(std::max<int64_t>(1, (rows + 4 * 152 - 1) / (4 * 152)));
+  const int grid = int((rows + rows_per - 1) / rows_per);
+  wgrad32_kernel<NA><<<grid, 288, wgrad_smem(NA), st>>>(db, Gz, H, dW, rows_per);
+}
+
+tsp_status wgrad32(const Dims& d, int B, const bf16* Gz, const bf16* H, float* dW, cudaStream_t st) {
+  switch (d.Na) {
+    case 32: launch_wgrad<32>(d, B, Gz, H, dW, st); break;
+    case 64: launch_wgrad<64>(d, B, Gz, H, dW, st); break;
+    case 96: launch_wgrad<96>(d, B, Gz, H, dW, st); break;
+    case 128: launch_wgrad<128>(d, B, Gz, H, dW, st); break;
+    case 160: launch_wgrad<160>(d, B, Gz, H, dW, st); break;
+    case 192: launch_wgrad<192>(d, B, Gz, H, dW, st); break;
+    default: return fail(TSP_ENOTSUP, "wgrad: azimuth count must be a multiple of 32 up to 192");
+  }
+  return TSP_OK;
+}
+
+template <int NA>
+tsp_status wgrad_attr() {
+  TSP_CUDA(cudaFuncSetAttribute(wgrad32_kernel<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wgrad_smem(NA))));
+  return TSP_OK;
+}
+
+tsp_status prepare_weights(tsp_net n, cudaStream_t st) {
+  for (int k = 0; k < 4; ++k)
+    prep_weights_kernel<<<(27 * CH * CH + 255) / 256, 256, 0, st>>>(n->params + n->off_w[k + 1], n->wf[k], n->wd[k]);
+  round_bf16_kernel<<<(27 * CH + 255) / 256, 256, 0, st>>>(n->params + n->off_w[0], n->w1r, 27 * CH);
+  round_bf16_kernel<<<(27 * CH + 255) / 256, 256, 0, st>>>(n->params + n->off_w[5], n->w6r, 27 * CH);
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
+tsp_status net_forward(tsp_net n, const float* a, int B, cudaStream_t st) {
+  const Dims& d = n->d;
+  Dims db = d;
+  db.B = B;
+  const int64_t nv = int64_t(B) * d.V;
+  tsp_status s = prepare_weights(n, st);
+  if (s != TSP_OK) return s;
+  to_bf16_kernel<<<blocks_for(nv, 256), 256, 0, st>>>(a, n->a16, nv);
+  conv_in_fwd_kernel<<<blocks_for(nv, 128), 128, 0, st>>>(db, n->a16, n->w1r, n->params + n->off_b[0], n->h[0],
+                                                          n->mask[0]);
+  for (int k = 0; k < 4; ++k)
+    conv32(0, d, B, n->h[k], n->wf[k], n->params + n->off_b[k + 1], n->h[k], n->h[k + 1], n->mask[k + 1], nullptr, st);
+  conv_out_fwd_kernel<<<blocks_for(nv, 128), 128, 0, st>>>(db, n->h[4], n->w6r, n->params + n->off_b[5], n->a16,
+                                                           n->out);
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
+}  // namespace
+
+extern "C" tsp_status tsp_net_create(int n_r, int n_e, int n_a, int max_batch, tsp_net* out) {
+  if (!out) return fail(TSP_EINVAL, "tsp_net_create: out is NULL");
+  *out = nullptr;
+  if (n_r <= 0 || n_e <= 0 || max_batch <= 0) return fail(TSP_EINVAL, "tsp_net_create: bad size");
+  if (n_a % 32 != 0 || n_a < 32 || n_a > 192)
+    return fail(TSP_ENOTSUP, "tsp_net_create: the azimuth count must be a multiple of 32 in [32, 192]");
+  tsp_net n = new (std::nothrow) tsp_net_s();
+  if (!n) return fail(TSP_ENOMEM, "tsp_net_create: host allocation");
+  n->d = Dims{max_batch, n_r, n_e, n_a, int64_t(n_r) * n_e * n_a};
+  n->max_batch = max_batch;
+  cudaGetDevice(&n->device);
+  size_t off = 0;
+  const size_t wsz[6] = {27 * CH, 27 * CH * CH, 27 * CH * CH, 27 * CH * CH, 27 * CH * CH, 27 * CH};
+  const size_t bsz[6] = {CH, CH, CH, CH, CH, 1};
+  for (int k = 0; k < 6; ++k) {
+    n->off_w[k] = off;
+    off += wsz[k];
+    n->off_b[k] = off;
+    off += bsz[k];
+  }
+  n->n_params = off;
+  const int64_t nv = int64_t(max_batch) * n->d.V;
+  tsp_status st = TSP_OK;
+  if (st == TSP_OK) st = net_alloc(n, &n->params, off);
+  if (st == TSP_OK) st = net_alloc(n, &n->grads, off);
+  if (st == TSP_OK) st = net_alloc(n, &n->m, off);
+  if (st == TSP_OK) st = net_alloc(n, &n->v, off);
+  for (int k = 0; k < 4 && st == TSP_OK; ++k) {
+    st = net_alloc(n, &n->wf[k], 27 * CH * CH);
+    if (st == TSP_OK) st = net_alloc(n, &n->wd[k], 27 * CH * CH);
+  }
+  if (st == TSP_OK) st = net_alloc(n, &n->w1r, 27 * CH);
+  if (st == TSP_OK) st = net_alloc(n, &n->w6r, 27 * CH);
+  if (st == TSP_OK) st = net_alloc(n, &n->a16, nv);
+  for (int k = 0; k < 5 && st == TSP_OK; ++k) {
+    st = net_alloc(n, &n->h[k], nv * CH);
+    if (st == TSP_OK) st = net_alloc(n, &n->mask[k], nv);
+  }
+  if (st == TSP_OK) st = net_alloc(n, &n->out, nv);
+  if (st == TSP_OK) st = net_alloc(n, &n->gout, nv);
+  if (st == TSP_OK) st = net_alloc(n, &n->gh, nv * CH);
+  if (st == TSP_OK) st = net_alloc(n, &n->gz, nv * CH);
+  if (st == TSP_OK) st = net_alloc(n, &n->loss, 1);
+  if (st == TSP_OK) {
+    const int MT = n_a / 32;
+    switch (MT) {
+      case 1: st = set_attrs<1>(n_a); break;
+      case 2: st = set_attrs<2>(n_a); break;
+      case 3: st = set_attrs<3>(n_a); break;
+      case 4: st = set_attrs<4>(n_a); break;
+      case 5: st = set_attrs<5>(n_a); break;
+      default: st = set_attrs<6>(n_a); break;
+    }
+  }
+  if (st == TSP_OK) {
+    switch (n_a) {
+      case 32: st = wgrad_attr<32>(); break;
+      case 64: st = wgrad_attr<64>(); break;
+      case 96: st = wgrad_attr<96>(); break;
+      case 128: st = wgrad_attr<128>(); break;
+      case 160: st = wgrad_attr<160>(); break;
+      default: st = wgrad_attr<192>(); break;
+    }
+  }
+  if (st == TSP_OK) {
+    cudaError_t e = cudaMemset(n->params, 0, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMemset(n->m, 0, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMemset(n->v, 0, sizeof(float) * off);
+    if (e != cudaSuccess) st = cuda_fail(e, "tsp_net_create: clear");
+  }
+  if (st != TSP_OK) {
+    tsp_net_destroy(n);
+    return st;
+  }
+  *out = n;
+  return TSP_OK;
+}
+
+extern "C" void tsp_net_destroy(tsp_net n) {
+  if (!n) return;
+  for (void* p : n->allocs) cudaFree(p);
+  delete n;
+}
+
+extern "C" tsp_status tsp_net_num_params(tsp_net n, size_t* count) {
+  if (!n || !count) return fail(TSP_EINVAL, "tsp_net_num_params: NULL argument");
+  *count = n->n_params;
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_net_set_params(tsp_net n, const float* host, size_t count) {
+  if (!n || !host || count != n->n_params) return fail(TSP_EINVAL, "tsp_net_set_params: bad argument");
+  TSP_CUDA(cudaMemcpy(n->params, host, sizeof(float) * count, cudaMemcpyHostToDevice));
+  TSP_CUDA(cudaMemset(n->m, 0, sizeof(float) * count));
+  TSP_CUDA(cudaMemset(n->v, 0, sizeof(float) * count));
+  n->adam_step = 0;
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_net_get_params(tsp_net n, float* host, size_t count) {
+  if (!n || !host || count != n->n_params) return fail(TSP_EINVAL, "tsp_net_get_params: bad argument");
+  TSP_CUDA(cudaMemcpy(host, n->params, sizeof(float) * count, cudaMemcpyDeviceToHost));
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_net_get_grads(tsp_net n, float* host, size_t count) {
+  if (!n || !host || count != n->n_params) return fail(TSP_EINVAL, "tsp_net_get_grads: bad argument");
+  TSP_CUDA(cudaMemcpy(host, n->grads, sizeof(float) * count, cudaMemcpyDeviceToHost));
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_net_forward(tsp_net n, const float* a, int batch, float* out, void* stream) {
+  if (!n || !a || !out || batch <= 0 || batch > n->max_batch) return fail(TSP_EINVAL, "tsp_net_forward: bad argument");
+  tsp_status st = check_device(n->device);
+  if (st != TSP_OK) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  st = net_forward(n, a, batch, cs);
+  if (st != TSP_OK) return st;
+  TSP_CUDA(cudaMemcpyAsync(out, n->out, sizeof(float) * size_t(batch) * n->d.V, cudaMemcpyDeviceToDevice, cs));
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_net_loss_grad(tsp_net n, const float* a, const float* target, int batch, double* loss_host,
+                                        void* stream) {
+  if (!n || !a || !target || batch <= 0 || batch > n->max_batch)
+    return fail(TSP_EINVAL, "tsp_net_loss_grad: bad argument");
+  tsp_status st = check_device(n->device);
+  if (st != TSP_OK) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  st = net_forward(n, a, batch, cs);
+  if (st != TSP_OK) return st;
+  const Dims& d = n->d;
+  Dims db = d;
+  db.B = batch;
+  const int64_t nv = int64_t(batch) * d.V;
+  TSP_CUDA(cudaMemsetAsync(n->loss, 0, sizeof(double), cs));
+  TSP_CUDA(cudaMemsetAsync(n->grads, 0, sizeof(float) * n->n_params, cs));
+  mse_kernel<<<std::min(blocks_for(nv, 256), 152 * 8), 256, 0, cs>>>(n->out, target, nv, n->gout, n->loss);
+  // output layer
+  const int chunks = std::max(1, std::min(blocks_for(nv, 256), 152 * 4 / 27 + 1));
+  thin_wgrad_kernel<0><<<dim3(chunks, 27), 256, 0, cs>>>(db, n->gout, n->h[4], nullptr, nullptr, nullptr,
+                                                         n->grads + n->off_w[5], n->grads + n->off_b[5]);
+  conv_out_dgrad_kernel<<<blocks_for(nv, 128), 128, 0, cs>>>(db, n->gout, n->w6r, n->gh);
+  // residual 32 -> 32 layers, last to first
+  for (int k = 3; k >= 0; --k) {
+    gate_kernel<<<blocks_for(nv * CH, 256), 256, 0, cs>>>(n->gh, n->mask[k + 1], n->gz, nv);
+    st = wgrad32(d, batch, n->gz, n->h[k], n->grads + n->off_w[k + 1], cs);
+    if (st != TSP_OK) return st;
+    colsum32_kernel<<<std::min(blocks_for(nv, 8), 152 * 4), 256, 0, cs>>>(n->gz, nv, n->grads + n->off_b[k + 1]);
+    conv32(1, d, batch, n->gz, n->wd[k], nullptr, nullptr, nullptr, nullptr, n->gh, cs);
+  }
+  // input layer (ReLU gate applied inside)
+  thin_wgrad_kernel<1><<<dim3(chunks, 27), 256, 0, cs>>>(db, nullptr, nullptr, n->gh, n->mask[0], n->a16,
+                                                         n->grads + n->off_w[0], n->grads + n->off_b[0]);
+  TSP_CUDA(cudaGetLastError());
+  if (loss_host) {
+    TSP_CUDA(cudaMemcpyAsync(loss_host, n->loss, sizeof(double), cudaMemcpyDeviceToHost, cs));
+    TSP_CUDA(cudaStreamSynchronize(cs));
+  }
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_net_adam(tsp_net n, float lr, float beta1, float beta2, float eps, float weight_decay,
+                                   void* stream) {
+  if (!n) return fail(TSP_EINVAL, "tsp_net_adam: NULL net");
+  n->adam_step += 1;
+  return tsp_adam(n->params, n->grads, n->m, n->v, int64_t(n->n_params), lr, beta1, beta2, eps, weight_decay,
+                  n->adam_step, stream);
+}
+
+extern "C" tsp_status tsp_net_activation(tsp_net n, int layer, int batch, void* host) {
+  if (!n || !host || layer < 0 || layer > 5 || batch <= 0 || batch > n->max_batch)
+    return fail(TSP_EINVAL, "tsp_net_activation: bad argument");
+  const size_t nv = size_t(batch) * n->d.V;
+  if (layer < 5) TSP_CUDA(cudaMemcpy(host, n->h[layer], sizeof(bf16) * nv * CH, cudaMemcpyDeviceToHost));
+  else TSP_CUDA(cudaMemcpy(host, n->out, sizeof(float) * nv, cudaMemcpyDeviceToHost));
+  return TSP_OK;
+}

@@ -131,3 +131,89 @@ class Adam:
             check(L.tsp_adam(ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(m.data_ptr()),
                              ctypes.c_void_p(v.data_ptr()), p.numel(), self.lr, self.betas[0], self.betas[1], self.eps,
                              self.wd, self.t, _stream(p)), "tsp_adam")
+
+
+class WarmStartNet:
+    """Residual 3D convolutional network on the spherical grid (tsp_net_*):
+    bfloat16 weights/activations, float32 accumulation, trained by the
+    library's own forward, backward and Adam kernels."""
+
+    def __init__(self, shape, max_batch: int):
+        L_ = _lib.load()
+        h = ctypes.c_void_p()
+        check(L_.tsp_net_create(shape[0], shape[1], shape[2], max_batch, ctypes.byref(h)), "tsp_net_create")
+        self.handle = h
+        self.shape = tuple(shape)
+        self.max_batch = max_batch
+        n = ctypes.c_size_t()
+        check(L_.tsp_net_num_params(h, ctypes.byref(n)), "tsp_net_num_params")
+        self.n_params = n.value
+
+    @staticmethod
+    def layout():
+        """(offset, shape) of each weight and bias in the flat parameter vector."""
+        shapes = [(27, 32, 1), (32,)] + [(27, 32, 32), (32,)] * 4 + [(27, 1, 32), (1,)]
+        out, off = [], 0
+        for sh in shapes:
+            out.append((off, sh))
+            off += int(np.prod(sh))
+        return out
+
+    def set_params(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        check(_lib.load().tsp_net_set_params(self.handle, ctypes.c_void_p(flat.ctypes.data), flat.size),
+              "tsp_net_set_params")
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32)
+        check(_lib.load().tsp_net_get_params(self.handle, ctypes.c_void_p(out.ctypes.data), out.size),
+              "tsp_net_get_params")
+        return out
+
+    def get_grads(self) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32)
+        check(_lib.load().tsp_net_get_grads(self.handle, ctypes.c_void_p(out.ctypes.data), out.size),
+              "tsp_net_get_grads")
+        return out
+
+    def forward(self, a: torch.Tensor) -> torch.Tensor:
+        _require_cuda(a, "a")
+        B = a.shape[0]
+        out = torch.empty_like(a)
+        check(_lib.load().tsp_net_forward(self.handle, ctypes.c_void_p(a.data_ptr()), B, ctypes.c_void_p(out.data_ptr()),
+                                          _stream(a)), "tsp_net_forward")
+        return out
+
+    def loss_grad(self, a: torch.Tensor, target: torch.Tensor) -> float:
+        _require_cuda(a, "a")
+        _require_cuda(target, "target")
+        loss = ctypes.c_double()
+        check(_lib.load().tsp_net_loss_grad(self.handle, ctypes.c_void_p(a.data_ptr()),
+                                            ctypes.c_void_p(target.data_ptr()), a.shape[0], ctypes.byref(loss),
+                                            _stream(a)), "tsp_net_loss_grad")
+        return loss.value
+
+    def adam(self, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, weight_decay=0.0):
+        check(_lib.load().tsp_net_adam(self.handle, lr, betas[0], betas[1], eps, weight_decay,
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)), "tsp_net_adam")
+
+    def activation(self, layer: int, batch: int) -> np.ndarray:
+        nv = batch * int(np.prod(self.shape))
+        if layer < 5:
+            raw = np.zeros(nv * 32, np.uint16)
+            check(_lib.load().tsp_net_activation(self.handle, layer, batch, ctypes.c_void_p(raw.ctypes.data)),
+                  "tsp_net_activation")
+            return (raw.astype(np.uint32) << 16).view(np.float32).reshape(batch, *self.shape, 32)
+        out = np.zeros(nv, np.float32)
+        check(_lib.load().tsp_net_activation(self.handle, 5, batch, ctypes.c_void_p(out.ctypes.data)),
+              "tsp_net_activation")
+        return out.reshape(batch, *self.shape)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _lib.load(build_if_missing=False).tsp_net_destroy(h)
+            except Exception:
+                pass
+            self.handle = None

@@ -1,0 +1,93 @@
+"""Warm-start network kernels (implicit-GEMM BF16 tensor-core convolutions and
+CUDA-core end layers) against the network oracle, which rounds weights and
+stored activations to bfloat16 at the same points and accumulates in float64.
+
+Tolerances follow from that arithmetic: the GPU accumulates in float32, so a
+pre-rounding value within ~1e-6 of a bfloat16 rounding boundary can land one
+bfloat16 ulp (2^-8 relative) away; activations must agree to one ulp and such
+flips must be rare (a flip feeds the next layer, hence two ulps); outputs and gradients (sums over many voxels) agree
+normwise to 1e-2.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import net as onet
+from paper_2608_16960_gb300 import synth
+from paper_2608_16960_gb300.model import WarmStartNet
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+
+
+def _params(seed):
+    ps = onet.init_params(seed)
+    rng = synth.SplitMix64(seed + 100)
+    return [(w, (0.05 * rng.normal(len(b))).astype(np.float32)) for w, b in ps]
+
+
+def _flat(params):
+    return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in params]).astype(np.float32)
+
+
+def _unflat(flat):
+    out = []
+    for (off_w, sh_w), (off_b, sh_b) in zip(WarmStartNet.layout()[0::2], WarmStartNet.layout()[1::2]):
+        out.append((flat[off_w:off_w + int(np.prod(sh_w))].reshape(sh_w), flat[off_b:off_b + int(np.prod(sh_b))]))
+    return out
+
+
+@pytest.fixture(scope="module")
+def case():
+    shape = (4, 5, 64)  # five theta-rows: exercises the partial last tile
+    B = 2
+    params = _params(1)
+    rng = synth.SplitMix64(2)
+    a = np.abs(rng.normal(B * int(np.prod(shape)))).reshape(B, *shape).astype(np.float32)
+    t = np.abs(rng.normal(B * int(np.prod(shape)))).reshape(B, *shape).astype(np.float32)
+    net = WarmStartNet(shape, max_batch=B)
+    net.set_params(_flat(params))
+    return shape, B, params, a, t, net
+
+
+def test_param_layout_roundtrip(case):
+    shape, B, params, a, t, net = case
+    assert net.n_params == sum(w.size + b.size for w, b in params)
+    assert np.array_equal(net.get_params(), _flat(params))
+
+
+def test_forward_matches_oracle(case):
+    shape, B, params, a, t, net = case
+    out = net.forward(torch.tensor(a, device=DEV)).cpu().numpy()
+    ref, (a16, ws, h, masks) = onet.forward(params, a, keep=True)
+    for k in range(5):
+        hg = net.activation(k, B)
+        diff = np.abs(hg - h[k])
+        ulp = np.maximum(np.abs(h[k]), 1e-30) * 2.0 ** -6  # two bfloat16 ulps
+        assert np.all(diff <= ulp + 1e-6), (k, diff.max())
+        assert np.mean(diff > 0) < 0.01, (k, np.mean(diff > 0))
+    assert np.linalg.norm(out - ref) <= 1e-2 * np.linalg.norm(ref)
+
+
+def test_gradients_match_oracle(case):
+    shape, B, params, a, t, net = case
+    loss = net.loss_grad(torch.tensor(a, device=DEV), torch.tensor(t, device=DEV))
+    ref_loss, grads = onet.loss_and_grads(params, a, t)
+    assert abs(loss - ref_loss) <= 1e-2 * ref_loss
+    g = _unflat(net.get_grads())
+    for k in range(6):
+        for which in range(2):
+            gg, rr = g[k][which].astype(np.float64), np.asarray(grads[k][which], np.float64)
+            assert np.linalg.norm(gg - rr) <= 2e-2 * np.linalg.norm(rr) + 1e-9, (k, which)
+
+
+def test_training_steps_reduce_loss(case):
+    shape, B, params, a, t, net = case
+    at, tt = torch.tensor(a, device=DEV), torch.tensor(t, device=DEV)
+    net.set_params(_flat(params))
+    losses = []
+    for _ in range(30):
+        losses.append(net.loss_grad(at, tt))
+        net.adam(lr=2e-3)
+    assert losses[-1] < 0.7 * losses[0], losses[::5]
+    net.set_params(_flat(params))
