@@ -296,6 +296,36 @@ tsp_status tsp_net_adam(tsp_net net, float lr, float beta1, float beta2, float e
 tsp_status tsp_net_activation(tsp_net net, int layer, int batch, void* host);
 
 /*
+ * tsp_sirt_weights - the SIRT weights alone: R = 1/(F 1) per ray (device float32
+ * [n_rays]) and C = 1/(F^T 1) per voxel (device float32 [voxels]), 0 where the
+ * sum is 0. Used to form the warm start's input C * F^T(R * y).
+ */
+tsp_status tsp_sirt_weights(tsp_grid grid, tsp_geom geom, float* R, float* C, void* stream);
+
+/*
+ * Data pipeline of the learned warm start (synthetic training data).
+ * tsp_phantoms  - rho[b] = exp(-r/H_b) + sum_j A_j exp(-|p - c_j|^2 / (2 s_j^2)) at
+ *                 the voxel centres (arithmetic midpoints of the edges); params:
+ *                 device float32 [batch][rows][5], row 0 = (H, 0, 0, 0, 0), each
+ *                 further row a blob (c_x, c_y, c_z, A, s); rho [batch][voxels].
+ * tsp_batch_max - out[b] = max_i x[b][i] (device float32 [batch]).
+ * tsp_add_noise - y[b][i] += frac * max_i y[b][i] * z_i with z_i standard normal
+ *                 from SplitMix64 on the counter seeds[b] + (i+1)*golden and
+ *                 Box-Muller over the sample (z_i uses draws i and n+i);
+ *                 seeds: device uint64 [batch]; ymax receives the per-sample max.
+ * tsp_mul_bcast - x[b][i] *= s[i].
+ * tsp_scale_batch - x[b][i] /= scale[b] (divide != 0) or *= scale[b]; scale 0
+ *                 leaves the sample unchanged.
+ * All device pointers; asynchronous on stream.
+ */
+tsp_status tsp_phantoms(tsp_grid grid, const float* params, int rows, int batch, float* rho, void* stream);
+tsp_status tsp_batch_max(const float* x, int64_t n, int batch, float* out, void* stream);
+tsp_status tsp_add_noise(float* y, int64_t n, int batch, const uint64_t* seeds, float frac, float* ymax,
+                         void* stream);
+tsp_status tsp_mul_bcast(float* x, const float* s, int64_t n, int batch, void* stream);
+tsp_status tsp_scale_batch(float* x, const float* scale, int64_t n, int batch, int divide, void* stream);
+
+/*
  * tsp_device_status - synchronises `stream`, then reads and clears the device
  * error word (0 = no kernel reported an inconsistency).
  */

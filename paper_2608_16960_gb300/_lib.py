@@ -89,6 +89,12 @@ SIGNATURES = {
     "tsp_net_loss_grad": (_I, [_P, _P, _P, _I, ctypes.POINTER(ctypes.c_double), _P]),
     "tsp_net_adam": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
     "tsp_net_activation": (_I, [_P, _I, _I, _P]),
+    "tsp_sirt_weights": (_I, [_P, _P, _P, _P, _P]),
+    "tsp_phantoms": (_I, [_P, _P, _I, _I, _P, _P]),
+    "tsp_batch_max": (_I, [_P, _I64, _I, _P, _P]),
+    "tsp_add_noise": (_I, [_P, _I64, _I, _P, ctypes.c_float, _P, _P]),
+    "tsp_mul_bcast": (_I, [_P, _P, _I64, _I, _P]),
+    "tsp_scale_batch": (_I, [_P, _P, _I64, _I, _I, _P]),
     "tsp_device_status": (_I, [_P, _IP]),
     "tsp_last_error": (ctypes.c_char_p, []),
     "tsp_version": (_I, []),

@@ -180,13 +180,30 @@ extern "C" tsp_status tsp_grid_create(const double* r_edges, int n_r_edges, cons
     delete g;
     return fail(TSP_ENOTSUP, "tsp_grid_create: boundary tables exceed 48 KB (too many edges)");
   }
+  // voxel centres at the arithmetic midpoints of the edges (for phantoms and models)
+  std::vector<float> centres(size_t(Nr + 2 * Ne + 2 * Na));
+  for (int k = 0; k < Nr; ++k) centres[k] = float(0.5 * (r_edges[k] + r_edges[k + 1]));
+  for (int k = 0; k < Ne; ++k) {
+    const double t = 0.5 * (theta_edges[k] + theta_edges[k + 1]);
+    centres[Nr + k] = float(std::sin(t));
+    centres[Nr + Ne + k] = float(std::cos(t));
+  }
+  for (int k = 0; k < Na; ++k) {
+    const double p = 0.5 * (phi_edges[k] + phi_edges[k + 1]);
+    centres[Nr + 2 * Ne + k] = float(std::cos(p));
+    centres[Nr + 2 * Ne + Na + k] = float(std::sin(p));
+  }
   cudaError_t e = cudaGetDevice(&g->device);
   if (e == cudaSuccess) e = cudaMalloc(&g->d_table, sizeof(float) * table.size());
   if (e == cudaSuccess)
     e = cudaMemcpy(g->d_table, table.data(), sizeof(float) * table.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_centres, sizeof(float) * centres.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(g->d_centres, centres.data(), sizeof(float) * centres.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     tsp_status st = tsp::cuda_fail(e, "tsp_grid_create: upload");
     if (g->d_table) cudaFree(g->d_table);
+    if (g->d_centres) cudaFree(g->d_centres);
     delete g;
     return st;
   }
@@ -205,6 +222,7 @@ extern "C" tsp_status tsp_grid_shape(tsp_grid g, int* n_r, int* n_e, int* n_a) {
 extern "C" void tsp_grid_destroy(tsp_grid g) {
   if (!g) return;
   if (g->d_table) cudaFree(g->d_table);
+  if (g->d_centres) cudaFree(g->d_centres);
   delete g;
 }
 

@@ -150,6 +150,23 @@ size_t sirt_workspace_bytes(const tsp_grid_s* grid, const tsp_geom_s* geom) { re
 
 using namespace tsp;
 
+extern "C" tsp_status tsp_sirt_weights(tsp_grid grid, tsp_geom geom, float* R, float* C, void* stream) {
+  tsp_status st = check_trace_args(grid, geom, R, C, 1, nullptr, "tsp_sirt_weights");
+  if (st != TSP_OK) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const int64_t V = grid->voxels();
+  PathLenOp lop;
+  lop.R = R;
+  launch_trace(grid, geom, preferred_launch(grid, geom, false), lop, cs);
+  TSP_CUDA(cudaMemsetAsync(C, 0, sizeof(float) * size_t(V), cs));
+  UnitScatterOp uop;
+  uop.c = C;
+  launch_trace(grid, geom, preferred_launch(grid, geom, true), uop, cs);
+  reciprocal_kernel<<<elementwise_blocks(V), 256, 0, cs>>>(C, V);
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
 extern "C" tsp_status tsp_sirt_workspace_bytes(tsp_grid grid, tsp_geom geom, size_t* bytes) {
   if (!grid || !geom || !bytes) return fail(TSP_EINVAL, "tsp_sirt_workspace_bytes: NULL argument");
   *bytes = workspace_bytes(grid, geom);

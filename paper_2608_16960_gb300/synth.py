@@ -103,30 +103,50 @@ def voxel_centres(edges: GridEdges):
     return R * np.sin(T) * np.cos(P), R * np.sin(T) * np.sin(P), R * np.cos(T), R
 
 
-def blob_phantom(edges: GridEdges, seed: int, n_blobs: int = 5, scale_height: float = 4.0,
-                 sigma=(1.0, 3.0), amp=(0.1, 1.0), centre_r=(4.0, 20.0)) -> np.ndarray:
-    """exp(-r/H) background plus seeded isotropic Gaussian blobs, float32, C-order
-    (N_r, N_e, N_a)."""
+def blob_params(seed: int, n_blobs: int = 5, scale_height: float = 4.0, sigma=(1.0, 3.0), amp=(0.1, 1.0),
+                centre_r=(4.0, 20.0)) -> np.ndarray:
+    """Phantom parameters: row 0 = (scale height, 0, 0, 0, 0), then one row per
+    blob (centre x, y, z, amplitude, sigma). float64 (1 + n_blobs, 5)."""
     rng = SplitMix64(seed)
-    x, y, z, r = voxel_centres(edges)
-    rho = np.exp(-r / scale_height)
     dirs = rng.unit_vectors(n_blobs)
     radii = rng.uniform(n_blobs, *centre_r)
     amps = rng.uniform(n_blobs, *amp)
     sig = rng.uniform(n_blobs, *sigma)
-    for j in range(n_blobs):
-        c = dirs[j] * radii[j]
-        d2 = (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2
-        rho = rho + amps[j] * np.exp(-d2 / (2.0 * sig[j] ** 2))
+    out = np.zeros((1 + n_blobs, 5))
+    out[0, 0] = scale_height
+    out[1:, :3] = dirs * radii[:, None]
+    out[1:, 3] = amps
+    out[1:, 4] = sig
+    return out
+
+
+def render_phantom(edges: GridEdges, params: np.ndarray) -> np.ndarray:
+    """exp(-r/H) + sum_j A_j exp(-|p - c_j|^2 / (2 s_j^2)) at the voxel centres."""
+    x, y, z, r = voxel_centres(edges)
+    rho = np.exp(-r / params[0, 0])
+    for c0, c1, c2, A, s in params[1:]:
+        d2 = (x - c0) ** 2 + (y - c1) ** 2 + (z - c2) ** 2
+        rho = rho + A * np.exp(-d2 / (2.0 * s * s))
     return rho.astype(np.float32)
 
 
-def training_phantom(edges: GridEdges, seed: int) -> np.ndarray:
+def blob_phantom(edges: GridEdges, seed: int, n_blobs: int = 5, scale_height: float = 4.0,
+                 sigma=(1.0, 3.0), amp=(0.1, 1.0), centre_r=(4.0, 20.0)) -> np.ndarray:
+    """exp(-r/H) background plus seeded isotropic Gaussian blobs, float32, C-order
+    (N_r, N_e, N_a)."""
+    return render_phantom(edges, blob_params(seed, n_blobs, scale_height, sigma, amp, centre_r))
+
+
+def training_params(seed: int) -> np.ndarray:
     """Phantom family of the learned warm start: 1-8 blobs on exp(-r/H), H in U(2,6)."""
     rng = SplitMix64(seed ^ 0x5A5A5A5A)
     nb = int(rng.integers(1, 8, 1)[0])
     h = float(rng.uniform(1, 2.0, 6.0)[0])
-    return blob_phantom(edges, seed, n_blobs=nb, scale_height=h)
+    return blob_params(seed, n_blobs=nb, scale_height=h)
+
+
+def training_phantom(edges: GridEdges, seed: int) -> np.ndarray:
+    return render_phantom(edges, training_params(seed))
 
 
 def circular_orbit(n_views: int, radius: float = 60.0, incline_deg: float = 0.0,

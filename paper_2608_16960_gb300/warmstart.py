@@ -1,0 +1,136 @@
+"""Learned warm start for SIRT: training data from this projector, a small
+residual 3D convolutional network (tsp_net_*), and the warm-vs-cold
+reconstruction comparison.
+
+Every numerical step runs in the library: phantoms (tsp_phantoms), projection
+(tsp_forward), noise (tsp_add_noise), the normalised back-projection
+a = C * F^T(R * y) (tsp_sirt_weights, tsp_mul_bcast, tsp_adjoint,
+tsp_scale_batch), the network and its training (tsp_net_*), SIRT (tsp_sirt).
+Torch holds the buffers and computes the reported error metrics.
+"""
+from __future__ import annotations
+
+import ctypes
+import time
+
+import numpy as np
+import torch
+
+from . import _lib, synth
+from ._lib import check
+from .model import WarmStartNet
+from .projector import Geometry, Grid, sirt_workspace, tsp_adjoint, tsp_forward, tsp_sirt
+
+MAX_BLOBS = 8
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _st():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class WarmStart:
+    def __init__(self, edges, pos, det, fov_deg, max_batch=8, noise_frac=0.01):
+        self.edges = edges
+        self.grid = Grid.from_edges(edges)
+        self.geom = Geometry.cone(pos, (det, det), fov_deg)
+        self.shape = self.grid.shape
+        self.V = self.grid.voxels
+        self.noise_frac = noise_frac
+        self.max_batch = max_batch
+        self.net = WarmStartNet(self.shape, max_batch)
+        L = _lib.load()
+        self.R = torch.empty(self.geom.n_rays, device="cuda")
+        self.C = torch.empty(self.shape, device="cuda")
+        check(L.tsp_sirt_weights(self.grid.handle, self.geom.handle, _p(self.R), _p(self.C), _st()), "tsp_sirt_weights")
+        self.mask = self.C > 0  # voxels some ray crosses
+        self.ws = sirt_workspace(self.grid, self.geom)
+
+    # ---- data -------------------------------------------------------------
+    def phantoms(self, seeds):
+        rows = 1 + MAX_BLOBS
+        P = np.zeros((len(seeds), rows, 5), np.float32)
+        for i, s in enumerate(seeds):
+            prm = synth.training_params(int(s))
+            P[i, :len(prm)] = prm
+            P[i, len(prm):, 4] = 1.0  # unused rows: amplitude 0, unit width
+        Pd = torch.tensor(P, device="cuda")
+        rho = torch.empty((len(seeds),) + self.shape, device="cuda")
+        check(_lib.load().tsp_phantoms(self.grid.handle, _p(Pd), rows, len(seeds), _p(rho), _st()), "tsp_phantoms")
+        return rho
+
+    def measure(self, rho, seeds):
+        """Noisy measurements y = F rho + noise (1% of each sample's peak)."""
+        y = tsp_forward(self.grid, self.geom, rho.contiguous())
+        s = torch.tensor(np.asarray(seeds, dtype=np.uint64).view(np.int64), device="cuda")
+        ymax = torch.empty(len(seeds), device="cuda")
+        check(_lib.load().tsp_add_noise(_p(y), self.geom.n_rays, len(seeds), _p(s), self.noise_frac, _p(ymax), _st()),
+              "tsp_add_noise")
+        return y
+
+    def net_input(self, y):
+        """a = C * F^T(R * y), each sample divided by its maximum; returns (a, scale)."""
+        L = _lib.load()
+        B = y.shape[0]
+        yr = y.clone()
+        check(L.tsp_mul_bcast(_p(yr), _p(self.R), self.geom.n_rays, B, _st()), "tsp_mul_bcast")
+        a = tsp_adjoint(self.grid, self.geom, yr)
+        check(L.tsp_mul_bcast(_p(a), _p(self.C), self.V, B, _st()), "tsp_mul_bcast")
+        scale = torch.empty(B, device="cuda")
+        check(L.tsp_batch_max(_p(a), self.V, B, _p(scale), _st()), "tsp_batch_max")
+        check(L.tsp_scale_batch(_p(a), _p(scale), self.V, B, 1, _st()), "tsp_scale_batch")
+        return a, scale
+
+    def batch(self, seeds):
+        rho = self.phantoms(seeds)
+        y = self.measure(rho, seeds)
+        a, scale = self.net_input(y)
+        t = rho.clone()
+        check(_lib.load().tsp_scale_batch(_p(t), _p(scale), self.V, len(seeds), 1, _st()), "tsp_scale_batch")
+        return a, t, y, rho, scale
+
+    # ---- training -----------------------------------------------------------
+    def train(self, n_samples, batch=8, lr=1e-3, seed0=1000, log_every=0):
+        losses = []
+        steps = (n_samples + batch - 1) // batch
+        for s in range(steps):
+            seeds = [seed0 + s * batch + i for i in range(batch)]
+            a, t, _, _, _ = self.batch(seeds)
+            losses.append(self.net.loss_grad(a, t))
+            self.net.adam(lr=lr)
+            if log_every and s % log_every == 0:
+                print(f"step {s}/{steps} loss {losses[-1]:.4e}", flush=True)
+        return losses
+
+    # ---- reconstruction -------------------------------------------------------
+    def rel_error(self, x, truth):
+        m = self.mask
+        return float(torch.linalg.norm((x - truth)[m]) / torch.linalg.norm(truth[m]))
+
+    def warm_start(self, y):
+        """rho0 = net(a) * scale (clamped at 0)."""
+        a, scale = self.net_input(y[None])
+        out = self.net.forward(a)
+        check(_lib.load().tsp_scale_batch(_p(out), _p(scale), self.V, 1, 0, _st()), "tsp_scale_batch")
+        return torch.clamp(out[0], min=0.0)
+
+    def sirt_curve(self, y, truth, x0, n_iter, every=1):
+        """Errors after 0, every, 2*every, ... SIRT iterations from x0 and the time per iteration."""
+        x = x0.clone()
+        errs = [self.rel_error(x, truth)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        first = True
+        done = 0
+        while done < n_iter:
+            k = min(every, n_iter - done)
+            tsp_sirt(self.grid, self.geom, y.contiguous(), x, k, nonneg=True, workspace=self.ws,
+                     reuse_weights=not first)
+            first = False
+            done += k
+            errs.append(self.rel_error(x, truth))
+        torch.cuda.synchronize()
+        return x, errs, (time.perf_counter() - t0) / max(1, n_iter)

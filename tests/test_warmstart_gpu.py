@@ -1,0 +1,73 @@
+"""Learned warm-start pipeline: phantom and noise kernels against their host
+definitions, the network input against the FP64 oracle, and a small training
+run in which the trained network improves on its own input (the SIRT-weighted
+back-projection)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import sirt as osirt
+from paper_2608_16960_gb300 import _lib, synth
+from paper_2608_16960_gb300.warmstart import WarmStart, _p, _st
+
+from _util import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ws():
+    e = synth.grid_edges(12, 10, 32)
+    pos = synth.circular_orbit(12, 60.0, incline_deg=35.0)
+    return WarmStart(e, pos, 32, 50.0, max_batch=4)
+
+
+def test_phantoms_match_host_renderer(ws):
+    seeds = [7, 8, 9]
+    rho = ws.phantoms(seeds).cpu().numpy()
+    for i, s in enumerate(seeds):
+        ref = synth.render_phantom(ws.edges, synth.training_params(s)).astype(np.float64)
+        assert np.max(np.abs(rho[i] - ref)) <= 1e-5 * np.max(ref)
+
+
+def test_noise_matches_host_stream(ws):
+    n = 10007
+    y = torch.tensor(np.linspace(0.0, 2.0, 2 * n, dtype=np.float32).reshape(2, n), device="cuda")
+    seeds = torch.tensor(np.array([123, 456], dtype=np.uint64).view(np.int64), device="cuda")
+    ymax = torch.empty(2, device="cuda")
+    y0 = y.clone()
+    assert _lib.load().tsp_add_noise(_p(y), n, 2, _p(seeds), 0.01, _p(ymax), _st()) == 0
+    assert np.allclose(ymax.cpu().numpy(), [y0[0].max().item(), y0[1].max().item()])
+    for b, s in enumerate((123, 456)):
+        z = synth.SplitMix64(s).normal(n)
+        got = (y[b] - y0[b]).cpu().numpy().astype(np.float64) / (0.01 * ymax[b].item())
+        assert np.max(np.abs(got - z)) < 2e-4
+
+
+def test_net_input_matches_oracle(ws):
+    """Measurements come from the oracle's own projection of the host-rendered phantom."""
+    st, di = oracle.cone_rays(synth.circular_orbit(12, 60.0, incline_deg=35.0), 32, 32, 50.0)
+    rho = synth.render_phantom(ws.edges, synth.training_params(11))
+    y = oracle.forward(ws.edges, st, di, rho)
+    a, scale = ws.net_input(torch.tensor(y.astype(np.float32).reshape((1,) + ws.geom.det_shape), device="cuda"))
+    R, C = osirt.weights(ws.edges, st, di)
+    ref = C * oracle.adjoint(ws.edges, st, di, R * y.astype(np.float32).astype(np.float64))
+    parity(a[0].cpu().numpy() * scale[0].item(), ref, what="network input")
+    assert abs(scale[0].item() - ref.max()) <= 1e-4 * ref.max()
+
+
+def test_training_improves_on_the_input(ws):
+    losses = ws.train(n_samples=320, batch=4, lr=2e-3, seed0=1000)
+    assert np.mean(losses[-10:]) < 0.7 * np.mean(losses[:10])
+    gains = []
+    for s in (900001, 900002, 900003):
+        rho = ws.phantoms([s])
+        y = ws.measure(rho, [s])
+        a, scale = ws.net_input(y)
+        base = ws.rel_error(torch.clamp(a[0] * scale[0], min=0.0), rho[0])
+        warm = ws.rel_error(ws.warm_start(y[0]), rho[0])
+        gains.append(base - warm)
+    assert np.mean(gains) > 0, gains
