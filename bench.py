@@ -48,12 +48,17 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["paper_scale", "batched", "differentiation"], default="paper_scale",
+    ap.add_argument("--workload", choices=["paper_scale", "batched", "differentiation", "warmstart"],
+                    default="paper_scale",
                     help="batched: 64 uneven SIRT reconstructions in one captured graph (not the headline metric)")
     ap.add_argument("--iters", type=int, default=50, help="SIRT iterations of the batched workload")
     ap.add_argument("--autotune", action="store_true", help="autotune launch knobs before timing")
     ap.add_argument("--adam-steps", type=int, default=500, help="Adam steps of the differentiation workload")
     ap.add_argument("--lr", type=float, default=1e-2, help="Adam learning rate of the differentiation workload")
+    ap.add_argument("--train-samples", type=int, default=20000, help="warm start: training phantoms")
+    ap.add_argument("--eval", type=int, default=8, help="warm start: held-out phantoms")
+    ap.add_argument("--cap", type=int, default=500, help="warm start: cold SIRT iteration cap")
+    ap.add_argument("--target", type=float, default=0.01, help="warm start: relative error target")
     return ap.parse_args()
 
 
@@ -465,6 +470,78 @@ def run_differentiation(args):
     print(json.dumps(out), flush=True)
 
 
+def run_warmstart(args):
+    """Learned warm start vs plain SIRT: 64x48x96 grid, 48 cone views of 256^2 (50 deg,
+    orbit radius 60), 1% noise. Train the network on fresh phantoms, then on held-out
+    phantoms time (a) warm: input + network + SIRT iterations, (b) cold: SIRT from 0,
+    each to the error target (or, if cold SIRT never reaches it within the cap, to the
+    cold solver's best error)."""
+    import torch
+
+    from paper_2608_16960_gb300 import synth
+    from paper_2608_16960_gb300.projector import tsp_autotune, tsp_sirt
+    from paper_2608_16960_gb300.warmstart import WarmStart
+
+    torch.cuda.set_device(0)
+    e = synth.grid_edges(64, 48, 96)
+    ws = WarmStart(e, synth.circular_orbit(48, 60.0, incline_deg=20.0), 256, 50.0, max_batch=8)
+    tuned = tsp_autotune(ws.grid, ws.geom)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = ws.train(args.train_samples, batch=8, lr=1e-3, seed0=1000)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+
+    # per-iteration SIRT time and warm-start overhead, timed without error evaluations
+    rho = ws.phantoms([900000])
+    y = ws.measure(rho, [900000])[0]
+    x = torch.zeros_like(rho[0])
+    tsp_sirt(ws.grid, ws.geom, y, x, 1, nonneg=True, workspace=ws.ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    tsp_sirt(ws.grid, ws.geom, y, x, 50, nonneg=True, workspace=ws.ws, reuse_weights=True)
+    e1.record()
+    torch.cuda.synchronize()
+    t_iter = e0.elapsed_time(e1) / 50 / 1e3
+    ws.warm_start(y)
+    e0.record()
+    for _ in range(10):
+        ws.warm_start(y)
+    e1.record()
+    torch.cuda.synchronize()
+    t_warm0 = e0.elapsed_time(e1) / 10 / 1e3
+
+    results = []
+    for i in range(args.eval):
+        s = 900001 + i
+        rho = ws.phantoms([s])
+        y = ws.measure(rho, [s])[0]
+        _, cold, _ = ws.sirt_curve(y, rho[0], torch.zeros_like(rho[0]), args.cap, every=5)
+        x0 = ws.warm_start(y)
+        _, warm, _ = ws.sirt_curve(y, rho[0], x0, max(20, args.cap // 5), every=1)
+        target = args.target if min(cold) <= args.target else min(cold)
+        k_cold = next(5 * j for j, v in enumerate(cold) if v <= target * (1 + 1e-9))
+        k_warm = next((j for j, v in enumerate(warm) if v <= target * (1 + 1e-9)), None)
+        results.append({"seed": s, "target": target, "cold_iters": k_cold, "cold_time_s": k_cold * t_iter,
+                         "cold_err_at_20": cold[4], "cold_best": min(cold),
+                         "warm_iters": k_warm, "warm_time_s": None if k_warm is None else t_warm0 + k_warm * t_iter,
+                         "warm_err_at_0": warm[0], "warm_err_at_20": warm[20]})
+    ok = [r for r in results if r["warm_time_s"] is not None]
+    out = {"metric": "time to target relative error, learned warm start vs plain SIRT", "unit": "s",
+           "higher_is_better": False, "dtype": "bf16 net / f32 projector", "data": "synthetic",
+           "value": float(np.median([r["warm_time_s"] for r in ok])) if ok else None,
+           "cold_value": float(np.median([r["cold_time_s"] for r in results])),
+           "warm_reached": f"{len(ok)}/{len(results)}",
+           "speedup_median": float(np.median([r["cold_time_s"] / r["warm_time_s"] for r in ok])) if ok else None,
+           "sirt_iter_ms": 1e3 * t_iter, "warm_start_overhead_ms": 1e3 * t_warm0,
+           "train": {"samples": args.train_samples, "seconds": t_train, "loss_first": float(np.mean(losses[:20])),
+                     "loss_last": float(np.mean(losses[-20:]))},
+           "config": {"workload": "grid 64x48x96, 48 cone views 256^2, 1% noise", "target": args.target,
+                      "cold_cap": args.cap, "launch_fwd_adj": tuned},
+           "per_phantom": results}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -473,6 +550,8 @@ def main():
         run_batched(args)
     elif args.workload == "differentiation":
         run_differentiation(args)
+    elif args.workload == "warmstart":
+        run_warmstart(args)
     else:
         run_ours(args)
 
