@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-segments", action="store_true", help="skip the stored-segment-list leg")
+    ap.add_argument("--views", type=int, default=0,
+                    help="paper-scale workload: keep only the first N views of each set (small profiling case)")
     ap.add_argument("--workload", choices=["paper_scale", "batched", "differentiation", "warmstart"],
                     default="paper_scale",
                     help="batched: 64 uneven SIRT reconstructions in one captured graph (not the headline metric)")
@@ -220,6 +223,8 @@ def run_ours(args):
     L = _lib.load()
 
     wl = workloads.paper_scale()
+    if args.views:
+        wl.views = [type(v)(v.kind, v.pos[:args.views], v.shape, v.fov_deg, v.size) for v in wl.views]
     grid = Grid.from_edges(wl.edges)
     geoms = [Geometry.cone(v.pos, v.shape, v.fov_deg) if v.kind == "cone" else Geometry.parallel(v.pos, v.shape, v.size)
              for v in wl.views]
@@ -325,6 +330,9 @@ def run_ours(args):
                "d2h_bytes_per_step": d2h}
 
     peaks, peak_kind = measured_peaks()
+    seg_leg = None
+    if not args.no_segments:
+        seg_leg = time_segment_lists(args, grid, geoms, rho, ws, flush, stream, n_rays, n_segs, peaks, dist)
     # dominant kernel: whichever of the forward / adjoint traversals takes longer
     dom = "forward" if t_fwd >= t_adj else "adjoint"
     t_dom_launch = (max(t_fwd, t_adj) / args.steps) / len(geoms) / 1e3  # s per launch
@@ -348,13 +356,89 @@ def run_ours(args):
            "adj_rays_per_s": world * n_rays * args.steps / (t_adj / 1e3),
            "segments_per_s": world * 2 * n_segs * args.steps / (t_tot / 1e3),
            "roofline": roofline, "clocks": clocks, "e2e": e2e,
-           "gpu_launches": 2 * len(geoms) * args.steps, "peaks": peak_kind}
+           "gpu_launches": 2 * len(geoms) * args.steps, "peaks": peak_kind, "segment_lists": seg_leg}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def time_segment_lists(args, grid, geoms, rho, ws, flush, stream, n_rays, n_segs, peaks, dist):
+    """Stored segment lists (steps 1-3 once, step 4 repeated): build time, then
+    the same F + F^T step from the lists, forward as a stream over the
+    ray-major lists and adjoint as a gather over the voxel-major lists.
+    Roofline: HBM, algorithmic bytes = the lists (8 B per segment) + offsets
+    (8 B per ray or voxel) + the output written + the input read once."""
+    import ctypes
+
+    import torch
+
+    from paper_2608_16960_gb300 import _lib
+    from paper_2608_16960_gb300.projector import Segments
+
+    L = _lib.load()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    t0 = time.perf_counter()
+    segs = [Segments(grid, g, transpose=True) for g in geoms]
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    info = [s.info() for s in segs]
+    ys = [torch.empty(g.det_shape, device="cuda") for g in geoms]
+    gs = [torch.empty(grid.shape, device="cuda") for _ in geoms]
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        for s, y in zip(segs, ys):
+            _lib.check(L.tsp_segments_forward(s.handle, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                              1, sp), "tsp_segments_forward")
+        if ev:
+            ev[1].record(stream)
+        for s, w, g in zip(segs, ws, gs):
+            _lib.check(L.tsp_segments_adjoint(s.handle, ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                              1, 0, sp), "tsp_segments_adjoint")
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        step(evs[k])
+    torch.cuda.synchronize()
+    t_fwd = sum(e[0].elapsed_time(e[1]) for e in evs) / 1e3
+    t_adj = sum(e[1].elapsed_time(e[2]) for e in evs) / 1e3
+    world = 1
+    if dist:
+        t = torch.tensor([t_fwd, t_adj], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_fwd, t_adj = (float(v) for v in t.tolist())
+        world = dist.get_world_size()
+    V = grid.voxels
+    fwd_bytes = sum(8 * ns + 8 * (nr + 1) + 4 * nr for nr, ns, _ in info) + 4 * V * len(segs)
+    adj_bytes = sum(8 * ns + 8 * (V + 1) + 4 * V + 4 * nr for nr, ns, _ in info)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bw_f = fwd_bytes * args.steps / t_fwd / 1e9
+    bw_a = adj_bytes * args.steps / t_adj / 1e9
+    dom_f = t_fwd >= t_adj
+    out = {"value": world * n_rays * args.steps / (t_fwd + t_adj), "unit": UNIT,
+           "fwd_rays_per_s": world * n_rays * args.steps / t_fwd, "adj_rays_per_s": world * n_rays * args.steps / t_adj,
+           "ms_per_step": 1e3 * (t_fwd + t_adj) / args.steps, "build_s": t_build,
+           "list_bytes": sum(b for _, _, b in info), "segments": n_segs,
+           "roofline": {"bound": "hbm", "achieved": bw_f if dom_f else bw_a, "peak": hbm, "unit": "GB/s",
+                        "frac": (bw_f if dom_f else bw_a) / hbm, "traffic": None,
+                        "kernel": "seg_stream_kernel (forward, ray-major)" if dom_f else
+                        "row_gather_kernel (adjoint, voxel-major)",
+                        "fwd_gbs": bw_f, "adj_gbs": bw_a, "fwd_frac": bw_f / hbm, "adj_frac": bw_a / hbm},
+           "gpu_launches": 2 * len(segs) * args.steps}
+    del segs
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batched(args):

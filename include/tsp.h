@@ -130,6 +130,61 @@ tsp_status tsp_adjoint_ex(tsp_grid grid, tsp_geom geom, const float* y, float* r
 tsp_status tsp_count_segments(tsp_grid grid, tsp_geom geom, int* counts, void* stream);
 
 /*
+ * Precomputed segment lists (Sec. 3: steps 1-3 done once and stored, step 4
+ * repeated; Sec. 4.4's stored region indices and lengths). The lists are the
+ * valid segments only (Table 2c's zeroed rows dropped), 8 bytes each: uint32
+ * flat voxel index r*N_e*N_a + e*N_a + a and float32 length, ray-major in
+ * order along each ray. With transpose != 0 the build also stores the same
+ * segments voxel-major (uint32 ray index, float32 length), so that the
+ * adjoint is a per-voxel gather instead of a per-segment scatter; the order of
+ * the rays within one voxel's list is unspecified (it comes from atomic slot
+ * claims), so adjoint results may differ run to run by float32 summation
+ * order.
+ *
+ * The segments are those tsp_forward walks: lists and on-the-fly traversal
+ * give the same F up to float32 rounding order. Forward and adjoint read the
+ * lists once per call, coalesced, and sum each ray (voxel) in a fixed order
+ * without atomics, so repeated calls on the same lists give identical
+ * results. Memory: 8 bytes per segment (16 with transpose) plus at most 12
+ * bytes per ray (and per voxel) and 17 bytes per 256 segments per direction;
+ * tsp_segments_info reports it. A handle holds per-call scratch: calls on one
+ * handle must not run concurrently on different streams. Limits: fewer than
+ * 2^31 rays and voxels, fewer than 2^32 segments (TSP_ENOTSUP).
+ */
+typedef struct tsp_segments_s* tsp_segments;
+
+/*
+ * tsp_segments_build - traverses every ray of geom twice (count, then fill)
+ * and builds the lists on grid's device. Synchronises `stream` (it reads the
+ * total segment count back to size the lists). *out receives the handle, or
+ * NULL on error. TSP_ENOMEM/TSP_ECUDA on allocation or launch failure.
+ */
+tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int transpose, tsp_segments* out,
+                              void* stream);
+/* n_rays, n_segments: counts; bytes: device memory held. Any may be NULL. */
+tsp_status tsp_segments_info(tsp_segments s, int64_t* n_rays, int64_t* n_segments, size_t* bytes);
+/*
+ * tsp_segments_export - copies the ray-major lists to HOST buffers (any may be
+ * NULL): ray_off int64 [n_rays + 1] (segments of ray i are [ray_off[i],
+ * ray_off[i+1])), vox uint32 [n_segments], len float32 [n_segments].
+ * Synchronous.
+ */
+tsp_status tsp_segments_export(tsp_segments s, int64_t* ray_off, uint32_t* vox, float* len);
+/*
+ * tsp_segments_forward - y = F rho (Eq. 5) from the stored lists, one pass
+ * over the lists per density. Shapes as tsp_forward; y overwritten.
+ */
+tsp_status tsp_segments_forward(tsp_segments s, const float* rho, float* y, int batch, void* stream);
+/*
+ * tsp_segments_adjoint - rho (+)= F^T y from the stored lists: a gather over
+ * the voxel-major lists when the handle has them, else one atomic add per
+ * segment from the ray-major lists. Shapes and accumulate as tsp_adjoint.
+ */
+tsp_status tsp_segments_adjoint(tsp_segments s, const float* y, float* rho, int batch, int accumulate,
+                                void* stream);
+void tsp_segments_destroy(tsp_segments s);
+
+/*
  * tsp_autotune - times candidate launch knobs (threads per block 64..512, warp
  * tiles 4..32 pixels wide, and for the adjoint the scatter strategy) for this
  * grid and geometry, and caches the fastest per size class (each grid and

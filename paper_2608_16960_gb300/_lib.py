@@ -58,6 +58,12 @@ SIGNATURES = {
     "tsp_adjoint": (_I, [_P, _P, _P, _P, _I, _I, _P]),
     "tsp_adjoint_ex": (_I, [_P, _P, _P, _P, _I, _I, _LP, _P]),
     "tsp_count_segments": (_I, [_P, _P, _P, _P]),
+    "tsp_segments_build": (_I, [_P, _P, _I, ctypes.POINTER(_P), _P]),
+    "tsp_segments_info": (_I, [_P, _I64P, _I64P, ctypes.POINTER(ctypes.c_size_t)]),
+    "tsp_segments_export": (_I, [_P, _P, _P, _P]),
+    "tsp_segments_forward": (_I, [_P, _P, _P, _I, _P]),
+    "tsp_segments_adjoint": (_I, [_P, _P, _P, _I, _I, _P]),
+    "tsp_segments_destroy": (None, [_P]),
     "tsp_sirt_workspace_bytes": (_I, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "tsp_sirt": (_I, [_P, _P, _P, _P, _I, _I, _P, ctypes.c_size_t, _LP, _P]),
     "tsp_sirt_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _P]),

@@ -1,0 +1,723 @@
+// Precomputed segment lists (the paper's steps 1-3 stored once, Sec. 3 and
+// Sec. 4.4's stored region indices and lengths; step 4 repeated): per ray the
+// (voxel, length) pairs of its valid segments in order along the ray,
+// compressed (no padding slots: Eq. 8's padded arrays are not needed), and
+// optionally their transpose per voxel (ray, length). Forward and adjoint on
+// these lists are one streaming kernel over 8 bytes per segment: the lists
+// are read once, coalesced, and multiply an input gathered from L2 (the
+// volume, or the detector values), summed per output row in registers.
+#include "tsp_kernels.cuh"
+
+namespace tsp {
+constexpr int SE = 8;             // entries per lane in the streaming kernel
+constexpr int TILE = 32 * SE;     // entries per warp tile
+constexpr uint32_t HEAD = 0x80000000u;  // bit 31 of a column: first entry of its row
+constexpr uint32_t NO_ROW = 0xFFFFFFFFu;
+}  // namespace tsp
+
+// One direction of the lists: rows (rays or voxels) with their entries
+// (column index with the row-head flag in bit 31, length), the ids of the
+// non-empty rows in order, and per warp tile the number of row heads before
+// it. carry / headless / open_row are per-call scratch of the streaming
+// kernel (one value per tile).
+struct SegList {
+  int64_t n_rows = 0, n_cols = 0, S = 0, n_tiles = 0, n_nz = 0;
+  int64_t* off = nullptr;        // [n_rows + 1] row offsets
+  uint32_t* idx = nullptr;       // [S] column | HEAD on each row's first entry
+  float* len = nullptr;          // [S]
+  uint32_t* nz = nullptr;        // [n_nz] row id of the k-th non-empty row
+  int64_t* tile_base = nullptr;  // [n_tiles + 1] heads before tile t
+  float* carry = nullptr;        // [n_tiles]
+  uint8_t* headless = nullptr;   // [n_tiles]
+  uint32_t* open_row = nullptr;  // [n_tiles]
+};
+
+struct tsp_segments_s {
+  int64_t n_rays = 0, n_segs = 0, V = 0;
+  SegList fwd;  // ray-major: rows = rays, columns = voxels
+  SegList adj;  // voxel-major (transposed): rows = voxels, columns = rays
+  bool has_adj = false;
+  size_t bytes = 0;
+  int device = 0;
+};
+
+namespace tsp {
+namespace {
+
+struct CountOnlyOp {
+  int* __restrict__ counts;
+  int n;
+  __device__ __forceinline__ bool begin(int64_t) {
+    n = 0;
+    return true;
+  }
+  __device__ __forceinline__ void operator()(int, float) { ++n; }
+  __device__ __forceinline__ void end(int64_t ray) { counts[ray] = n; }
+};
+
+// The fill walk repeats the count walk bit for bit (same code, no FMA
+// contraction), so each ray fills exactly its slots; the bound check only
+// guards memory should that ever fail, and flags the error word.
+struct FillOp {
+  const int64_t* __restrict__ off;
+  uint32_t* __restrict__ vox;
+  float* __restrict__ len;
+  int64_t pos, lim;
+  __device__ __forceinline__ bool begin(int64_t ray) {
+    pos = off[ray];
+    first = pos;
+    lim = off[ray + 1];
+    return true;
+  }
+  int64_t first;
+  __device__ __forceinline__ void operator()(int v, float dl) {
+    if (pos < lim) {
+      vox[pos] = uint32_t(v) | (pos == first ? HEAD : 0u);
+      len[pos] = dl;
+    }
+    ++pos;
+  }
+  __device__ __forceinline__ void end(int64_t) {
+    if (pos != lim) atomicOr(&g_tsp_error_word, 2);
+  }
+};
+
+// ---- exclusive scan of int32 counts into int64 offsets (out[n] = total) ----
+constexpr int SCAN_T = 1024, SCAN_E = 2;  // threads, elements per thread
+
+__device__ __forceinline__ int64_t block_incl_scan(int64_t v, int64_t* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < int(blockDim.x >> 5) ? sh[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  if (warp > 0) v += sh[warp - 1];
+  __syncthreads();
+  return v;
+}
+
+__global__ void scan_blocks_kernel(const int* __restrict__ in, int64_t n, int64_t* __restrict__ block_sums) {
+  __shared__ int64_t sh[32];
+  const int64_t base = int64_t(blockIdx.x) * SCAN_T * SCAN_E + int64_t(threadIdx.x) * SCAN_E;
+  int64_t s = 0;
+  for (int k = 0; k < SCAN_E; ++k)
+    if (base + k < n) s += in[base + k];
+  const int64_t incl = block_incl_scan(s, sh);
+  if (threadIdx.x == blockDim.x - 1) block_sums[blockIdx.x] = incl;
+}
+
+// one block: exclusive scan of the block sums in place, total at [nb]
+__global__ void scan_sums_kernel(int64_t* __restrict__ sums, int64_t nb) {
+  __shared__ int64_t sh[32];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t c0 = 0; c0 < nb; c0 += blockDim.x) {
+    const int64_t i = c0 + threadIdx.x;
+    const int64_t v = i < nb ? sums[i] : 0;
+    const int64_t incl = block_incl_scan(v, sh);
+    const int64_t base = carry;
+    if (i < nb) sums[i] = base + incl - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = base + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void scan_final_kernel(const int* __restrict__ in, int64_t n, const int64_t* __restrict__ sums,
+                                  int64_t* __restrict__ out) {
+  __shared__ int64_t sh[32];
+  const int64_t base = int64_t(blockIdx.x) * SCAN_T * SCAN_E + int64_t(threadIdx.x) * SCAN_E;
+  int64_t v[SCAN_E];
+  int64_t s = 0;
+  for (int k = 0; k < SCAN_E; ++k) {
+    v[k] = base + k < n ? in[base + k] : 0;
+    s += v[k];
+  }
+  int64_t run = block_incl_scan(s, sh) - s + sums[blockIdx.x];
+  for (int k = 0; k < SCAN_E; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    int64_t nb = gridDim.x;
+    out[n] = sums[nb];
+  }
+}
+
+tsp_status exclusive_scan(const int* in, int64_t n, int64_t* out, cudaStream_t st) {
+  if (n == 0) {
+    TSP_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
+    return TSP_OK;
+  }
+  const int64_t per = int64_t(SCAN_T) * SCAN_E;
+  const int64_t nb = (n + per - 1) / per;
+  int64_t* sums = nullptr;
+  TSP_CUDA(cudaMallocAsync(&sums, sizeof(int64_t) * size_t(nb + 1), st));
+  scan_blocks_kernel<<<unsigned(nb), SCAN_T, 0, st>>>(in, n, sums);
+  scan_sums_kernel<<<1, 1024, 0, st>>>(sums, nb);
+  scan_final_kernel<<<unsigned(nb), SCAN_T, 0, st>>>(in, n, sums, out);
+  TSP_CUDA(cudaGetLastError());
+  TSP_CUDA(cudaFreeAsync(sums, st));
+  return TSP_OK;
+}
+
+__global__ void voxel_hist_kernel(const uint32_t* __restrict__ vox, int64_t S, int64_t V, int* __restrict__ cnt) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < S; i += int64_t(gridDim.x) * blockDim.x)
+    if ((vox[i] & ~HEAD) < V) atomicAdd(cnt + (vox[i] & ~HEAD), 1);
+}
+
+// warp per ray: scatter its segments into the voxel-major lists
+__global__ void transpose_kernel(const int64_t* __restrict__ ray_off, const uint32_t* __restrict__ vox,
+                                 const float* __restrict__ len, int64_t n_rays, int64_t V,
+                                 unsigned long long* __restrict__ cursor, uint32_t* __restrict__ ray_of,
+                                 float* __restrict__ len_t) {
+  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_rays) return;
+  for (int64_t s = ray_off[w] + lane; s < ray_off[w + 1]; s += 32) {
+    const uint32_t v = vox[s] & ~HEAD;
+    if (v >= V) continue;
+    const unsigned long long p = atomicAdd(cursor + v, 1ull);
+    ray_of[p] = uint32_t(w);
+    len_t[p] = len[s];
+  }
+}
+
+__global__ void i64_to_u64_kernel(const int64_t* __restrict__ a, unsigned long long* __restrict__ b, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    b[i] = (unsigned long long)a[i];
+}
+
+// ---- streaming forward / adjoint ----
+// The lists are read as one flat stream: warp t takes entries [t*TILE,
+// (t+1)*TILE), SE consecutive ones per lane (two 16-byte loads of columns, two
+// of lengths), gathers the input at the SE columns (L2-resident: the volume,
+// or the detector values) and multiplies. Rows are runs of entries that start
+// at a flagged head; a run's row id is nz[rank], its rank counted from the
+// tile's head base plus the heads of earlier lanes. Each lane sums its runs
+// in order; a shuffle scan of (pass-through, value) pairs carries an open run
+// across lanes. Writes (no atomics, every row written by one thread per pass;
+// "+=" when accumulating, a plain store otherwise):
+//  - a run that starts and ends inside the tile: dst[row] (+)= sum;
+//  - the run open at the tile's end (it starts at the tile's last head):
+//    dst[row] (+)= partial, and open_row[t] = row when it continues;
+//  - the piece before the tile's first head: carry[t] (the whole tile when it
+//    has no head: headless[t] = 1).
+// seg_fixup_kernel then adds, for each open row, the carries of the following
+// tiles in order. Rows without entries are left alone (the caller zeroes dst
+// when overwriting). All sums have a fixed order, so results are
+// bit-reproducible.
+template <bool FULL, bool ACC>
+__device__ __forceinline__ void stream_tile(int64_t t, int lane, uint32_t* s_nz, const uint32_t* __restrict__ idx,
+                                            const float* __restrict__ len, int64_t S, uint32_t col_max,
+                                            const uint32_t* __restrict__ nz, int64_t n_nz, int64_t base,
+                                            uint32_t nxt_first, const float* __restrict__ src,
+                                            float* __restrict__ dst, float* __restrict__ carry,
+                                            uint8_t* __restrict__ headless, uint32_t* __restrict__ open_row) {
+  const int64_t T0 = t * TILE, e0 = T0 + int64_t(lane) * SE;
+  uint32_t iv[SE];
+  float lv[SE];
+  if (FULL) {
+    const uint4* pi = reinterpret_cast<const uint4*>(idx + e0);
+    const float4* pl = reinterpret_cast<const float4*>(len + e0);
+#pragma unroll
+    for (int h = 0; h < SE / 4; ++h) {
+      const uint4 a = __ldcs(pi + h);
+      const float4 b = __ldcs(pl + h);
+      iv[4 * h] = a.x, iv[4 * h + 1] = a.y, iv[4 * h + 2] = a.z, iv[4 * h + 3] = a.w;
+      lv[4 * h] = b.x, lv[4 * h + 1] = b.y, lv[4 * h + 2] = b.z, lv[4 * h + 3] = b.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < SE; ++i) {
+      const bool ok = e0 + i < S;
+      iv[i] = ok ? __ldcs(idx + e0 + i) : 0u;
+      lv[i] = ok ? __ldcs(len + e0 + i) : 0.0f;
+    }
+  }
+  // row ids of the ranks this tile can touch (base-1 .. base+30), one coalesced load
+  {
+    const int64_t r = base - 1 + lane;
+    s_nz[lane] = (r >= 0 && r < n_nz) ? nz[r] : NO_ROW;
+  }
+  unsigned heads = 0;
+  float p[SE];
+#pragma unroll
+  for (int i = 0; i < SE; ++i) {
+    heads |= (iv[i] >> 31) << i;
+    p[i] = __ldg(src + min(iv[i] & ~HEAD, col_max));  // the clamp only guards memory: columns are valid
+  }
+#pragma unroll
+  for (int i = 0; i < SE; ++i) p[i] = (FULL || e0 + i < S) ? p[i] * lv[i] : 0.0f;
+  const int nh = __popc(heads);
+  int hb = nh;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, hb, o);
+    if (lane >= o) hb += v;
+  }
+  const int tile_heads = __shfl_sync(0xffffffffu, hb, 31);
+  hb -= nh;
+  __syncwarp();
+  auto row_of = [&](int64_t rank) -> uint32_t {
+    const int64_t i = rank - (base - 1);
+    if (i >= 0 && i < 32) return s_nz[i];
+    if (rank < 0 || rank >= n_nz) {  // inconsistent lists: reported, the write dropped
+      atomicOr(&g_tsp_error_word, 8);
+      return NO_ROW;
+    }
+    return nz[rank];
+  };
+  auto put = [&](uint32_t row, float v) {
+    if (row == NO_ROW) return;
+    if (ACC) dst[row] += v;
+    else dst[row] = v;
+  };
+  // in-lane runs
+  float run = 0.0f, lead = 0.0f;
+  int64_t rk = base + hb - 1;
+  bool seen = false;
+#pragma unroll
+  for (int i = 0; i < SE; ++i) {
+    if ((heads >> i) & 1u) {
+      if (!seen) {
+        lead = run;
+        seen = true;
+      } else {
+        put(row_of(rk), run);  // complete run inside this lane
+      }
+      run = 0.0f;
+      ++rk;
+    }
+    run += p[i];
+  }
+  if (!seen) lead = run;
+  // carry across lanes: lane function x -> seen ? tail : x + lead
+  int c = seen ? 0 : 1;
+  float d = seen ? run : lead;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int cp = __shfl_up_sync(0xffffffffu, c, o);
+    const float dp = __shfl_up_sync(0xffffffffu, d, o);
+    if (lane >= o) {
+      d = c ? dp + d : d;
+      c = cp & c;
+    }
+  }
+  float cin = __shfl_up_sync(0xffffffffu, d, 1);
+  if (lane == 0) cin = 0.0f;
+  const float d_last = __shfl_sync(0xffffffffu, d, 31);
+  if (seen) {
+    const float tot = cin + lead;  // the run closed at this lane's first head
+    if (hb > 0) put(row_of(base + hb - 1), tot);
+    else carry[t] = tot;  // continues a row begun before this tile
+  }
+  if (lane == 31) {
+    if (tile_heads == 0) {
+      carry[t] = d_last;
+      headless[t] = 1;
+      open_row[t] = NO_ROW;
+    } else {
+      const uint32_t row = row_of(base + tile_heads - 1);
+      put(row, d_last);
+      headless[t] = 0;
+      open_row[t] = (nxt_first & HEAD) ? NO_ROW : row;
+    }
+  }
+}
+
+template <bool ACC>
+__global__ void __launch_bounds__(256, 6) seg_stream_kernel(const uint32_t* __restrict__ idx,
+                                                         const float* __restrict__ len, int64_t S, uint32_t n_cols,
+                                                         const uint32_t* __restrict__ nz, int64_t n_nz,
+                                                         const int64_t* __restrict__ tile_base, int64_t n_tiles,
+                                                         const float* __restrict__ src, float* __restrict__ dst,
+                                                         float* __restrict__ carry, uint8_t* __restrict__ headless,
+                                                         uint32_t* __restrict__ open_row) {
+  __shared__ uint32_t s_nz[8][32];
+  const int64_t t = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= n_tiles) return;
+  const int64_t base = tile_base[t];
+  const int64_t nxt = (t + 1) * TILE;
+  const uint32_t nxt_first = (lane == 31 && nxt < S) ? idx[nxt] : HEAD;  // does the next tile open a new row
+  uint32_t* sn = s_nz[threadIdx.x >> 5];
+  if (nxt <= S)
+    stream_tile<true, ACC>(t, lane, sn, idx, len, S, n_cols - 1, nz, n_nz, base, nxt_first, src, dst, carry, headless,
+                           open_row);
+  else
+    stream_tile<false, ACC>(t, lane, sn, idx, len, S, n_cols - 1, nz, n_nz, base, nxt_first, src, dst, carry,
+                            headless, open_row);
+}
+
+// Long rows (voxel-major lists: hundreds of entries per voxel): a warp per row
+// streams the row's entries, U per lane per pass (all U loads issued before
+// the U gathers), and a shuffle tree sums the lanes. Fixed order, no atomics.
+constexpr int RU = 4;
+
+template <int NB>
+__global__ void __launch_bounds__(256) row_gather_kernel(const int64_t* __restrict__ off,
+                                                         const uint32_t* __restrict__ idx,
+                                                         const float* __restrict__ len, int64_t n_rows,
+                                                         uint32_t col_max, const float* __restrict__ src,
+                                                         int64_t src_stride, float* __restrict__ dst,
+                                                         int64_t dst_stride, int nb, int accumulate) {
+  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_rows) return;
+  float acc[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) acc[b] = 0.0f;
+  const int64_t s1 = off[w + 1];
+  for (int64_t s = off[w] + lane; s < s1; s += 32 * RU) {
+    uint32_t i[RU];
+    float l[RU];
+#pragma unroll
+    for (int k = 0; k < RU; ++k) {
+      const int64_t sk = s + 32 * k;
+      i[k] = sk < s1 ? min(__ldcs(idx + sk) & ~HEAD, col_max) : 0u;
+      l[k] = sk < s1 ? __ldcs(len + sk) : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < RU; ++k)
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (b < nb) acc[b] = fmaf(__ldg(src + b * src_stride + i[k]), l[k], acc[b]);
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    float v = acc[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0 && b < nb) {
+      float* p = dst + b * dst_stride + w;
+      *p = accumulate ? *p + v : v;
+    }
+  }
+}
+
+// dst[row] += the carries of the tiles after t that continue the row open at
+// t's end, in tile order.
+__global__ void seg_fixup_kernel(const float* __restrict__ carry, const uint8_t* __restrict__ headless,
+                                 const uint32_t* __restrict__ open_row, int64_t n_tiles, float* __restrict__ dst) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  const uint32_t row = open_row[t];
+  if (row == NO_ROW) return;
+  float v = 0.0f;
+  for (int64_t k = t + 1; k < n_tiles; ++k) {
+    v += carry[k];
+    if (!headless[k]) break;
+  }
+  dst[row] += v;
+}
+
+// adjoint without the transposed lists: one atomic per segment
+__global__ void seg_scatter_kernel(const int64_t* __restrict__ off, const uint32_t* __restrict__ vox,
+                                   const float* __restrict__ len, const float* __restrict__ y, float* __restrict__ g,
+                                   int64_t n_rays) {
+  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_rays) return;
+  const float yv = y[w];
+  if (yv == 0.0f) return;
+  for (int64_t s = off[w] + lane; s < off[w + 1]; s += 32) atomicAdd(g + (vox[s] & ~HEAD), yv * len[s]);
+}
+
+// Rows at least this long on average take the warp-per-row kernel.
+constexpr int64_t LONG_ROWS = 256;
+
+// dst (+)= lists x src: long rows a warp each (up to 4 right-hand sides per
+// pass over the lists), short rows by the flat stream (one per pass).
+tsp_status rows_apply(const SegList& l, const float* src, int64_t src_stride, float* dst, int64_t dst_stride, int nb,
+                      int accumulate, cudaStream_t st) {
+  if (l.S >= LONG_ROWS * l.n_rows) {
+    const unsigned blocks = unsigned((l.n_rows * 32 + 255) / 256);
+    for (int b0 = 0; b0 < nb; b0 += 4) {
+      const int k = std::min(4, nb - b0);
+      const float* sp = src + b0 * src_stride;
+      float* dp = dst + b0 * dst_stride;
+      if (k == 1)
+        row_gather_kernel<1><<<blocks, 256, 0, st>>>(l.off, l.idx, l.len, l.n_rows, uint32_t(l.n_cols - 1), sp,
+                                                     src_stride, dp, dst_stride, 1, accumulate);
+      else
+        row_gather_kernel<4><<<blocks, 256, 0, st>>>(l.off, l.idx, l.len, l.n_rows, uint32_t(l.n_cols - 1), sp,
+                                                     src_stride, dp, dst_stride, k, accumulate);
+    }
+    TSP_CUDA(cudaGetLastError());
+    return TSP_OK;
+  }
+  if (!accumulate) {
+    if (dst_stride == l.n_rows) {
+      TSP_CUDA(cudaMemsetAsync(dst, 0, sizeof(float) * size_t(l.n_rows) * nb, st));
+    } else {
+      for (int b = 0; b < nb; ++b)
+        TSP_CUDA(cudaMemsetAsync(dst + b * dst_stride, 0, sizeof(float) * size_t(l.n_rows), st));
+    }
+  }
+  if (l.n_tiles == 0) return TSP_OK;
+  const unsigned blocks = unsigned((l.n_tiles * 32 + 255) / 256);
+  const unsigned fix_blocks = unsigned((l.n_tiles + 255) / 256);
+  for (int b = 0; b < nb; ++b) {
+    if (accumulate)
+      seg_stream_kernel<true><<<blocks, 256, 0, st>>>(l.idx, l.len, l.S, uint32_t(l.n_cols), l.nz, l.n_nz,
+                                                      l.tile_base, l.n_tiles, src + b * src_stride,
+                                                      dst + b * dst_stride, l.carry, l.headless, l.open_row);
+    else
+      seg_stream_kernel<false><<<blocks, 256, 0, st>>>(l.idx, l.len, l.S, uint32_t(l.n_cols), l.nz, l.n_nz,
+                                                       l.tile_base, l.n_tiles, src + b * src_stride,
+                                                       dst + b * dst_stride, l.carry, l.headless, l.open_row);
+    seg_fixup_kernel<<<fix_blocks, 256, 0, st>>>(l.carry, l.headless, l.open_row, l.n_tiles, dst + b * dst_stride);
+  }
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
+__global__ void nonempty_flags_kernel(const int64_t* __restrict__ off, int64_t n_rows, int* __restrict__ flag) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r < n_rows) flag[r] = off[r + 1] > off[r] ? 1 : 0;
+}
+
+__global__ void nonempty_ids_kernel(const int64_t* __restrict__ off, const int64_t* __restrict__ pos, int64_t n_rows,
+                                    uint32_t* __restrict__ nz) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r < n_rows && off[r + 1] > off[r]) nz[pos[r]] = uint32_t(r);
+}
+
+__global__ void tile_heads_kernel(const uint32_t* __restrict__ idx, int64_t S, int64_t n_tiles, int* __restrict__ cnt) {
+  const int64_t t = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= n_tiles) return;
+  int c = 0;
+  for (int i = 0; i < SE; ++i) {
+    const int64_t e = t * TILE + int64_t(lane) * SE + i;
+    if (e < S) c += int(idx[e] >> 31);
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if (lane == 0) cnt[t] = c;
+}
+
+__global__ void mark_heads_kernel(const int64_t* __restrict__ off, int64_t n_rows, uint32_t* __restrict__ idx) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r < n_rows && off[r + 1] > off[r]) idx[off[r]] |= HEAD;
+}
+
+// Non-empty row ids, tile head bases and the per-call scratch of one
+// direction, once its offsets and (flagged) entries exist. `tmp` holds at
+// least max(n_rows, n_tiles) ints, `pos` n_rows + 1 int64.
+tsp_status finish_list(SegList& l, int* tmp, int64_t* pos, cudaStream_t st) {
+  const unsigned rb = unsigned((l.n_rows + 255) / 256);
+  nonempty_flags_kernel<<<rb, 256, 0, st>>>(l.off, l.n_rows, tmp);
+  tsp_status r = exclusive_scan(tmp, l.n_rows, pos, st);
+  if (r != TSP_OK) return r;
+  TSP_CUDA(cudaMemcpyAsync(&l.n_nz, pos + l.n_rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  TSP_CUDA(cudaStreamSynchronize(st));
+  TSP_CUDA(cudaMalloc(&l.nz, sizeof(uint32_t) * size_t(l.n_nz > 0 ? l.n_nz : 1)));
+  nonempty_ids_kernel<<<rb, 256, 0, st>>>(l.off, pos, l.n_rows, l.nz);
+  l.n_tiles = (l.S + TILE - 1) / TILE;
+  const size_t nt = size_t(l.n_tiles > 0 ? l.n_tiles : 1);
+  TSP_CUDA(cudaMalloc(&l.tile_base, sizeof(int64_t) * (nt + 1)));
+  TSP_CUDA(cudaMalloc(&l.carry, sizeof(float) * nt));
+  TSP_CUDA(cudaMalloc(&l.headless, nt));
+  TSP_CUDA(cudaMalloc(&l.open_row, sizeof(uint32_t) * nt));
+  if (l.n_tiles > 0) {
+    tile_heads_kernel<<<unsigned((l.n_tiles * 32 + 255) / 256), 256, 0, st>>>(l.idx, l.S, l.n_tiles, tmp);
+    r = exclusive_scan(tmp, l.n_tiles, l.tile_base, st);
+    if (r != TSP_OK) return r;
+  }
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
+size_t entries_alloc(int64_t S) { return size_t(S > 0 ? S : 1); }
+
+void free_list(SegList& l) {
+  cudaFree(l.off);
+  cudaFree(l.idx);
+  cudaFree(l.len);
+  cudaFree(l.nz);
+  cudaFree(l.tile_base);
+  cudaFree(l.carry);
+  cudaFree(l.headless);
+  cudaFree(l.open_row);
+  l = SegList();
+}
+
+size_t list_bytes(const SegList& l) {
+  if (!l.off) return 0;
+  const size_t nt = size_t(l.n_tiles > 0 ? l.n_tiles : 1);
+  return sizeof(int64_t) * size_t(l.n_rows + 1) + 8 * entries_alloc(l.S) + 4 * size_t(l.n_nz > 0 ? l.n_nz : 1) +
+         nt * (8 + 4 + 1 + 4) + 8;
+}
+
+}  // namespace
+}  // namespace tsp
+
+using namespace tsp;
+
+extern "C" void tsp_segments_destroy(tsp_segments s) {
+  if (!s) return;
+  free_list(s->fwd);
+  free_list(s->adj);
+  delete s;
+}
+
+extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int transpose, tsp_segments* out,
+                                         void* stream) {
+  if (!out) return fail(TSP_EINVAL, "tsp_segments_build: out is NULL");
+  *out = nullptr;
+  tsp_status st = check_trace_args(grid, geom, grid, geom, 1, nullptr, "tsp_segments_build");
+  if (st != TSP_OK) return st;
+  if (geom->n_rays >= (int64_t(1) << 31) || grid->voxels() >= (int64_t(1) << 31))
+    return fail(TSP_ENOTSUP, "tsp_segments_build: 2^31 or more rays or voxels");
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  tsp_segments s = new (std::nothrow) tsp_segments_s();
+  if (!s) return fail(TSP_ENOMEM, "tsp_segments_build: host allocation");
+  s->n_rays = geom->n_rays;
+  s->V = grid->voxels();
+  s->device = grid->device;
+  int* counts = nullptr;
+  int* vcount = nullptr;
+  int* tmp = nullptr;
+  int64_t* pos = nullptr;
+  unsigned long long* cursor = nullptr;
+  auto release = [&]() {
+    cudaFree(counts);
+    cudaFree(vcount);
+    cudaFree(tmp);
+    cudaFree(pos);
+    cudaFree(cursor);
+    counts = vcount = tmp = nullptr;
+    pos = nullptr;
+    cursor = nullptr;
+  };
+  auto bail = [&](tsp_status r) {
+    cudaStreamSynchronize(cs);
+    release();
+    tsp_segments_destroy(s);
+    return r;
+  };
+#define SEG_TRY(call)                                     \
+  do {                                                    \
+    cudaError_t e__ = (call);                             \
+    if (e__ != cudaSuccess) return bail(cuda_fail(e__, #call)); \
+  } while (0)
+  SegList& f = s->fwd;
+  f.n_rows = s->n_rays;
+  f.n_cols = s->V;
+  SEG_TRY(cudaMalloc(&counts, sizeof(int) * size_t(s->n_rays)));
+  SEG_TRY(cudaMalloc(&f.off, sizeof(int64_t) * size_t(s->n_rays + 1)));
+  const tsp_launch l = preferred_launch(grid, geom, false);
+  CountOnlyOp cop;
+  cop.counts = counts;
+  launch_trace(grid, geom, l, cop, cs);
+  st = exclusive_scan(counts, s->n_rays, f.off, cs);
+  if (st != TSP_OK) return bail(st);
+  SEG_TRY(cudaMemcpyAsync(&s->n_segs, f.off + s->n_rays, sizeof(int64_t), cudaMemcpyDeviceToHost, cs));
+  SEG_TRY(cudaStreamSynchronize(cs));
+  if (s->n_segs >= (int64_t(1) << 32)) return bail(fail(TSP_ENOTSUP, "tsp_segments_build: 2^32 or more segments"));
+  f.S = s->n_segs;
+  const size_t P = entries_alloc(s->n_segs);
+  SEG_TRY(cudaMalloc(&f.idx, sizeof(uint32_t) * P));
+  SEG_TRY(cudaMalloc(&f.len, sizeof(float) * P));
+  SEG_TRY(cudaMemsetAsync(f.idx, 0, sizeof(uint32_t) * P, cs));  // no stray head flags in unfilled slots
+  FillOp fop;
+  fop.off = f.off;
+  fop.vox = f.idx;
+  fop.len = f.len;
+  launch_trace(grid, geom, l, fop, cs);
+  SEG_TRY(cudaGetLastError());
+  const int64_t rows_max = std::max<int64_t>(s->n_rays, s->V);
+  SEG_TRY(cudaMalloc(&tmp, sizeof(int) * size_t(std::max<int64_t>(rows_max, (s->n_segs + TILE - 1) / TILE + 1))));
+  SEG_TRY(cudaMalloc(&pos, sizeof(int64_t) * size_t(rows_max + 1)));
+  st = finish_list(f, tmp, pos, cs);
+  if (st != TSP_OK) return bail(st);
+  if (transpose) {
+    SegList& t = s->adj;
+    t.n_rows = s->V;
+    t.n_cols = s->n_rays;
+    t.S = s->n_segs;
+    SEG_TRY(cudaMalloc(&vcount, sizeof(int) * size_t(s->V)));
+    SEG_TRY(cudaMalloc(&cursor, sizeof(unsigned long long) * size_t(s->V)));
+    SEG_TRY(cudaMalloc(&t.off, sizeof(int64_t) * size_t(s->V + 1)));
+    SEG_TRY(cudaMalloc(&t.idx, sizeof(uint32_t) * P));
+    SEG_TRY(cudaMalloc(&t.len, sizeof(float) * P));
+    SEG_TRY(cudaMemsetAsync(vcount, 0, sizeof(int) * size_t(s->V), cs));
+    SEG_TRY(cudaMemsetAsync(t.idx, 0, sizeof(uint32_t) * P, cs));
+    voxel_hist_kernel<<<152 * 16, 256, 0, cs>>>(f.idx, s->n_segs, s->V, vcount);
+    st = exclusive_scan(vcount, s->V, t.off, cs);
+    if (st != TSP_OK) return bail(st);
+    i64_to_u64_kernel<<<152 * 4, 256, 0, cs>>>(t.off, cursor, s->V);
+    transpose_kernel<<<unsigned((s->n_rays * 32 + 255) / 256), 256, 0, cs>>>(f.off, f.idx, f.len, s->n_rays, s->V,
+                                                                            cursor, t.idx, t.len);
+    mark_heads_kernel<<<unsigned((s->V + 255) / 256), 256, 0, cs>>>(t.off, s->V, t.idx);
+    SEG_TRY(cudaGetLastError());
+    st = finish_list(t, tmp, pos, cs);
+    if (st != TSP_OK) return bail(st);
+    s->has_adj = true;
+  }
+  SEG_TRY(cudaStreamSynchronize(cs));
+  release();
+#undef SEG_TRY
+  s->bytes = list_bytes(s->fwd) + list_bytes(s->adj);
+  *out = s;
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_segments_info(tsp_segments s, int64_t* n_rays, int64_t* n_segments, size_t* bytes) {
+  if (!s) return fail(TSP_EINVAL, "tsp_segments_info: NULL handle");
+  if (n_rays) *n_rays = s->n_rays;
+  if (n_segments) *n_segments = s->n_segs;
+  if (bytes) *bytes = s->bytes;
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_segments_export(tsp_segments s, int64_t* ray_off, uint32_t* vox, float* len) {
+  if (!s) return fail(TSP_EINVAL, "tsp_segments_export: NULL handle");
+  tsp_status st = check_device(s->device);
+  if (st != TSP_OK) return st;
+  if (ray_off)
+    TSP_CUDA(cudaMemcpy(ray_off, s->fwd.off, sizeof(int64_t) * size_t(s->n_rays + 1), cudaMemcpyDeviceToHost));
+  if (vox && s->n_segs) {
+    TSP_CUDA(cudaMemcpy(vox, s->fwd.idx, sizeof(uint32_t) * size_t(s->n_segs), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < s->n_segs; ++i) vox[i] &= ~HEAD;
+  }
+  if (len && s->n_segs) TSP_CUDA(cudaMemcpy(len, s->fwd.len, sizeof(float) * size_t(s->n_segs), cudaMemcpyDeviceToHost));
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_segments_forward(tsp_segments s, const float* rho, float* y, int batch, void* stream) {
+  if (!s || !rho || !y || batch <= 0) return fail(TSP_EINVAL, "tsp_segments_forward: bad argument");
+  tsp_status st = check_device(s->device);
+  if (st != TSP_OK) return st;
+  return rows_apply(s->fwd, rho, s->V, y, s->n_rays, batch, 0, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" tsp_status tsp_segments_adjoint(tsp_segments s, const float* y, float* rho, int batch, int accumulate,
+                                           void* stream) {
+  if (!s || !y || !rho || batch <= 0) return fail(TSP_EINVAL, "tsp_segments_adjoint: bad argument");
+  tsp_status st = check_device(s->device);
+  if (st != TSP_OK) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  if (s->has_adj) return rows_apply(s->adj, y, s->n_rays, rho, s->V, batch, accumulate, cs);
+  if (!accumulate) TSP_CUDA(cudaMemsetAsync(rho, 0, sizeof(float) * size_t(s->V) * batch, cs));
+  for (int b = 0; b < batch; ++b)
+    seg_scatter_kernel<<<unsigned((s->n_rays * 32 + 255) / 256), 256, 0, cs>>>(s->fwd.off, s->fwd.idx, s->fwd.len,
+                                                                              y + b * s->n_rays, rho + b * s->V,
+                                                                              s->n_rays);
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}

@@ -244,6 +244,80 @@ def tsp_count_segments(grid: Grid, geom: Geometry) -> torch.Tensor:
     return counts
 
 
+class Segments:
+    """Stored segment lists of one grid and geometry (Sec. 3 steps 1-3 kept,
+    step 4 repeated): forward and adjoint stream 8 bytes per segment instead
+    of re-tracing. transpose=True also keeps voxel-major lists, so that the
+    adjoint gathers per voxel without atomics (twice the memory)."""
+
+    def __init__(self, grid: Grid, geom: Geometry, transpose: bool = True):
+        L = _lib.load()
+        self.grid, self.geom = grid, geom
+        h = ctypes.c_void_p()
+        st = torch.cuda.current_stream(torch.device("cuda", geom.device)).cuda_stream
+        check(L.tsp_segments_build(grid.handle, geom.handle, int(transpose), ctypes.byref(h), ctypes.c_void_p(st)),
+              "tsp_segments_build")
+        self.handle = h
+
+    def info(self):
+        """(n_rays, n_segments, device bytes)."""
+        L = _lib.load()
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_size_t()
+        check(L.tsp_segments_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+              "tsp_segments_info")
+        return a.value, b.value, c.value
+
+    def export(self):
+        """Host copies (ray_off int64, vox uint32, len float32) of the ray-major lists."""
+        n_rays, n_segs, _ = self.info()
+        off = np.zeros(n_rays + 1, dtype=np.int64)
+        vox = np.zeros(max(n_segs, 1), dtype=np.uint32)
+        ln = np.zeros(max(n_segs, 1), dtype=np.float32)
+        vp = lambda a: ctypes.c_void_p(a.ctypes.data)
+        check(_lib.load().tsp_segments_export(self.handle, vp(off), vp(vox), vp(ln)), "tsp_segments_export")
+        return off, vox[:n_segs], ln[:n_segs]
+
+    def forward(self, rho: torch.Tensor) -> torch.Tensor:
+        _require_cuda(rho, "rho")
+        if tuple(rho.shape[-3:]) != self.grid.shape or rho.dim() not in (3, 4):
+            raise ValueError(f"rho shape {tuple(rho.shape)} does not match grid {self.grid.shape}")
+        rho = rho.contiguous()
+        B = rho.shape[0] if rho.dim() == 4 else 1
+        y = torch.empty((B,) + self.geom.det_shape, device=rho.device, dtype=torch.float32)
+        check(_lib.load().tsp_segments_forward(self.handle, ctypes.c_void_p(rho.data_ptr()),
+                                               ctypes.c_void_p(y.data_ptr()), B, _stream(rho)),
+              "tsp_segments_forward")
+        return y if rho.dim() == 4 else y[0]
+
+    def adjoint(self, y: torch.Tensor, out: torch.Tensor | None = None, accumulate: bool = False) -> torch.Tensor:
+        _require_cuda(y, "y")
+        nd = len(self.geom.det_shape)
+        if tuple(y.shape[-nd:]) != self.geom.det_shape or y.dim() not in (nd, nd + 1):
+            raise ValueError(f"y shape {tuple(y.shape)} does not match geometry {self.geom.det_shape}")
+        y = y.contiguous()
+        B = y.shape[0] if y.dim() == nd + 1 else 1
+        if out is None:
+            out = torch.empty((B,) + self.grid.shape, device=y.device, dtype=torch.float32)
+            accumulate = False
+        else:
+            _require_cuda(out, "out")
+            if out.numel() != B * self.grid.voxels or not out.is_contiguous():
+                raise ValueError("out has the wrong size or is not contiguous")
+        check(_lib.load().tsp_segments_adjoint(self.handle, ctypes.c_void_p(y.data_ptr()),
+                                               ctypes.c_void_p(out.data_ptr()), B, int(accumulate), _stream(y)),
+              "tsp_segments_adjoint")
+        return out.view((B,) + self.grid.shape) if y.dim() == nd + 1 else out.view(self.grid.shape)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _lib.load(build_if_missing=False).tsp_segments_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
 def tsp_device_status(device_tensor: torch.Tensor | None = None) -> int:
     L = _lib.load()
     code = ctypes.c_int(0)
