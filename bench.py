@@ -563,12 +563,13 @@ def run_warmstart(args):
     import torch
 
     from paper_2608_16960_gb300 import synth
-    from paper_2608_16960_gb300.projector import tsp_autotune, tsp_sirt
+    from paper_2608_16960_gb300.projector import tsp_autotune
     from paper_2608_16960_gb300.warmstart import WarmStart
 
     torch.cuda.set_device(0)
     e = synth.grid_edges(64, 48, 96)
-    ws = WarmStart(e, synth.circular_orbit(48, 60.0, incline_deg=20.0), 256, 50.0, max_batch=8)
+    ws = WarmStart(e, synth.circular_orbit(48, 60.0, incline_deg=20.0), 256, 50.0, max_batch=8,
+                   use_lists=not args.no_segments)
     tuned = tsp_autotune(ws.grid, ws.geom)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -580,10 +581,10 @@ def run_warmstart(args):
     rho = ws.phantoms([900000])
     y = ws.measure(rho, [900000])[0]
     x = torch.zeros_like(rho[0])
-    tsp_sirt(ws.grid, ws.geom, y, x, 1, nonneg=True, workspace=ws.ws)
+    ws.sirt(y, x, 1, reuse_weights=False)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    tsp_sirt(ws.grid, ws.geom, y, x, 50, nonneg=True, workspace=ws.ws, reuse_weights=True)
+    ws.sirt(y, x, 50, reuse_weights=True)
     e1.record()
     torch.cuda.synchronize()
     t_iter = e0.elapsed_time(e1) / 50 / 1e3
@@ -621,7 +622,8 @@ def run_warmstart(args):
            "train": {"samples": args.train_samples, "seconds": t_train, "loss_first": float(np.mean(losses[:20])),
                      "loss_last": float(np.mean(losses[-20:]))},
            "config": {"workload": "grid 64x48x96, 48 cone views 256^2, 1% noise", "target": args.target,
-                      "cold_cap": args.cap, "launch_fwd_adj": tuned},
+                      "cold_cap": args.cap, "launch_fwd_adj": tuned,
+                      "sirt_projections": "on-the-fly traversal" if args.no_segments else "stored segment lists"},
            "per_phantom": results}
     print(json.dumps(out), flush=True)
 

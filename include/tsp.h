@@ -182,6 +182,18 @@ tsp_status tsp_segments_forward(tsp_segments s, const float* rho, float* y, int 
  */
 tsp_status tsp_segments_adjoint(tsp_segments s, const float* y, float* rho, int batch, int accumulate,
                                 void* stream);
+/*
+ * tsp_segments_sirt - tsp_sirt (same update, weights and flags) with every
+ * projection taken from the stored lists. The workspace needs
+ * tsp_segments_sirt_workspace_bytes() bytes (the same as tsp_sirt's for the
+ * grid and geometry the lists were built from), 256-byte aligned; with
+ * TSP_SIRT_REUSE_WEIGHTS it must hold the weights of an earlier call on the
+ * same lists. Per iteration: forward, residual, adjoint, update (plus the
+ * lists' fixup and memset launches). No host synchronisation.
+ */
+tsp_status tsp_segments_sirt_workspace_bytes(tsp_segments s, size_t* bytes);
+tsp_status tsp_segments_sirt(tsp_segments s, const float* y, float* x, int n_iter, int flags,
+                             void* workspace, size_t workspace_bytes, void* stream);
 void tsp_segments_destroy(tsp_segments s);
 
 /*

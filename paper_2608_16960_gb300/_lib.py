@@ -63,6 +63,8 @@ SIGNATURES = {
     "tsp_segments_export": (_I, [_P, _P, _P, _P]),
     "tsp_segments_forward": (_I, [_P, _P, _P, _I, _P]),
     "tsp_segments_adjoint": (_I, [_P, _P, _P, _I, _I, _P]),
+    "tsp_segments_sirt_workspace_bytes": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "tsp_segments_sirt": (_I, [_P, _P, _P, _I, _I, _P, ctypes.c_size_t, _P]),
     "tsp_segments_destroy": (None, [_P]),
     "tsp_sirt_workspace_bytes": (_I, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "tsp_sirt": (_I, [_P, _P, _P, _P, _I, _I, _P, ctypes.c_size_t, _LP, _P]),

@@ -542,6 +542,40 @@ tsp_status finish_list(SegList& l, int* tmp, int64_t* pos, cudaStream_t st) {
   return TSP_OK;
 }
 
+// ---- SIRT on the stored lists (same update as tsp_sirt) ----
+__global__ void fill_kernel(float* __restrict__ a, int64_t n, float v) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    a[i] = v;
+}
+
+// a[i] = 1 / a[i], 0 where a[i] <= 0 (rays missing the grid, voxels no ray meets)
+__global__ void recip_kernel(float* __restrict__ a, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const float v = a[i];
+    a[i] = v > 0.0f ? __frcp_rn(v) : 0.0f;
+  }
+}
+
+// r = R * (y - f), in place over f
+__global__ void residual_kernel(float* __restrict__ f, const float* __restrict__ y, const float* __restrict__ R,
+                                int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    f[i] = __fmul_rn(R[i], __fsub_rn(y[i], f[i]));
+}
+
+// x += C * g, clamped at 0 if asked
+__global__ void xupdate_kernel(float* __restrict__ x, const float* __restrict__ g, const float* __restrict__ C,
+                               int64_t n, int nonneg) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    float v = fmaf(C[i], g[i], x[i]);
+    if (nonneg) v = fmaxf(v, 0.0f);
+    x[i] = v;
+  }
+}
+
+unsigned ew_blocks(int64_t n) { return unsigned(std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
 size_t entries_alloc(int64_t S) { return size_t(S > 0 ? S : 1); }
 
 void free_list(SegList& l) {
@@ -718,6 +752,55 @@ extern "C" tsp_status tsp_segments_adjoint(tsp_segments s, const float* y, float
     seg_scatter_kernel<<<unsigned((s->n_rays * 32 + 255) / 256), 256, 0, cs>>>(s->fwd.off, s->fwd.idx, s->fwd.len,
                                                                               y + b * s->n_rays, rho + b * s->V,
                                                                               s->n_rays);
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_segments_sirt_workspace_bytes(tsp_segments s, size_t* bytes) {
+  if (!s || !bytes) return fail(TSP_EINVAL, "tsp_segments_sirt_workspace_bytes: NULL argument");
+  *bytes = 2 * align256(sizeof(float) * size_t(s->n_rays)) + 2 * align256(sizeof(float) * size_t(s->V));
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_segments_sirt(tsp_segments s, const float* y, float* x, int n_iter, int flags,
+                                        void* workspace, size_t workspace_bytes, void* stream) {
+  if (!s || !y || !x || !workspace) return fail(TSP_EINVAL, "tsp_segments_sirt: NULL argument");
+  if (n_iter < 0) return fail(TSP_EINVAL, "tsp_segments_sirt: n_iter < 0");
+  if (flags & ~(TSP_SIRT_NONNEG | TSP_SIRT_REUSE_WEIGHTS)) return fail(TSP_EINVAL, "tsp_segments_sirt: unknown flags");
+  if (reinterpret_cast<uintptr_t>(workspace) & 255u) return fail(TSP_EINVAL, "tsp_segments_sirt: workspace not 256-byte aligned");
+  size_t need = 0;
+  tsp_segments_sirt_workspace_bytes(s, &need);
+  if (workspace_bytes < need)
+    return fail(TSP_EINVAL, "tsp_segments_sirt: workspace of " + std::to_string(workspace_bytes) + " bytes, " +
+                                std::to_string(need) + " needed");
+  tsp_status st = check_device(s->device);
+  if (st != TSP_OK) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const int64_t nr = s->n_rays, V = s->V;
+  char* p = static_cast<char*>(workspace);
+  float* R = reinterpret_cast<float*>(p);
+  float* r = reinterpret_cast<float*>(p + align256(4 * size_t(nr)));
+  float* C = reinterpret_cast<float*>(p + 2 * align256(4 * size_t(nr)));
+  float* g = reinterpret_cast<float*>(p + 2 * align256(4 * size_t(nr)) + align256(4 * size_t(V)));
+  if (!(flags & TSP_SIRT_REUSE_WEIGHTS)) {
+    // R = 1 / (F 1), C = 1 / (F^T 1)
+    fill_kernel<<<ew_blocks(V), 256, 0, cs>>>(g, V, 1.0f);
+    st = rows_apply(s->fwd, g, V, R, nr, 1, 0, cs);
+    if (st != TSP_OK) return st;
+    recip_kernel<<<ew_blocks(nr), 256, 0, cs>>>(R, nr);
+    fill_kernel<<<ew_blocks(nr), 256, 0, cs>>>(r, nr, 1.0f);
+    st = s->has_adj ? rows_apply(s->adj, r, nr, C, V, 1, 0, cs) : tsp_segments_adjoint(s, r, C, 1, 0, stream);
+    if (st != TSP_OK) return st;
+    recip_kernel<<<ew_blocks(V), 256, 0, cs>>>(C, V);
+  }
+  for (int it = 0; it < n_iter; ++it) {
+    st = rows_apply(s->fwd, x, V, r, nr, 1, 0, cs);  // r = F x
+    if (st != TSP_OK) return st;
+    residual_kernel<<<ew_blocks(nr), 256, 0, cs>>>(r, y, R, nr);
+    st = tsp_segments_adjoint(s, r, g, 1, 0, stream);  // g = F^T r
+    if (st != TSP_OK) return st;
+    xupdate_kernel<<<ew_blocks(V), 256, 0, cs>>>(x, g, C, V, flags & TSP_SIRT_NONNEG);
+  }
   TSP_CUDA(cudaGetLastError());
   return TSP_OK;
 }

@@ -308,6 +308,28 @@ class Segments:
               "tsp_segments_adjoint")
         return out.view((B,) + self.grid.shape) if y.dim() == nd + 1 else out.view(self.grid.shape)
 
+    def sirt_workspace(self) -> torch.Tensor:
+        n = ctypes.c_size_t()
+        check(_lib.load().tsp_segments_sirt_workspace_bytes(self.handle, ctypes.byref(n)),
+              "tsp_segments_sirt_workspace_bytes")
+        return torch.empty(n.value, dtype=torch.uint8, device=torch.device("cuda", self.geom.device))
+
+    def sirt(self, y: torch.Tensor, x: torch.Tensor, n_iter: int, nonneg: bool = False,
+             workspace: torch.Tensor | None = None, reuse_weights: bool = False) -> torch.Tensor:
+        """n_iter SIRT updates of x in place (as tsp_sirt), projections from the lists."""
+        _require_cuda(y, "y")
+        _require_cuda(x, "x")
+        if x.numel() != self.grid.voxels or y.numel() != self.geom.n_rays:
+            raise ValueError("x must match the grid and y the geometry")
+        if reuse_weights and workspace is None:
+            raise ValueError("reuse_weights needs the workspace of an earlier call")
+        ws = self.sirt_workspace() if workspace is None else workspace
+        flags = (_lib.TSP_SIRT_NONNEG if nonneg else 0) | (_lib.TSP_SIRT_REUSE_WEIGHTS if reuse_weights else 0)
+        check(_lib.load().tsp_segments_sirt(self.handle, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                            int(n_iter), flags, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                            _stream(x)), "tsp_segments_sirt")
+        return x
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value:

@@ -19,7 +19,7 @@ import torch
 from . import _lib, synth
 from ._lib import check
 from .model import WarmStartNet
-from .projector import Geometry, Grid, sirt_workspace, tsp_adjoint, tsp_forward, tsp_sirt
+from .projector import Geometry, Grid, Segments, sirt_workspace, tsp_adjoint, tsp_forward, tsp_sirt
 
 MAX_BLOBS = 8
 
@@ -33,7 +33,7 @@ def _st():
 
 
 class WarmStart:
-    def __init__(self, edges, pos, det, fov_deg, max_batch=8, noise_frac=0.01):
+    def __init__(self, edges, pos, det, fov_deg, max_batch=8, noise_frac=0.01, use_lists=False):
         self.edges = edges
         self.grid = Grid.from_edges(edges)
         self.geom = Geometry.cone(pos, (det, det), fov_deg)
@@ -47,7 +47,9 @@ class WarmStart:
         self.C = torch.empty(self.shape, device="cuda")
         check(L.tsp_sirt_weights(self.grid.handle, self.geom.handle, _p(self.R), _p(self.C), _st()), "tsp_sirt_weights")
         self.mask = self.C > 0  # voxels some ray crosses
-        self.ws = sirt_workspace(self.grid, self.geom)
+        # SIRT projections: stored segment lists (steps 1-3 once) or on-the-fly traversal
+        self.segs = Segments(self.grid, self.geom) if use_lists else None
+        self.ws = self.segs.sirt_workspace() if use_lists else sirt_workspace(self.grid, self.geom)
 
     # ---- data -------------------------------------------------------------
     def phantoms(self, seeds):
@@ -117,6 +119,13 @@ class WarmStart:
         check(_lib.load().tsp_scale_batch(_p(out), _p(scale), self.V, 1, 0, _st()), "tsp_scale_batch")
         return torch.clamp(out[0], min=0.0)
 
+    def sirt(self, y, x, n_iter, reuse_weights):
+        """n_iter non-negative SIRT updates of x in place (weights kept in self.ws)."""
+        if self.segs is not None:
+            return self.segs.sirt(y.contiguous(), x, n_iter, nonneg=True, workspace=self.ws, reuse_weights=reuse_weights)
+        return tsp_sirt(self.grid, self.geom, y.contiguous(), x, n_iter, nonneg=True, workspace=self.ws,
+                        reuse_weights=reuse_weights)
+
     def sirt_curve(self, y, truth, x0, n_iter, every=1):
         """Errors after 0, every, 2*every, ... SIRT iterations from x0 and the time per iteration."""
         x = x0.clone()
@@ -127,8 +136,7 @@ class WarmStart:
         done = 0
         while done < n_iter:
             k = min(every, n_iter - done)
-            tsp_sirt(self.grid, self.geom, y.contiguous(), x, k, nonneg=True, workspace=self.ws,
-                     reuse_weights=not first)
+            self.sirt(y, x, k, reuse_weights=not first)
             first = False
             done += k
             errs.append(self.rel_error(x, truth))

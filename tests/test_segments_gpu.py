@@ -194,3 +194,39 @@ def test_paper_scale_lists(paper_scale):
         parity(out, oracle.adjoint(wl.edges, st2, di2, y2.reshape(-1).astype(np.float64)),
                what=f"dense list adjoint {v.kind}")
     assert tsp_device_status() == 0
+
+
+@pytest.mark.parametrize("n_iter,nonneg", [(1, False), (5, True)])
+def test_list_sirt_matches_oracle(n_iter, nonneg):
+    from oracle import sirt as osirt
+    wl = workloads.tiny()
+    grid = Grid.from_edges(wl.edges)
+    v = wl.views[0]
+    geom = Geometry.cone(v.pos, v.shape, v.fov_deg)
+    st, di = oracle_rays(v)
+    y = oracle.forward(wl.edges, st, di, wl.rho)
+    seg = Segments(grid, geom)
+    x = torch.zeros(grid.shape, device=DEV)
+    seg.sirt(torch.tensor(y.astype(np.float32).reshape(geom.det_shape), device=DEV), x, n_iter, nonneg=nonneg)
+    ref = osirt.sirt(wl.edges, st, di, y.astype(np.float32), np.zeros(wl.edges.shape), n_iter, nonneg=nonneg)
+    parity(x.cpu().numpy(), ref, what=f"list sirt {n_iter}")
+    assert tsp_device_status() == 0
+
+
+def test_list_sirt_follows_traversal_sirt_and_is_reproducible():
+    from paper_2608_16960_gb300.projector import sirt_workspace, tsp_sirt
+    e = synth.grid_edges(16, 12, 24)
+    grid = Grid.from_edges(e)
+    geom = Geometry.cone(synth.circular_orbit(12, 60.0, incline_deg=20.0), (48, 48), 50.0)
+    y = tsp_forward(grid, geom, torch.tensor(synth.training_phantom(e, 1234), device=DEV))
+    seg = Segments(grid, geom)
+    a = torch.zeros(grid.shape, device=DEV)
+    ws = seg.sirt_workspace()
+    seg.sirt(y, a, 6, nonneg=True, workspace=ws)
+    seg.sirt(y, a, 4, nonneg=True, workspace=ws, reuse_weights=True)
+    b = torch.zeros(grid.shape, device=DEV)
+    seg.sirt(y, b, 10, nonneg=True)
+    assert torch.equal(a, b)  # no atomics: the same lists give the same iterates
+    c = torch.zeros(grid.shape, device=DEV)
+    tsp_sirt(grid, geom, y, c, 10, nonneg=True, workspace=sirt_workspace(grid, geom))
+    assert torch.allclose(a, c, rtol=1e-4, atol=1e-4 * c.abs().max().item())
