@@ -6,14 +6,15 @@
 //   h_k = h_{k-1} + relu(conv(h_{k-1}; wk) + bk)  32 -> 32  tensor cores (k = 2..5)
 //   out = a + conv(h5; w6) + b6                   32 -> 1   CUDA cores
 //
-// The 32 -> 32 layers are implicit GEMMs (M = voxels, N = 32, K = 27 taps x 32)
-// on mma.sync m16n8k16 BF16 tensor cores: a CTA covers four theta-rows of one
-// shell; its shared-memory slab holds the 3 x 6 neighbouring rows with the
-// periodic phi halo, and ldmatrix takes each lane's own (shifted) voxel row, so
-// every tap is the same GEMM on a shifted view. dgrad is the same kernel with
-// the mirrored, transposed kernel; wgrad uses ldmatrix.trans on both operands.
-// Shared-memory rows (64 bytes = 32 channels) are XOR-swizzled in 16-byte
-// chunks so that eight consecutive rows hit disjoint banks.
+// The 32 -> 32 layers are implicit GEMMs (M = voxels, N = 32, K = 27 taps x 32).
+// Forward and dgrad run on the tcgen05 tensor cores with TMEM accumulators
+// (conv32_tc_kernel): every tap is one 128-row window of a shared-memory slab
+// of the neighbouring rows, so one descriptor per tap addresses it; dgrad is
+// the same kernel with the mirrored, transposed kernel. The weight gradient
+// (M = N = 32 per tap, K = voxels: too narrow for a 128-row tcgen05 tile) uses
+// mma.sync m16n8k16 with ldmatrix.trans on both operands; its shared-memory
+// rows (64 bytes = 32 channels) are XOR-swizzled in 16-byte chunks so that
+// eight consecutive rows hit disjoint banks.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -23,11 +24,30 @@
 
 struct tsp_net_s;
 
+// Device error word of this translation unit: a tensor-core wait that gives up
+// sets it (no trap); tsp_device_status reads and clears it.
+static __device__ int g_conv_error_word;
+
 namespace tsp {
+
+static cudaError_t take_conv_error(int* out, cudaStream_t st) {
+  int v = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_conv_error_word, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const int zero = 0;
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_conv_error_word, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  *out |= v << 8;
+  return e;
+}
+
 namespace {
+struct ConvErrorRegistrar {
+  ConvErrorRegistrar() { register_error_reader(&take_conv_error); }
+};
+ConvErrorRegistrar conv_error_registrar;
 
 constexpr int CH = 32;
-constexpr int TR = 4;  // theta-rows per forward/dgrad CTA (one per warp pair)
 
 struct Dims {
   int B, Nr, Ne, Na;
@@ -55,12 +75,17 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::);
 }
-
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
+// 16-byte copy that reads `src_bytes` (16 or 0) bytes and zero-fills the rest
+__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, uint32_t src_bytes) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
 __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
@@ -76,124 +101,259 @@ __device__ __forceinline__ void mma16816(float* c, const uint32_t* a, uint32_t b
 }
 
 // ---------------------------------------------------------------------------
-// 32 -> 32 implicit GEMM: MODE 0 forward (bias, ReLU, residual, mask, bf16
-// out), MODE 1 dgrad (accumulate into float32 G).
+// 32 -> 32 implicit GEMM on the 5th-generation tensor cores (tcgen05, TMEM).
+// MODE 0 forward (bias, ReLU, residual, mask, bf16 out), MODE 1 dgrad
+// (accumulate into float32 G).
+//
+// Output positions of one shell are flattened with the two periodic halo
+// columns of every theta-row, o = e * (N_a + 2) + p, p = 1..N_a the azimuth
+// bins (p = 0 and N_a + 1 are computed and discarded). A CTA takes T tiles of
+// 128 consecutive positions. Its shared-memory slab holds, for the three
+// neighbouring shells, the theta-rows those tiles need (with halo columns,
+// zeros outside the grid in r and theta), stored "chunk-major": the 16-byte
+// chunk c (channels 8c..8c+7) of slab row s at c * SRP * 16 + s * 16. In that
+// layout the A operand of every tap is one 128-row window of the slab, which
+// is exactly the canonical no-swizzle K-major layout (8-row x 16-byte core
+// matrices, 128 bytes apart along M, SRP * 16 apart along K), so one
+// descriptor per (tap, K half) addresses it. The weights (B, N = 32 output
+// channels x K = 27 taps x 32 input channels) sit in the same layout. One
+// thread issues T * 27 * 2 MMAs (M = 128, N = 32, K = 16, bf16 x bf16 -> f32)
+// into T accumulators of 32 TMEM columns, commits them to an mbarrier, and
+// all warps read the accumulators back (tcgen05.ld 32x32b) for the epilogue.
 // ---------------------------------------------------------------------------
-template <int MODE, int MT>
-__global__ void __launch_bounds__(256) conv32_kernel(Dims d, const bf16* __restrict__ X, const bf16* __restrict__ W,
-                                                     const float* __restrict__ bias, const bf16* __restrict__ Xres,
-                                                     bf16* __restrict__ Y, uint32_t* __restrict__ mask,
-                                                     float* __restrict__ G) {
+constexpr int WROWS = 27 * CH + 2;  // weight rows per chunk plane (+2: chunk planes 32 bytes off a bank period)
+constexpr long long TC_WAIT_BUDGET = 2000000000LL;
+
+// Tiles per CTA and slab size for an azimuth count (host and device agree).
+struct TcPlan {
+  int T, nrows, NS, SRP;
+  size_t smem;
+};
+__host__ __device__ inline TcPlan tc_plan(int Na) {
+  const int cols = Na + 2;
+  TcPlan pl{1, 0, 0, 0, 0};
+  for (int T = 4; T >= 1; --T) {
+    pl.T = T;
+    pl.nrows = (128 * T - 1) / cols + 4;  // theta-rows the T tiles touch, plus the r/theta halo
+    pl.NS = pl.nrows * cols;
+    const int SR = 3 * pl.NS + 2;       // +2 rows: the last tile's largest tap shift
+    pl.SRP = (SR + 7) / 8 * 8 + 2;      // chunk planes 32 bytes off a 128-byte bank period
+    pl.smem = size_t(pl.SRP) * 64 + size_t(WROWS) * 64;
+    if (pl.smem <= 232448 - 256) break;
+  }
+  return pl;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return uint64_t((addr & 0x3FFFFu) >> 4) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+         (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
+}
+// Instruction descriptor, kind::f16: f32 accumulator, bf16 A and B, both
+// K-major, N = 32, M = 128.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > TC_WAIT_BUDGET) return false;
+  return true;
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 1) conv32_tc_kernel(Dims d, const bf16* __restrict__ X,
+                                                           const bf16* __restrict__ W, const float* __restrict__ bias,
+                                                           const bf16* __restrict__ Xres, bf16* __restrict__ Y,
+                                                           uint32_t* __restrict__ mask, float* __restrict__ G) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const int Na = d.Na, cols = Na + 2;
-  const int slab_rows = 3 * (TR + 2) * cols;
-  unsigned char* s_x = smem;
-  unsigned char* s_w = smem + size_t(slab_rows) * 64;
-  const int b = blockIdx.z, r = blockIdx.y, e0 = blockIdx.x * TR;
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int Na = d.Na, cols = Na + 2, P = d.Ne * cols;
+  const TcPlan pl = tc_plan(Na);
+  const int T = pl.T, NS = pl.NS, SRP = pl.SRP;
+  const uint32_t ncols = T == 1 ? 32u : (T == 2 ? 64u : 128u);
+  unsigned char* s_x = smem;                      // 4 chunk planes x SRP rows x 16 B
+  unsigned char* s_w = smem + size_t(SRP) * 64;   // 4 chunk planes x WROWS rows x 16 B
+  const int b = blockIdx.z, r = blockIdx.y;
+  const int o0 = blockIdx.x * 128 * T;
+  const int e_lo = o0 / cols - 1;
   const bf16* Xb = X + size_t(b) * d.V * CH;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // weights: 27 x 32 rows of 64 bytes
-  for (int i = threadIdx.x; i < 27 * 32 * 4; i += blockDim.x) {
-    const int row = i >> 2, ch = i & 3;
-    cp_async16(s_w + swz(row, ch), W + size_t(row) * CH + ch * 8);
+  // weights: row = tap * 32 + output channel, K = input channel (async group 0, with shell 0)
+  for (int i = tid; i < 27 * CH * 4; i += blockDim.x) {
+    const int row = i >> 2, c = i & 3;
+    cp_async16(s_w + size_t(c) * WROWS * 16 + row * 16, W + size_t(row) * CH + c * 8);
   }
-  // input slab: (dr, theta row, phi with halo) x 4 chunks, zeros outside in r/theta
-  for (int i = threadIdx.x; i < slab_rows * 4; i += blockDim.x) {
-    const int cell = i >> 2, ch = i & 3;
-    const int c = cell % cols, rowj = (cell / cols) % (TR + 2), dri = cell / (cols * (TR + 2));
-    const int rr = r + dri - 1, ee = e0 + rowj - 1;
-    unsigned char* dst = s_x + swz(cell, ch);
-    if (rr < 0 || rr >= d.Nr || ee < 0 || ee >= d.Ne) {
-      *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
-    } else {
-      int aa = c - 1;
-      aa = aa < 0 ? aa + Na : (aa >= Na ? aa - Na : aa);
-      const int64_t v = (int64_t(rr) * d.Ne + ee) * Na + aa;
-      cp_async16(dst, Xb + v * CH + ch * 8);
-    }
+  // pad rows (row 0 and the rows past the three shells) are zero
+  for (int i = tid; i < (SRP - 3 * NS) * 4; i += blockDim.x) {
+    const int k = i >> 2, c = i & 3;
+    const int srow = k == 0 ? 0 : 3 * NS + k;
+    *reinterpret_cast<uint4*>(s_x + size_t(c) * SRP * 16 + srow * 16) = make_uint4(0, 0, 0, 0);
   }
-  cp_async_wait_all();
-  __syncthreads();
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row_l = warp >> 1, half = warp & 1;
-  const int phi0 = half * (Na >> 1);
-  float acc[MT][4][4];
-#pragma unroll
-  for (int i = 0; i < MT; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.0f;
-
-  const uint32_t sx = static_cast<uint32_t>(__cvta_generic_to_shared(s_x));
-  const uint32_t sw = static_cast<uint32_t>(__cvta_generic_to_shared(s_w));
-  const int mat = lane >> 3, rr8 = lane & 7;
-#pragma unroll 1
-  for (int tap = 0; tap < 27; ++tap) {
-    const int dri = tap / 9, dei = (tap / 3) % 3, dai = tap % 3;
-    const int base_row = (dri * (TR + 2) + row_l + dei) * cols + dai;
-#pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-      uint32_t bfr[4][2];
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        const uint32_t wrow = tap * 32 + p * 16 + rr8 + 8 * (mat >> 1);
-        uint32_t q0, q1, q2, q3;
-        ldsm_x4(sw + swz(wrow, 2 * kk + (mat & 1)), q0, q1, q2, q3);
-        bfr[2 * p][0] = q0;
-        bfr[2 * p][1] = q1;
-        bfr[2 * p + 1][0] = q2;
-        bfr[2 * p + 1][1] = q3;
-      }
-#pragma unroll
-      for (int mt = 0; mt < MT; ++mt) {
-        const uint32_t arow = base_row + phi0 + mt * 16 + rr8 + 8 * (mat & 1);
-        uint32_t a[4];
-        ldsm_x4(sx + swz(arow, 2 * kk + (mat >> 1)), a[0], a[1], a[2], a[3]);
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) mma16816(acc[mt][nt], a, bfr[nt][0], bfr[nt][1]);
-      }
-    }
-  }
-
-  const int e = e0 + row_l;
-  if (e >= d.Ne) return;
-  const int g = lane >> 2, t = lane & 3;
-  const size_t rowbase = ((size_t(b) * d.Nr + r) * d.Ne + e) * Na;
-#pragma unroll
-  for (int mt = 0; mt < MT; ++mt) {
-#pragma unroll
-    for (int hh = 0; hh < 2; ++hh) {
-      const size_t vox = rowbase + phi0 + mt * 16 + g + 8 * hh;
-      uint32_t bits = 0;
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int co = nt * 8 + 2 * t;
-        const float z0 = acc[mt][nt][2 * hh], z1 = acc[mt][nt][2 * hh + 1];
-        if (MODE == 0) {
-          const float y0 = z0 + bias[co], y1 = z1 + bias[co + 1];
-          bits |= (y0 > 0.0f ? 1u : 0u) << co;
-          bits |= (y1 > 0.0f ? 1u : 0u) << (co + 1);
-          const __nv_bfloat162 xr = *reinterpret_cast<const __nv_bfloat162*>(Xres + vox * CH + co);
-          const float o0 = __bfloat162float(xr.x) + fmaxf(y0, 0.0f);
-          const float o1 = __bfloat162float(xr.y) + fmaxf(y1, 0.0f);
-          *reinterpret_cast<__nv_bfloat162*>(Y + vox * CH + co) = __floats2bfloat162_rn(o0, o1);
-        } else {
-          float2* gp = reinterpret_cast<float2*>(G + vox * CH + co);
-          float2 gv = *gp;
-          gv.x += z0;
-          gv.y += z1;
-          *gp = gv;
+  // slab, one async group per shell: row 1 + dri * NS + j * cols + p holds shell r + dri - 1,
+  // theta-row e_lo + j, halo column p (azimuth p - 1 with wrap-around); zeros outside the grid
+  {
+    const int per_shell = NS * 4;
+    const int c = tid & 3;
+    const int rest0 = tid >> 2;
+    const int j0 = rest0 / cols, p0 = rest0 - j0 * cols;
+    constexpr int STEP = 256 / 4;  // rows advanced per loop step (blockDim.x == 256)
+    for (int dri = 0; dri < 3; ++dri) {
+      const int rr = r + dri - 1;
+      const bool shell_ok = rr >= 0 && rr < d.Nr;
+      const bf16* Xs = Xb + int64_t(shell_ok ? rr : 0) * d.Ne * Na * CH + c * 8;
+      unsigned char* dst0 = s_x + size_t(c) * SRP * 16 + size_t(1 + dri * NS) * 16;
+      int j = j0, p = p0;
+      for (int i = tid; i < per_shell; i += 256) {
+        const int ee = e_lo + j;
+        const bool ok = shell_ok && ee >= 0 && ee < d.Ne;
+        const int aa = p == 0 ? Na - 1 : (p == cols - 1 ? 0 : p - 1);
+        const bf16* src = ok ? Xs + (int64_t(ee) * Na + aa) * CH : Xb;
+        cp_async16_zfill(dst0 + size_t(j * cols + p) * 16, src, ok ? 16u : 0u);
+        p += STEP;
+        while (p >= cols) {
+          p -= cols;
+          ++j;
         }
       }
-      if (MODE == 0) {
-        bits |= __shfl_xor_sync(0xffffffffu, bits, 1);
-        bits |= __shfl_xor_sync(0xffffffffu, bits, 2);
-        if (t == 0) mask[vox] = bits;
-      }
+      cp_async_commit();
     }
   }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // Issue each shell's 9 taps as soon as its rows have landed.
+  const uint32_t lbo_x = uint32_t(SRP) * 16, lbo_w = uint32_t(WROWS) * 16;
+  const uint64_t xd0 = umma_desc(smem_u32(s_x), lbo_x, 128), wd0 = umma_desc(smem_u32(s_w), lbo_w, 128);
+  uint32_t tmem = 0;
+#pragma unroll 1
+  for (int dri = 0; dri < 3; ++dri) {
+    if (dri == 0) cp_async_wait<2>();
+    else if (dri == 1) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem = tmem_base;
+    if (tid == 0) {
+      for (int t = 0; t < T; ++t) {
+        const int orel = o0 + 128 * t - e_lo * cols;
+        const uint32_t dt = tmem + uint32_t(t) * 32;
+        for (int dei = 0; dei < 3; ++dei) {
+#pragma unroll
+          for (int dai = 0; dai < 3; ++dai) {
+            const int tap = dri * 9 + dei * 3 + dai;
+            // first A row of this tap's window: input column p + dai - 1, stored one row down
+            const uint32_t srow = uint32_t(orel + dri * NS + (dei - 1) * cols + dai);
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+              const uint64_t ad = xd0 + ((srow * 16u + uint32_t(kk) * 2u * lbo_x) >> 4);
+              const uint64_t bd = wd0 + ((uint32_t(tap) * CH * 16u + uint32_t(kk) * 2u * lbo_w) >> 4);
+              tc_mma(dt, ad, bd, (tap | kk) != 0);
+            }
+          }
+        }
+      }
+      if (dri == 2)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&bar))
+                     : "memory");
+    }
+  }
+  bool ok = mbar_wait_bounded(&bar, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (__syncthreads_and(ok)) {
+    const int q = warp & 3;  // TMEM lane quarter this warp may read
+    for (int t = warp >> 2; t < T; t += 2) {
+      float acc[32];
+      tmem_ld32(tmem + (uint32_t(32 * q) << 16) + uint32_t(t) * 32, acc);
+      const int o = o0 + 128 * t + 32 * q + lane;
+      const int e = o / cols, p = o - e * cols;
+      if (o >= P || p == 0 || p == cols - 1) continue;
+      const size_t vox = ((size_t(b) * d.Nr + r) * d.Ne + e) * Na + (p - 1);
+      if (MODE == 0) {
+        uint32_t bits = 0;
+        const uint4* xr = reinterpret_cast<const uint4*>(Xres + vox * CH);
+        uint4* yo = reinterpret_cast<uint4*>(Y + vox * CH);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const uint4 xv = xr[h];
+          const __nv_bfloat162* x2 = reinterpret_cast<const __nv_bfloat162*>(&xv);
+          uint4 ov;
+          __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(&ov);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int co = 8 * h + 2 * u;
+            const float y0 = acc[co] + bias[co], y1 = acc[co + 1] + bias[co + 1];
+            bits |= (y0 > 0.0f ? 1u : 0u) << co;
+            bits |= (y1 > 0.0f ? 1u : 0u) << (co + 1);
+            const float2 xf = __bfloat1622float2(x2[u]);
+            o2[u] = __floats2bfloat162_rn(xf.x + fmaxf(y0, 0.0f), xf.y + fmaxf(y1, 0.0f));
+          }
+          yo[h] = ov;
+        }
+        mask[vox] = bits;
+      } else {
+        float4* gp = reinterpret_cast<float4*>(G + vox * CH);
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+          float4 gv = gp[h];
+          gv.x += acc[4 * h];
+          gv.y += acc[4 * h + 1];
+          gv.z += acc[4 * h + 2];
+          gv.w += acc[4 * h + 3];
+          gp[h] = gv;
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(&g_conv_error_word, 1);
+    mbar_wait_bounded(&bar, 0);  // let the MMAs finish before their accumulators are released
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -571,7 +731,6 @@ struct tsp_net_s {
 
 namespace {
 
-size_t fwd_smem(int Na) { return size_t(3 * (TR + 2) * (Na + 2)) * 64 + size_t(27 * 32) * 64; }
 size_t wgrad_smem(int Na) { return size_t(9 * (Na + 2)) * 64 + size_t(Na) * 64; }
 
 template <class T>
@@ -582,33 +741,22 @@ tsp_status net_alloc(tsp_net n, T** p, size_t count) {
   return TSP_OK;
 }
 
-template <int MT>
 tsp_status set_attrs(int Na) {
-  TSP_CUDA(cudaFuncSetAttribute(conv32_kernel<0, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwd_smem(Na))));
-  TSP_CUDA(cudaFuncSetAttribute(conv32_kernel<1, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fwd_smem(Na))));
+  const int sm = int(tc_plan(Na).smem);
+  TSP_CUDA(cudaFuncSetAttribute(conv32_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  TSP_CUDA(cudaFuncSetAttribute(conv32_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   return TSP_OK;
-}
-
-template <int MT>
-void launch_conv32(int mode, const Dims& d, int B, const bf16* X, const bf16* W, const float* bias, const bf16* Xres,
-                   bf16* Y, uint32_t* mask, float* G, cudaStream_t st) {
-  Dims db = d;
-  db.B = B;
-  dim3 grid((d.Ne + TR - 1) / TR, d.Nr, B);
-  if (mode == 0) conv32_kernel<0, MT><<<grid, 256, fwd_smem(d.Na), st>>>(db, X, W, bias, Xres, Y, mask, G);
-  else conv32_kernel<1, MT><<<grid, 256, fwd_smem(d.Na), st>>>(db, X, W, bias, Xres, Y, mask, G);
 }
 
 void conv32(int mode, const Dims& d, int B, const bf16* X, const bf16* W, const float* bias, const bf16* Xres, bf16* Y,
             uint32_t* mask, float* G, cudaStream_t st) {
-  switch (d.Na / 32) {
-    case 1: launch_conv32<1>(mode, d, B, X, W, bias, Xres, Y, mask, G, st); break;
-    case 2: launch_conv32<2>(mode, d, B, X, W, bias, Xres, Y, mask, G, st); break;
-    case 3: launch_conv32<3>(mode, d, B, X, W, bias, Xres, Y, mask, G, st); break;
-    case 4: launch_conv32<4>(mode, d, B, X, W, bias, Xres, Y, mask, G, st); break;
-    case 5: launch_conv32<5>(mode, d, B, X, W, bias, Xres, Y, mask, G, st); break;
-    default: launch_conv32<6>(mode, d, B, X, W, bias, Xres, Y, mask, G, st); break;
-  }
+  Dims db = d;
+  db.B = B;
+  const TcPlan pl = tc_plan(d.Na);
+  const int P = d.Ne * (d.Na + 2);
+  dim3 grid((P + 128 * pl.T - 1) / (128 * pl.T), d.Nr, B);
+  if (mode == 0) conv32_tc_kernel<0><<<grid, 256, pl.smem, st>>>(db, X, W, bias, Xres, Y, mask, G);
+  else conv32_tc_kernel<1><<<grid, 256, pl.smem, st>>>(db, X, W, bias, Xres, Y, mask, G);
 }
 
 template <int NA>
@@ -712,17 +860,7 @@ extern "C" tsp_status tsp_net_create(int n_r, int n_e, int n_a, int max_batch, t
   if (st == TSP_OK) st = net_alloc(n, &n->gh, nv * CH);
   if (st == TSP_OK) st = net_alloc(n, &n->gz, nv * CH);
   if (st == TSP_OK) st = net_alloc(n, &n->loss, 1);
-  if (st == TSP_OK) {
-    const int MT = n_a / 32;
-    switch (MT) {
-      case 1: st = set_attrs<1>(n_a); break;
-      case 2: st = set_attrs<2>(n_a); break;
-      case 3: st = set_attrs<3>(n_a); break;
-      case 4: st = set_attrs<4>(n_a); break;
-      case 5: st = set_attrs<5>(n_a); break;
-      default: st = set_attrs<6>(n_a); break;
-    }
-  }
+  if (st == TSP_OK) st = set_attrs(n_a);
   if (st == TSP_OK) {
     switch (n_a) {
       case 32: st = wgrad_attr<32>(); break;

@@ -37,9 +37,13 @@ def _unflat(flat):
     return out
 
 
-@pytest.fixture(scope="module")
-def case():
-    shape = (4, 5, 64)  # five theta-rows: exercises the partial last tile
+# Grid shapes covering every tensor-core tile plan: azimuth 32..128 take 4
+# tiles of 128 positions per CTA, 160 takes 2, 192 takes 1; several CTAs per
+# shell and a last CTA whose tiles run past the shell's end.
+SHAPES = [(4, 5, 64), (3, 9, 96), (3, 20, 32), (2, 4, 160), (2, 3, 192)]
+
+
+def _case(shape):
     B = 2
     params = _params(1)
     rng = synth.SplitMix64(2)
@@ -50,14 +54,24 @@ def case():
     return shape, B, params, a, t, net
 
 
+@pytest.fixture(scope="module")
+def case():
+    return _case(SHAPES[0])
+
+
+@pytest.fixture(scope="module", params=SHAPES, ids=lambda s: "x".join(map(str, s)))
+def shaped(request):
+    return _case(request.param)
+
+
 def test_param_layout_roundtrip(case):
     shape, B, params, a, t, net = case
     assert net.n_params == sum(w.size + b.size for w, b in params)
     assert np.array_equal(net.get_params(), _flat(params))
 
 
-def test_forward_matches_oracle(case):
-    shape, B, params, a, t, net = case
+def test_forward_matches_oracle(shaped):
+    shape, B, params, a, t, net = shaped
     out = net.forward(torch.tensor(a, device=DEV)).cpu().numpy()
     ref, (a16, ws, h, masks) = onet.forward(params, a, keep=True)
     for k in range(5):
@@ -71,8 +85,8 @@ def test_forward_matches_oracle(case):
     assert np.linalg.norm(out - ref) <= 1e-2 * np.linalg.norm(ref)
 
 
-def test_gradients_match_oracle(case):
-    shape, B, params, a, t, net = case
+def test_gradients_match_oracle(shaped):
+    shape, B, params, a, t, net = shaped
     loss = net.loss_grad(torch.tensor(a, device=DEV), torch.tensor(t, device=DEV))
     ref_loss, grads = onet.loss_and_grads(params, a, t)
     assert abs(loss - ref_loss) <= 1e-2 * ref_loss
