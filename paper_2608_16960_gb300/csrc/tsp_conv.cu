@@ -80,7 +80,6 @@ __device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, u
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
@@ -107,38 +106,43 @@ __device__ __forceinline__ void mma16816(float* c, const uint32_t* a, uint32_t b
 //
 // Output positions of one shell are flattened with the two periodic halo
 // columns of every theta-row, o = e * (N_a + 2) + p, p = 1..N_a the azimuth
-// bins (p = 0 and N_a + 1 are computed and discarded). A CTA takes T tiles of
-// 128 consecutive positions. Its shared-memory slab holds, for the three
-// neighbouring shells, the theta-rows those tiles need (with halo columns,
-// zeros outside the grid in r and theta), stored "chunk-major": the 16-byte
-// chunk c (channels 8c..8c+7) of slab row s at c * SRP * 16 + s * 16. In that
-// layout the A operand of every tap is one 128-row window of the slab, which
-// is exactly the canonical no-swizzle K-major layout (8-row x 16-byte core
-// matrices, 128 bytes apart along M, SRP * 16 apart along K), so one
-// descriptor per (tap, K half) addresses it. The weights (B, N = 32 output
-// channels x K = 27 taps x 32 input channels) sit in the same layout. One
-// thread issues T * 27 * 2 MMAs (M = 128, N = 32, K = 16, bf16 x bf16 -> f32)
-// into T accumulators of 32 TMEM columns, commits them to an mbarrier, and
-// all warps read the accumulators back (tcgen05.ld 32x32b) for the epilogue.
+// bins (p = 0 and N_a + 1 are computed and discarded); a "chunk" is T tiles of
+// 128 consecutive positions. A shell buffer holds the theta-rows a chunk
+// needs from one shell (halo columns included, zeros outside the grid),
+// stored "chunk-major": the 16-byte chunk c (channels 8c..8c+7) of buffer row
+// s at c * SBP * 16 + s * 16, row 0 a zero pad. In that layout the A operand
+// of a tap is one 128-row window of a shell buffer, exactly the canonical
+// no-swizzle K-major layout (8-row x 16-byte core matrices, 128 bytes apart
+// along M, SBP * 16 apart along K), so one descriptor per (tap, K half)
+// addresses it. The weights (B: N = 32 output channels x K = 27 taps x 32
+// input channels) sit in the same layout, loaded once per CTA.
+//
+// Persistent CTAs take work items (sample, chunk, run of consecutive shells).
+// Walking along r, a ring of three shell buffers holds shells r-1, r, r+1, so
+// each step loads one new shell. One thread issues the step's 27 taps x T
+// tiles x 2 K halves (M = 128, N = 32, K = 16, bf16 x bf16 -> f32) shell by
+// shell, committing after the outgoing shell's taps so that its buffer is
+// refilled with shell r+2 while the other MMAs run; accumulators alternate
+// between two TMEM buffers so that every warp reads the previous step's
+// (tcgen05.ld 32x32b) and runs its epilogue while the tensor cores work.
 // ---------------------------------------------------------------------------
 constexpr int WROWS = 27 * CH + 2;  // weight rows per chunk plane (+2: chunk planes 32 bytes off a bank period)
 constexpr long long TC_WAIT_BUDGET = 2000000000LL;
 
-// Tiles per CTA and slab size for an azimuth count (host and device agree).
+// Tiles per chunk and shell-buffer size for an azimuth count (host and device agree).
 struct TcPlan {
-  int T, nrows, NS, SRP;
+  int T, nrows, SBP;
   size_t smem;
 };
 __host__ __device__ inline TcPlan tc_plan(int Na) {
   const int cols = Na + 2;
-  TcPlan pl{1, 0, 0, 0, 0};
+  TcPlan pl{1, 0, 0, 0};
   for (int T = 4; T >= 1; --T) {
     pl.T = T;
-    pl.nrows = (128 * T - 1) / cols + 4;  // theta-rows the T tiles touch, plus the r/theta halo
-    pl.NS = pl.nrows * cols;
-    const int SR = 3 * pl.NS + 2;       // +2 rows: the last tile's largest tap shift
-    pl.SRP = (SR + 7) / 8 * 8 + 2;      // chunk planes 32 bytes off a 128-byte bank period
-    pl.smem = size_t(pl.SRP) * 64 + size_t(WROWS) * 64;
+    pl.nrows = (128 * T - 1) / cols + 4;  // theta-rows the T tiles touch, plus the theta halo
+    const int SB = pl.nrows * cols + 2;   // + row 0 (zero) and one row for the largest tap shift
+    pl.SBP = (SB + 7) / 8 * 8 + 2;        // chunk planes 32 bytes off a 128-byte bank period
+    pl.smem = 3 * size_t(pl.SBP) * 64 + size_t(WROWS) * 64;
     if (pl.smem <= 232448 - 256) break;
   }
   return pl;
@@ -157,13 +161,6 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
 // K-major, N = 32, M = 128.
 constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
-      : "memory");
-}
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -172,12 +169,6 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try(bar, parity))
-    if (clock64() - t0 > TC_WAIT_BUDGET) return false;
-  return true;
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
@@ -194,164 +185,300 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Load shell rr of sample b for the chunk whose first theta-row is e_lo + 1
+// into a shell buffer: row 1 + j * cols + p <- theta-row e_lo + j, halo column
+// p (azimuth p - 1, wrapped), zero-filled outside the grid. Run by `nt`
+// threads (a multiple of 4), lt = 0..nt-1; waits for its own copies.
+__device__ __forceinline__ void tc_load_shell(const Dims& d, const bf16* __restrict__ X, int b, int rr, int e_lo,
+                                              int nrows, int SBP, unsigned char* buf, int lt, int nt) {
+  const int Na = d.Na, cols = Na + 2;
+  const bool shell_ok = rr >= 0 && rr < d.Nr;
+  const int c = lt & 3;
+  const bf16* Xs = X + (size_t(b) * d.V + size_t(shell_ok ? rr : 0) * d.Ne * Na) * CH + c * 8;
+  unsigned char* dst0 = buf + size_t(c) * SBP * 16 + 16;  // data starts at row 1
+  int j = (lt >> 2) / cols, p = (lt >> 2) - j * cols;
+  const int step = nt >> 2;  // buffer rows advanced per loop step
+  for (int i = lt; i < nrows * cols * 4; i += nt) {
+    const int ee = e_lo + j;
+    const bool ok = shell_ok && ee >= 0 && ee < d.Ne;
+    const int aa = p == 0 ? Na - 1 : (p == cols - 1 ? 0 : p - 1);
+    const bf16* src = ok ? Xs + (int64_t(ee) * Na + aa) * CH : X;
+    cp_async16_zfill(dst0 + size_t(j * cols + p) * 16, src, ok ? 16u : 0u);
+    p += step;
+    while (p >= cols) {
+      p -= cols;
+      ++j;
+    }
+  }
+  cp_async_wait_all();
+}
+
+// Epilogue of one step (run by four warps, warp w reading TMEM lane quarter
+// w & 3): the accumulators of output shell r, chunk q, sit in TMEM columns
+// [col0, col0 + T * 32). Forward: y = x + relu(z + bias) with x the layer
+// input (the residual), plus the ReLU mask; dgrad: G += z. The residual rows
+// of all T tiles are requested before the first accumulator is read.
+template <int MODE, int T>
+__device__ __forceinline__ void tc_epilogue(const Dims& d, int b, int r, int q, uint32_t tmem, uint32_t col0,
+                                            const bf16* __restrict__ Xres, const float (&bz)[32],
+                                            bf16* __restrict__ Y, uint32_t* __restrict__ mask, float* __restrict__ G,
+                                            int warp, int lane) {
+  const int Na = d.Na, cols = Na + 2, P = d.Ne * cols;
+  const int o0 = q * 128 * T;
+  const int qd = warp & 3;  // TMEM lane quarter this warp may read
+  size_t vox[T];
+  bool valid[T];
+  uint4 xv[MODE == 0 ? T : 1][4];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int o = o0 + 128 * t + 32 * qd + lane;
+    const int e = o / cols, p = o - e * cols;
+    valid[t] = o < P && p != 0 && p != cols - 1;
+    vox[t] = valid[t] ? ((size_t(b) * d.Nr + r) * d.Ne + e) * Na + (p - 1) : 0;
+    if (MODE == 0) {
+      const uint4* xr = reinterpret_cast<const uint4*>(Xres + vox[t] * CH);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) xv[MODE == 0 ? t : 0][h] = valid[t] ? xr[h] : make_uint4(0, 0, 0, 0);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    float acc[32];
+    tmem_ld32(tmem + (uint32_t(32 * qd) << 16) + col0 + uint32_t(t) * 32, acc);
+    if (!valid[t]) continue;
+    if (MODE == 0) {
+      uint32_t bits = 0;
+      uint4* yo = reinterpret_cast<uint4*>(Y + vox[t] * CH);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const __nv_bfloat162* x2 = reinterpret_cast<const __nv_bfloat162*>(&xv[MODE == 0 ? t : 0][h]);
+        uint4 ov;
+        __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(&ov);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int co = 8 * h + 2 * u;
+          const float y0 = acc[co] + bz[co], y1 = acc[co + 1] + bz[co + 1];
+          bits |= (y0 > 0.0f ? 1u : 0u) << co;
+          bits |= (y1 > 0.0f ? 1u : 0u) << (co + 1);
+          const float2 xf = __bfloat1622float2(x2[u]);
+          o2[u] = __floats2bfloat162_rn(xf.x + fmaxf(y0, 0.0f), xf.y + fmaxf(y1, 0.0f));
+        }
+        yo[h] = ov;
+      }
+      mask[vox[t]] = bits;
+    } else {
+      float4* gp = reinterpret_cast<float4*>(G + vox[t] * CH);
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        float4 gv = gp[h];
+        gv.x += acc[4 * h];
+        gv.y += acc[4 * h + 1];
+        gv.z += acc[4 * h + 2];
+        gv.w += acc[4 * h + 3];
+        gp[h] = gv;
+      }
+    }
+  }
+}
+
+// Bounded wait on an mbarrier phase that also gives up when another role of
+// the CTA has already given up (s_abort); sets s_abort on its own timeout.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* s_abort) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (*s_abort) return false;
+    if (clock64() - t0 > TC_WAIT_BUDGET) {
+      *s_abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Warp-collective forms: the whole warp executes them (operands warp-uniform),
+// one elected lane issues the MMA / the commit.
+__device__ __forceinline__ void tc_mma_elect(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p, e;\n elect.sync _|e, 0xffffffff;\n setp.ne.u32 p, %4, 0;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit_elect(uint64_t* bar) {
+  asm volatile(
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}" ::"r"(smem_u32(bar))
+      : "memory");
+}
+
+constexpr int TC_LOADERS = 96;  // warps 1-3
+
 template <int MODE>
-__global__ void __launch_bounds__(256, 1) conv32_tc_kernel(Dims d, const bf16* __restrict__ X,
+__global__ void __launch_bounds__(256, 1) conv32_tc_kernel(Dims d, int rseg, const bf16* __restrict__ X,
                                                            const bf16* __restrict__ W, const float* __restrict__ bias,
-                                                           const bf16* __restrict__ Xres, bf16* __restrict__ Y,
-                                                           uint32_t* __restrict__ mask, float* __restrict__ G) {
+                                                           bf16* __restrict__ Y, uint32_t* __restrict__ mask,
+                                                           float* __restrict__ G) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar;
+  // full[s]: shell slot s loaded (96 loader arrivals); empty[s]: its last MMA done (commit);
+  // tfull[j]: TMEM buffer j holds a finished step (commit); tempty[j]: drained (128 epilogue arrivals)
+  __shared__ __align__(8) uint64_t full[3], empty[3], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_abort;
   const int Na = d.Na, cols = Na + 2, P = d.Ne * cols;
   const TcPlan pl = tc_plan(Na);
-  const int T = pl.T, NS = pl.NS, SRP = pl.SRP;
-  const uint32_t ncols = T == 1 ? 32u : (T == 2 ? 64u : 128u);
-  unsigned char* s_x = smem;                      // 4 chunk planes x SRP rows x 16 B
-  unsigned char* s_w = smem + size_t(SRP) * 64;   // 4 chunk planes x WROWS rows x 16 B
-  const int b = blockIdx.z, r = blockIdx.y;
-  const int o0 = blockIdx.x * 128 * T;
-  const int e_lo = o0 / cols - 1;
-  const bf16* Xb = X + size_t(b) * d.V * CH;
+  const int T = pl.T, nrows = pl.nrows, SBP = pl.SBP;
+  const uint32_t ncols = T == 1 ? 64u : (T == 2 ? 128u : 256u);  // two accumulator buffers of T * 32 columns
+  unsigned char* s_w = smem + 3 * size_t(SBP) * 64;           // 4 chunk planes x WROWS rows x 16 B
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nq = (P + 128 * T - 1) / (128 * T), nseg = (d.Nr + rseg - 1) / rseg;
+  const int items = d.B * nq * nseg;
 
-  // weights: row = tap * 32 + output channel, K = input channel (async group 0, with shell 0)
-  for (int i = tid; i < 27 * CH * 4; i += blockDim.x) {
+  // ---- set-up, all threads: pad rows, weights, barriers, TMEM ----
+  const int pad = SBP - nrows * cols;  // row 0 and the rows past the data stay zero
+  for (int i = tid; i < 3 * pad * 4; i += blockDim.x) {
+    const int k = i >> 2, c = i & 3, slot = k / pad, kr = k - slot * pad;
+    const int row = kr == 0 ? 0 : nrows * cols + kr;
+    *reinterpret_cast<uint4*>(smem + size_t(slot) * SBP * 64 + size_t(c) * SBP * 16 + size_t(row) * 16) =
+        make_uint4(0, 0, 0, 0);
+  }
+  for (int i = tid; i < 27 * CH * 4; i += blockDim.x) {  // row = tap * 32 + output channel, K = input channel
     const int row = i >> 2, c = i & 3;
     cp_async16(s_w + size_t(c) * WROWS * 16 + row * 16, W + size_t(row) * CH + c * 8);
   }
-  // pad rows (row 0 and the rows past the three shells) are zero
-  for (int i = tid; i < (SRP - 3 * NS) * 4; i += blockDim.x) {
-    const int k = i >> 2, c = i & 3;
-    const int srow = k == 0 ? 0 : 3 * NS + k;
-    *reinterpret_cast<uint4*>(s_x + size_t(c) * SRP * 16 + srow * 16) = make_uint4(0, 0, 0, 0);
-  }
-  // slab, one async group per shell: row 1 + dri * NS + j * cols + p holds shell r + dri - 1,
-  // theta-row e_lo + j, halo column p (azimuth p - 1 with wrap-around); zeros outside the grid
-  {
-    const int per_shell = NS * 4;
-    const int c = tid & 3;
-    const int rest0 = tid >> 2;
-    const int j0 = rest0 / cols, p0 = rest0 - j0 * cols;
-    constexpr int STEP = 256 / 4;  // rows advanced per loop step (blockDim.x == 256)
-    for (int dri = 0; dri < 3; ++dri) {
-      const int rr = r + dri - 1;
-      const bool shell_ok = rr >= 0 && rr < d.Nr;
-      const bf16* Xs = Xb + int64_t(shell_ok ? rr : 0) * d.Ne * Na * CH + c * 8;
-      unsigned char* dst0 = s_x + size_t(c) * SRP * 16 + size_t(1 + dri * NS) * 16;
-      int j = j0, p = p0;
-      for (int i = tid; i < per_shell; i += 256) {
-        const int ee = e_lo + j;
-        const bool ok = shell_ok && ee >= 0 && ee < d.Ne;
-        const int aa = p == 0 ? Na - 1 : (p == cols - 1 ? 0 : p - 1);
-        const bf16* src = ok ? Xs + (int64_t(ee) * Na + aa) * CH : Xb;
-        cp_async16_zfill(dst0 + size_t(j * cols + p) * 16, src, ok ? 16u : 0u);
-        p += STEP;
-        while (p >= cols) {
-          p -= cols;
-          ++j;
-        }
-      }
-      cp_async_commit();
+  cp_async_wait_all();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+  if (tid == 0) {
+    s_abort = 0;
+    for (int s = 0; s < 3; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(TC_LOADERS) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+    }
+    for (int j = 0; j < 2; ++j) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull[j])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&tempty[j])) : "memory");
     }
   }
-  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                  "r"(ncols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // Issue each shell's 9 taps as soon as its rows have landed.
-  const uint32_t lbo_x = uint32_t(SRP) * 16, lbo_w = uint32_t(WROWS) * 16;
-  const uint64_t xd0 = umma_desc(smem_u32(s_x), lbo_x, 128), wd0 = umma_desc(smem_u32(s_w), lbo_w, 128);
-  uint32_t tmem = 0;
-#pragma unroll 1
-  for (int dri = 0; dri < 3; ++dri) {
-    if (dri == 0) cp_async_wait<2>();
-    else if (dri == 1) cp_async_wait<1>();
-    else cp_async_wait<0>();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    tmem = tmem_base;
-    if (tid == 0) {
-      for (int t = 0; t < T; ++t) {
-        const int orel = o0 + 128 * t - e_lo * cols;
-        const uint32_t dt = tmem + uint32_t(t) * 32;
-        for (int dei = 0; dei < 3; ++dei) {
-#pragma unroll
-          for (int dai = 0; dai < 3; ++dai) {
-            const int tap = dri * 9 + dei * 3 + dai;
-            // first A row of this tap's window: input column p + dai - 1, stored one row down
-            const uint32_t srow = uint32_t(orel + dri * NS + (dei - 1) * cols + dai);
-#pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-              const uint64_t ad = xd0 + ((srow * 16u + uint32_t(kk) * 2u * lbo_x) >> 4);
-              const uint64_t bd = wd0 + ((uint32_t(tap) * CH * 16u + uint32_t(kk) * 2u * lbo_w) >> 4);
-              tc_mma(dt, ad, bd, (tap | kk) != 0);
-            }
-          }
-        }
-      }
-      if (dri == 2)
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&bar))
-                     : "memory");
-    }
-  }
-  bool ok = mbar_wait_bounded(&bar, 0);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (__syncthreads_and(ok)) {
-    const int q = warp & 3;  // TMEM lane quarter this warp may read
-    for (int t = warp >> 2; t < T; t += 2) {
-      float acc[32];
-      tmem_ld32(tmem + (uint32_t(32 * q) << 16) + uint32_t(t) * 32, acc);
-      const int o = o0 + 128 * t + 32 * q + lane;
-      const int e = o / cols, p = o - e * cols;
-      if (o >= P || p == 0 || p == cols - 1) continue;
-      const size_t vox = ((size_t(b) * d.Nr + r) * d.Ne + e) * Na + (p - 1);
-      if (MODE == 0) {
-        uint32_t bits = 0;
-        const uint4* xr = reinterpret_cast<const uint4*>(Xres + vox * CH);
-        uint4* yo = reinterpret_cast<uint4*>(Y + vox * CH);
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const uint4 xv = xr[h];
-          const __nv_bfloat162* x2 = reinterpret_cast<const __nv_bfloat162*>(&xv);
-          uint4 ov;
-          __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(&ov);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int co = 8 * h + 2 * u;
-            const float y0 = acc[co] + bias[co], y1 = acc[co + 1] + bias[co + 1];
-            bits |= (y0 > 0.0f ? 1u : 0u) << co;
-            bits |= (y1 > 0.0f ? 1u : 0u) << (co + 1);
-            const float2 xf = __bfloat1622float2(x2[u]);
-            o2[u] = __floats2bfloat162_rn(xf.x + fmaxf(y0, 0.0f), xf.y + fmaxf(y1, 0.0f));
-          }
-          yo[h] = ov;
-        }
-        mask[vox] = bits;
-      } else {
-        float4* gp = reinterpret_cast<float4*>(G + vox * CH);
-#pragma unroll
-        for (int h = 0; h < 8; ++h) {
-          float4 gv = gp[h];
-          gv.x += acc[4 * h];
-          gv.y += acc[4 * h + 1];
-          gv.z += acc[4 * h + 2];
-          gv.w += acc[4 * h + 3];
-          gp[h] = gv;
-        }
-      }
-    }
-  } else if (tid == 0) {
-    atomicOr(&g_conv_error_word, 1);
-    mbar_wait_bounded(&bar, 0);  // let the MMAs finish before their accumulators are released
-  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  // Every role walks the same sequence: items, their steps r = r0..r1-1 (global
+  // step K, TMEM buffer K & 1) and their shell loads r0-1..r1 (global load G,
+  // slot G % 3, the n-th use of a slot being phase n of its barriers).
+  if (warp == 0) {  // ---- MMA issuer: the warp walks the schedule, one elected lane issues ----
+    const uint32_t lbo_x = uint32_t(SBP) * 16, lbo_w = uint32_t(WROWS) * 16;
+    const uint64_t wd0 = umma_desc(smem_u32(s_w), lbo_w, 128);
+    int K = 0, G0 = 0;
+    bool go = true;
+    for (int item = blockIdx.x; item < items && go; item += gridDim.x) {
+      const int seg = item % nseg, q = (item / nseg) % nq;
+      const int r0 = seg * rseg, n = min(rseg, d.Nr - r0);
+      const int o0 = q * 128 * T, e_lo = o0 / cols - 1;
+      for (int i = 0; i < n && go; ++i, ++K) {
+        if (K >= 2 && !__all_sync(0xffffffffu, tc_wait(&tempty[K & 1], uint32_t((K >> 1) - 1) & 1u, &s_abort))) {
+          go = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc0 = tmem + uint32_t(K & 1) * uint32_t(T) * 32;
+        for (int dri = 0; dri < 3 && go; ++dri) {
+          const int Gl = G0 + i + dri, slot = Gl % 3;
+          if (!__all_sync(0xffffffffu, tc_wait(&full[slot], uint32_t(Gl / 3) & 1u, &s_abort))) {
+            go = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t xd0 = umma_desc(smem_u32(smem + size_t(slot) * SBP * 64), lbo_x, 128);
+          for (int t = 0; t < T; ++t) {
+            const int orel = o0 + 128 * t - e_lo * cols;
+#pragma unroll
+            for (int dei = 0; dei < 3; ++dei) {
+#pragma unroll
+              for (int dai = 0; dai < 3; ++dai) {
+                const int tap = dri * 9 + dei * 3 + dai;
+                // first A row of this tap's window: input column p + dai - 1, stored one row down
+                const uint32_t srow = uint32_t(orel + (dei - 1) * cols + dai);
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk) {
+                  const uint64_t ad = xd0 + ((srow * 16u + uint32_t(kk) * 2u * lbo_x) >> 4);
+                  const uint64_t bd = wd0 + ((uint32_t(tap) * CH * 16u + uint32_t(kk) * 2u * lbo_w) >> 4);
+                  tc_mma_elect(acc0 + uint32_t(t) * 32, ad, bd, (tap | kk) != 0);
+                }
+              }
+            }
+          }
+          if (dri == 0 || i == n - 1) tc_commit_elect(&empty[slot]);  // this load's last use
+          __syncwarp();
+        }
+        if (go) tc_commit_elect(&tfull[K & 1]);
+        __syncwarp();
+      }
+      G0 += n + 2;
+    }
+    if (!go && lane == 0) {  // let issued MMAs land before TMEM is released
+      const long long t0 = clock64();
+      while (clock64() - t0 < TC_WAIT_BUDGET / 8) {
+      }
+    }
+    __syncwarp();
+  } else if (warp < 4) {  // ---- shell loaders ----
+    const int lt = tid - 32;
+    int G0 = 0;
+    bool go = true;
+    for (int item = blockIdx.x; item < items && go; item += gridDim.x) {
+      const int seg = item % nseg, rest = item / nseg, q = rest % nq, b = rest / nq;
+      const int r0 = seg * rseg, n = min(rseg, d.Nr - r0);
+      const int e_lo = q * 128 * T / cols - 1;
+      for (int j = 0; j < n + 2; ++j) {
+        const int Gl = G0 + j, slot = Gl % 3;
+        if (Gl >= 3 && !tc_wait(&empty[slot], uint32_t(Gl / 3 - 1) & 1u, &s_abort)) {
+          go = false;
+          break;
+        }
+        tc_load_shell(d, X, b, r0 - 1 + j, e_lo, nrows, SBP, smem + size_t(slot) * SBP * 64, lt, TC_LOADERS);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // copies -> tensor-core reads
+        mbar_arrive(&full[slot]);
+      }
+      G0 += n + 2;
+    }
+  } else {  // ---- epilogue ----
+    float bz[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) bz[c] = MODE == 0 ? bias[c] : 0.0f;
+    int K = 0;
+    bool go = true;
+    for (int item = blockIdx.x; item < items && go; item += gridDim.x) {
+      const int seg = item % nseg, rest = item / nseg, q = rest % nq, b = rest / nq;
+      const int r0 = seg * rseg, n = min(rseg, d.Nr - r0);
+      for (int i = 0; i < n; ++i, ++K) {
+        const bool ok = __all_sync(0xffffffffu, tc_wait(&tfull[K & 1], uint32_t(K >> 1) & 1u, &s_abort));
+        if (!ok) {
+          go = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t col0 = uint32_t(K & 1) * uint32_t(T) * 32;
+        if (T == 4) tc_epilogue<MODE, 4>(d, b, r0 + i, q, tmem, col0, X, bz, Y, mask, G, warp, lane);
+        else if (T == 2) tc_epilogue<MODE, 2>(d, b, r0 + i, q, tmem, col0, X, bz, Y, mask, G, warp, lane);
+        else if (T == 3) tc_epilogue<MODE, 3>(d, b, r0 + i, q, tmem, col0, X, bz, Y, mask, G, warp, lane);
+        else tc_epilogue<MODE, 1>(d, b, r0 + i, q, tmem, col0, X, bz, Y, mask, G, warp, lane);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&tempty[K & 1]);
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && s_abort) atomicOr(&g_conv_error_word, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
@@ -741,22 +868,33 @@ tsp_status net_alloc(tsp_net n, T** p, size_t count) {
   return TSP_OK;
 }
 
+int g_sm_count = 152;  // multiprocessors of the device the network lives on (set at creation)
+
 tsp_status set_attrs(int Na) {
   const int sm = int(tc_plan(Na).smem);
   TSP_CUDA(cudaFuncSetAttribute(conv32_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   TSP_CUDA(cudaFuncSetAttribute(conv32_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  int dev = 0;
+  TSP_CUDA(cudaGetDevice(&dev));
+  TSP_CUDA(cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev));
   return TSP_OK;
 }
 
-void conv32(int mode, const Dims& d, int B, const bf16* X, const bf16* W, const float* bias, const bf16* Xres, bf16* Y,
-            uint32_t* mask, float* G, cudaStream_t st) {
+// Persistent launch: work items (sample, chunk, run of rseg shells), about
+// four per multiprocessor, one CTA per multiprocessor (its shared memory).
+void conv32(int mode, const Dims& d, int B, const bf16* X, const bf16* W, const float* bias, bf16* Y, uint32_t* mask,
+            float* G, cudaStream_t st) {
   Dims db = d;
   db.B = B;
   const TcPlan pl = tc_plan(d.Na);
   const int P = d.Ne * (d.Na + 2);
-  dim3 grid((P + 128 * pl.T - 1) / (128 * pl.T), d.Nr, B);
-  if (mode == 0) conv32_tc_kernel<0><<<grid, 256, pl.smem, st>>>(db, X, W, bias, Xres, Y, mask, G);
-  else conv32_tc_kernel<1><<<grid, 256, pl.smem, st>>>(db, X, W, bias, Xres, Y, mask, G);
+  const int nq = (P + 128 * pl.T - 1) / (128 * pl.T);
+  const int64_t steps = int64_t(B) * nq * d.Nr;
+  const int rseg = int(std::max<int64_t>(2, std::min<int64_t>(d.Nr, steps / (4 * int64_t(g_sm_count)))));
+  const int64_t items = int64_t(B) * nq * ((d.Nr + rseg - 1) / rseg);
+  const unsigned grid = unsigned(std::min<int64_t>(items, g_sm_count));
+  if (mode == 0) conv32_tc_kernel<0><<<grid, 256, pl.smem, st>>>(db, rseg, X, W, bias, Y, mask, G);
+  else conv32_tc_kernel<1><<<grid, 256, pl.smem, st>>>(db, rseg, X, W, bias, Y, mask, G);
 }
 
 template <int NA>
@@ -808,7 +946,7 @@ tsp_status net_forward(tsp_net n, const float* a, int B, cudaStream_t st) {
   conv_in_fwd_kernel<<<blocks_for(nv, 128), 128, 0, st>>>(db, n->a16, n->w1r, n->params + n->off_b[0], n->h[0],
                                                           n->mask[0]);
   for (int k = 0; k < 4; ++k)
-    conv32(0, d, B, n->h[k], n->wf[k], n->params + n->off_b[k + 1], n->h[k], n->h[k + 1], n->mask[k + 1], nullptr, st);
+    conv32(0, d, B, n->h[k], n->wf[k], n->params + n->off_b[k + 1], n->h[k + 1], n->mask[k + 1], nullptr, st);
   conv_out_fwd_kernel<<<blocks_for(nv, 128), 128, 0, st>>>(db, n->h[4], n->w6r, n->params + n->off_b[5], n->a16,
                                                            n->out);
   TSP_CUDA(cudaGetLastError());
@@ -956,7 +1094,7 @@ extern "C" tsp_status tsp_net_loss_grad(tsp_net n, const float* a, const float* 
     st = wgrad32(d, batch, n->gz, n->h[k], n->grads + n->off_w[k + 1], cs);
     if (st != TSP_OK) return st;
     colsum32_kernel<<<std::min(blocks_for(nv, 8), 152 * 4), 256, 0, cs>>>(n->gz, nv, n->grads + n->off_b[k + 1]);
-    conv32(1, d, batch, n->gz, n->wd[k], nullptr, nullptr, nullptr, nullptr, n->gh, cs);
+    conv32(1, d, batch, n->gz, n->wd[k], nullptr, nullptr, nullptr, n->gh, cs);
   }
   // input layer (ReLU gate applied inside)
   thin_wgrad_kernel<1><<<dim3(chunks, 27), 256, 0, cs>>>(db, nullptr, nullptr, n->gh, n->mask[0], n->a16,
