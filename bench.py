@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--eval", type=int, default=8, help="warm start: held-out phantoms")
     ap.add_argument("--cap", type=int, default=500, help="warm start: cold SIRT iteration cap")
     ap.add_argument("--target", type=float, default=0.01, help="warm start: relative error target")
+    ap.add_argument("--ws-lr", type=float, default=2e-3, help="warm start: peak Adam step size (cosine decay)")
     return ap.parse_args()
 
 
@@ -558,8 +559,8 @@ def run_warmstart(args):
     """Learned warm start vs plain SIRT: 64x48x96 grid, 48 cone views of 256^2 (50 deg,
     orbit radius 60), 1% noise. Train the network on fresh phantoms, then on held-out
     phantoms time (a) warm: input + network + SIRT iterations, (b) cold: SIRT from 0,
-    each to the error target (or, if cold SIRT never reaches it within the cap, to the
-    cold solver's best error)."""
+    each to the error target (or, if cold SIRT never reaches it within the cap, to within
+    5% of the cold solver's best error), errors evaluated after every iteration."""
     import torch
 
     from paper_2608_16960_gb300 import synth
@@ -573,7 +574,7 @@ def run_warmstart(args):
     tuned = tsp_autotune(ws.grid, ws.geom)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = ws.train(args.train_samples, batch=8, lr=1e-3, seed0=1000)
+    losses = ws.train(args.train_samples, batch=8, lr=args.ws_lr, seed0=1000)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
 
@@ -601,16 +602,18 @@ def run_warmstart(args):
         s = 900001 + i
         rho = ws.phantoms([s])
         y = ws.measure(rho, [s])[0]
-        _, cold, _ = ws.sirt_curve(y, rho[0], torch.zeros_like(rho[0]), args.cap, every=5)
+        _, cold, _ = ws.sirt_curve(y, rho[0], torch.zeros_like(rho[0]), args.cap, every=1)
         x0 = ws.warm_start(y)
-        _, warm, _ = ws.sirt_curve(y, rho[0], x0, max(20, args.cap // 5), every=1)
-        target = args.target if min(cold) <= args.target else min(cold)
-        k_cold = next(5 * j for j, v in enumerate(cold) if v <= target * (1 + 1e-9))
-        k_warm = next((j for j, v in enumerate(warm) if v <= target * (1 + 1e-9)), None)
+        _, warm, _ = ws.sirt_curve(y, rho[0], x0, args.cap, every=1)
+        # the error target, or (when 1% noise puts it out of reach) within 5% of the cold solver's best
+        target = args.target if min(cold) <= args.target else 1.05 * min(cold)
+        k_cold = next(j for j, v in enumerate(cold) if v <= target)
+        k_warm = next((j for j, v in enumerate(warm) if v <= target), None)
         results.append({"seed": s, "target": target, "cold_iters": k_cold, "cold_time_s": k_cold * t_iter,
-                         "cold_err_at_20": cold[4], "cold_best": min(cold),
-                         "warm_iters": k_warm, "warm_time_s": None if k_warm is None else t_warm0 + k_warm * t_iter,
-                         "warm_err_at_0": warm[0], "warm_err_at_20": warm[20]})
+                        "cold_err_at_20": cold[min(20, len(cold) - 1)], "cold_best": min(cold),
+                        "warm_iters": k_warm, "warm_time_s": None if k_warm is None else t_warm0 + k_warm * t_iter,
+                        "warm_err_at_0": warm[0], "warm_err_at_20": warm[min(20, len(warm) - 1)],
+                        "warm_best": min(warm)})
     ok = [r for r in results if r["warm_time_s"] is not None]
     out = {"metric": "time to target relative error, learned warm start vs plain SIRT", "unit": "s",
            "higher_is_better": False, "dtype": "bf16 net / f32 projector", "data": "synthetic",

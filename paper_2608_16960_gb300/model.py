@@ -14,7 +14,7 @@ import ctypes
 import numpy as np
 import torch
 
-from . import _lib
+from . import _lib, synth
 from ._lib import check
 from .projector import _require_cuda, _stream
 
@@ -158,6 +158,20 @@ class WarmStartNet:
             out.append((off, sh))
             off += int(np.prod(sh))
         return out
+
+    def init_params(self, seed: int = 0):
+        """Seeded He initialisation (normal, std sqrt(2 / fan_in), fan_in = 27 x
+        input channels), scaled by 1/2 in the four residual layers and by 1/10
+        in the output layer so that the untrained network stays close to its
+        input; biases zero. Draws from synth.SplitMix64."""
+        rng = synth.SplitMix64(seed)
+        flat = np.zeros(self.n_params, np.float32)
+        layers = self.layout()
+        for k in range(6):
+            off, sh = layers[2 * k]
+            std = np.sqrt(2.0 / (27 * sh[2])) * (0.1 if k == 5 else (0.5 if k > 0 else 1.0))
+            flat[off:off + int(np.prod(sh))] = (std * rng.normal(int(np.prod(sh)))).astype(np.float32)
+        self.set_params(flat)
 
     def set_params(self, flat: np.ndarray):
         flat = np.ascontiguousarray(flat, dtype=np.float32)

@@ -11,6 +11,7 @@ Torch holds the buffers and computes the reported error metrics.
 from __future__ import annotations
 
 import ctypes
+import math
 import time
 
 import numpy as np
@@ -42,6 +43,7 @@ class WarmStart:
         self.noise_frac = noise_frac
         self.max_batch = max_batch
         self.net = WarmStartNet(self.shape, max_batch)
+        self.net.init_params(seed=7)
         L = _lib.load()
         self.R = torch.empty(self.geom.n_rays, device="cuda")
         self.C = torch.empty(self.shape, device="cuda")
@@ -79,7 +81,7 @@ class WarmStart:
         B = y.shape[0]
         yr = y.clone()
         check(L.tsp_mul_bcast(_p(yr), _p(self.R), self.geom.n_rays, B, _st()), "tsp_mul_bcast")
-        a = tsp_adjoint(self.grid, self.geom, yr)
+        a = self.segs.adjoint(yr) if self.segs is not None else tsp_adjoint(self.grid, self.geom, yr)
         check(L.tsp_mul_bcast(_p(a), _p(self.C), self.V, B, _st()), "tsp_mul_bcast")
         scale = torch.empty(B, device="cuda")
         check(L.tsp_batch_max(_p(a), self.V, B, _p(scale), _st()), "tsp_batch_max")
@@ -95,14 +97,17 @@ class WarmStart:
         return a, t, y, rho, scale
 
     # ---- training -----------------------------------------------------------
-    def train(self, n_samples, batch=8, lr=1e-3, seed0=1000, log_every=0):
+    def train(self, n_samples, batch=8, lr=1e-3, seed0=1000, log_every=0, cosine=True):
+        """Adam on fresh phantoms, `batch` per step; with cosine=True the step
+        size decays from lr to lr / 20 along a half cosine."""
         losses = []
         steps = (n_samples + batch - 1) // batch
         for s in range(steps):
             seeds = [seed0 + s * batch + i for i in range(batch)]
             a, t, _, _, _ = self.batch(seeds)
             losses.append(self.net.loss_grad(a, t))
-            self.net.adam(lr=lr)
+            f = 0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * s / max(1, steps))) if cosine else 1.0
+            self.net.adam(lr=lr * f)
             if log_every and s % log_every == 0:
                 print(f"step {s}/{steps} loss {losses[-1]:.4e}", flush=True)
         return losses

@@ -59,6 +59,16 @@ def test_net_input_matches_oracle(ws):
     assert abs(scale[0].item() - ref.max()) <= 1e-4 * ref.max()
 
 
+def test_network_starts_initialised(ws):
+    """A fresh warm-start network has seeded non-zero weights (an all-zero
+    ReLU network has no gradient in its inner layers and cannot train)."""
+    p = ws.net.get_params()
+    for k, (off, sh) in enumerate(ws.net.layout()[0::2]):
+        w = p[off:off + int(np.prod(sh))]
+        assert np.std(w) > 0, k
+        assert abs(np.std(w) / np.sqrt(2.0 / (27 * sh[2])) - (1.0 if k == 0 else (0.1 if k == 5 else 0.5))) < 0.1, k
+
+
 def test_training_improves_on_the_input(ws):
     losses = ws.train(n_samples=320, batch=4, lr=2e-3, seed0=1000)
     assert np.mean(losses[-20:]) < np.mean(losses[:20])  # fresh phantoms every batch: a noisy but falling loss
