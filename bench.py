@@ -38,6 +38,10 @@ UNIT = "rays/s"
 # the derivation is written out in the design notes.
 OPS_PER_SEGMENT = 13.0
 SMS, FP32_LANES_PER_SM = 152, 128
+# DRAM bytes (read + write) per list entry of the forward stream kernel, from one
+# ncu capture of a smaller case of the same kernel (4 + 4 views of the paper-scale
+# workload; the traffic grows with the entries streamed), scaled to a full launch.
+STREAM_DRAM_BYTES_PER_ENTRY = 8.38
 
 
 def parse():
@@ -432,7 +436,8 @@ def time_segment_lists(args, grid, geoms, rho, ws, flush, stream, n_rays, n_segs
            "ms_per_step": 1e3 * (t_fwd + t_adj) / args.steps, "build_s": t_build,
            "list_bytes": sum(b for _, _, b in info), "segments": n_segs,
            "roofline": {"bound": "hbm", "achieved": bw_f if dom_f else bw_a, "peak": hbm, "unit": "GB/s",
-                        "frac": (bw_f if dom_f else bw_a) / hbm, "traffic": None,
+                        "frac": (bw_f if dom_f else bw_a) / hbm,
+                        "traffic": (STREAM_DRAM_BYTES_PER_ENTRY * n_segs / len(segs)) if dom_f else None,
                         "kernel": "seg_stream_kernel (forward, ray-major)" if dom_f else
                         "row_gather_kernel (adjoint, voxel-major)",
                         "fwd_gbs": bw_f, "adj_gbs": bw_a, "fwd_frac": bw_f / hbm, "adj_frac": bw_a / hbm},
@@ -550,7 +555,7 @@ def run_differentiation(args):
            "rays_per_s_fwd_adj": geom.n_rays * args.adam_steps / t,
            "config": {"workload": "SH L<=8 x 20 B-splines on 128x64x128, 64 cone views 512^2, 1% noise",
                       "lr": args.lr, "launch_fwd_adj": tuned},
-           "loss_first": float(first), "loss_last": float(loss), "noise_energy": noise_floor,
+           "loss_first": float(first), "loss_last": float(loss.detach()), "noise_energy": noise_floor,
            "coeff_rel_error": rel}
     print(json.dumps(out), flush=True)
 
