@@ -71,7 +71,8 @@ def parse():
 
 
 def dist_env():
-    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2608_16960_gb300.dist import rank_env
+    return rank_env()
 
 
 class ClockSampler:
@@ -288,12 +289,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_fwd = sum(e[0].elapsed_time(e[1]) for e in evs)  # ms
     t_adj = sum(e[1].elapsed_time(e[2]) for e in evs)
-    t_tot = t_fwd + t_adj
-    if dist:
-        t = torch.tensor([t_tot], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_tot = float(t.item())
-    value = world * n_rays * args.steps / (t_tot / 1e3)
+    from paper_2608_16960_gb300.dist import job_throughput, max_over_ranks
+    t_tot = max_over_ranks(t_fwd + t_adj, device="cuda")
+    value = job_throughput(n_rays * args.steps, t_tot / 1e3, world)
 
     # end to end through the public API: pinned host buffers, H2D + compute + D2H
     e2e = None
@@ -324,14 +322,10 @@ def run_ours(args):
             e2e_step()
         e1.record()
         torch.cuda.synchronize()
-        te = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(e0.elapsed_time(e1), device="cuda")
         h2d = h_rho.numel() * 4 + sum(h.numel() * 4 for h in h_ws)
         d2h = sum(h.numel() * 4 for h in h_ys) + sum(h.numel() * 4 for h in h_gs)
-        e2e = {"value": world * n_rays * ke / (te / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_throughput(n_rays * ke, te / 1e3, world), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
     peaks, peak_kind = measured_peaks()
@@ -418,12 +412,9 @@ def time_segment_lists(args, grid, geoms, rho, ws, flush, stream, n_rays, n_segs
     torch.cuda.synchronize()
     t_fwd = sum(e[0].elapsed_time(e[1]) for e in evs) / 1e3
     t_adj = sum(e[1].elapsed_time(e[2]) for e in evs) / 1e3
-    world = 1
-    if dist:
-        t = torch.tensor([t_fwd, t_adj], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_fwd, t_adj = (float(v) for v in t.tolist())
-        world = dist.get_world_size()
+    from paper_2608_16960_gb300.dist import max_over_ranks
+    t_fwd, t_adj = max_over_ranks(t_fwd, device="cuda"), max_over_ranks(t_adj, device="cuda")
+    world = dist.get_world_size() if dist else 1
     V = grid.voxels
     fwd_bytes = sum(8 * ns + 8 * (nr + 1) + 4 * nr for nr, ns, _ in info) + 4 * V * len(segs)
     adj_bytes = sum(8 * ns + 8 * (V + 1) + 4 * V + 4 * nr for nr, ns, _ in info)

@@ -50,6 +50,7 @@ namespace tsp {
 #define T_SQRT(a) __fsqrt_rn(a)
 #define T_RCP(a) __frcp_rn(a)
 #define T_DIV(a, b) __fdividef(a, b)
+#define T_SQRTA(a) sqrt_approx_(a)
 #else
 #define TSP_HD __host__ __device__ inline
 #define T_MUL(a, b) ((a) * (b))
@@ -58,6 +59,19 @@ namespace tsp {
 #define T_SQRT(a) sqrtf(a)
 #define T_RCP(a) (1.0f / (a))
 #define T_DIV(a, b) ((a) / (b))
+#define T_SQRTA(a) sqrtf(a)
+#endif
+
+#if defined(__CUDA_ARCH__)
+// Hardware square root (sqrt.approx.f32, about 1 ulp) for the per-crossing
+// formulas: every crossing of every ray takes one, and the correctly rounded
+// square root costs several more instructions on paths that diverge within a
+// warp. The once-per-ray float-float set-up keeps the rounded one (T_SQRT).
+__device__ __forceinline__ float sqrt_approx_(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 #endif
 
 // Grid tables as seen by a kernel (pointers into shared memory).
@@ -231,7 +245,7 @@ TSP_HD void radial_next(const TGrid& G, RayState& s) {
     const int k = s.ir;  // inner sphere of the current shell
     const float dk = k >= 0 ? sphere_disc(G, s, k) : -1.0f;
     if (dk > 0.0f) {
-      s.tr = -T_SQRT(dk);
+      s.tr = -T_SQRTA(dk);
       s.ir_next = k - 1;
       return;
     }
@@ -239,7 +253,7 @@ TSP_HD void radial_next(const TGrid& G, RayState& s) {
   }
   const int k = s.ir + 1;  // outer sphere of the current shell
   if (k <= G.Nr) {
-    s.tr = T_SQRT(fmaxf(sphere_disc(G, s, k), 0.0f));
+    s.tr = T_SQRTA(fmaxf(sphere_disc(G, s, k), 0.0f));
     s.ir_next = k;
   } else {
     s.tr = INFINITY;
@@ -255,11 +269,11 @@ TSP_HD float cone_w(const TGrid& G, const RayState& s, int k) {
   const float a0 = T_MUL(s.mxy2.hi, G.S2[k]);
   const float b0 = T_MUL(s.mz2.hi, G.K2[k]);
   const float w2f = T_SUB(a0, b0);
-  if (w2f >= T_MUL(0.25f, T_ADD(a0, b0))) return T_SQRT(w2f);
+  if (w2f >= T_MUL(0.25f, T_ADD(a0, b0))) return T_SQRTA(w2f);
   const ff a = ff_mul(s.mxy2, ff{G.S2[k], G.S2L[k]});
   const ff b = ff_mul(s.mz2, ff{G.K2[k], G.K2L[k]});
   const float w2 = T_ADD(T_SUB(a.hi, b.hi), T_SUB(a.lo, b.lo));
-  return T_SQRT(fmaxf(w2, 0.0f));
+  return T_SQRTA(fmaxf(w2, 0.0f));
 }
 
 TSP_HD void theta_next(const TGrid& G, RayState& s) {
