@@ -15,7 +15,9 @@
 // mma.sync m16n8k16 with ldmatrix.trans on both operands; its shared-memory
 // rows (64 bytes = 32 channels) are XOR-swizzled in 16-byte chunks so that
 // eight consecutive rows hit disjoint banks.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <vector>
@@ -129,19 +131,22 @@ __device__ __forceinline__ void mma16816(float* c, const uint32_t* a, uint32_t b
 constexpr int WROWS = 27 * CH + 2;  // weight rows per chunk plane (+2: chunk planes 32 bytes off a bank period)
 constexpr long long TC_WAIT_BUDGET = 2000000000LL;
 
-// Tiles per chunk and shell-buffer size for an azimuth count (host and device agree).
+// Tiles per chunk and shell-buffer geometry for an azimuth count (host and
+// device agree). Slab columns per theta-row: the N_a bins plus the two halo
+// columns, padded to a multiple of 8 so that every TMA box (8 channels x N_a
+// bins of one theta-row, stored from column 1) starts on a 128-byte boundary
+// of its chunk plane; the data start at buffer row TC_BASE.
+constexpr int TC_BASE = 7;
 struct TcPlan {
-  int T, nrows, SBP;
+  int T, colsP, nrows, SBP;
   size_t smem;
 };
 __host__ __device__ inline TcPlan tc_plan(int Na) {
-  const int cols = Na + 2;
-  TcPlan pl{1, 0, 0, 0};
+  TcPlan pl{1, (Na + 2 + 7) / 8 * 8, 0, 0, 0};
   for (int T = 4; T >= 1; --T) {
     pl.T = T;
-    pl.nrows = (128 * T - 1) / cols + 4;  // theta-rows the T tiles touch, plus the theta halo
-    const int SB = pl.nrows * cols + 2;   // + row 0 (zero) and one row for the largest tap shift
-    pl.SBP = (SB + 7) / 8 * 8 + 2;        // chunk planes 32 bytes off a 128-byte bank period
+    pl.nrows = (128 * T - 1) / pl.colsP + 4;              // theta-rows the T tiles touch, plus the theta halo
+    pl.SBP = (TC_BASE + pl.nrows * pl.colsP + 2 + 7) / 8 * 8;  // + the largest tap shift; planes 128-byte aligned
     pl.smem = 3 * size_t(pl.SBP) * 64 + size_t(WROWS) * 64;
     if (pl.smem <= 232448 - 256) break;
   }
@@ -185,32 +190,54 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Load shell rr of sample b for the chunk whose first theta-row is e_lo + 1
-// into a shell buffer: row 1 + j * cols + p <- theta-row e_lo + j, halo column
-// p (azimuth p - 1, wrapped), zero-filled outside the grid. Run by `nt`
-// threads (a multiple of 4), lt = 0..nt-1; waits for its own copies.
-__device__ __forceinline__ void tc_load_shell(const Dims& d, const bf16* __restrict__ X, int b, int rr, int e_lo,
-                                              int nrows, int SBP, unsigned char* buf, int lt, int nt) {
-  const int Na = d.Na, cols = Na + 2;
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// One 5-D tiled TMA box (coordinates innermost first) into shared memory,
+// completion counted in bytes on `bar`.
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                           uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+      "[%7];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Load shell rr of sample b, for the chunk whose first output theta-row is
+// e_lo + 1, into a shell buffer (one warp): buffer row TC_BASE + j * colsP + p
+// holds theta-row e_lo + j, column p (p = 1..N_a: azimuth p - 1; p = 0 and
+// N_a + 1: the periodic halo, azimuths N_a - 1 and 0). Lane 0 registers the
+// bytes and issues one TMA box per (theta-row, chunk plane) for columns
+// 1..N_a (zeros outside the grid); all lanes copy the halo columns with
+// 16-byte cp.async (zero-filled outside the grid), then arrive on `bar`.
+__device__ __forceinline__ void tc_load_shell(const CUtensorMap* map, const Dims& d, const bf16* __restrict__ X, int b,
+                                              int rr, int e_lo, const TcPlan& pl, unsigned char* buf, uint64_t* bar,
+                                              int lane) {
+  const int Na = d.Na;
+  if (lane == 0) {
+    mbar_expect_tx(bar, uint32_t(4 * pl.nrows * Na * 16));
+    for (int j = 0; j < pl.nrows; ++j)
+      for (int c = 0; c < 4; ++c)
+        tma_load_5d(buf + size_t(c) * pl.SBP * 16 + size_t(TC_BASE + j * pl.colsP + 1) * 16, map, 8 * c, 0, e_lo + j,
+                    rr, b, bar);
+  }
   const bool shell_ok = rr >= 0 && rr < d.Nr;
-  const int c = lt & 3;
-  const bf16* Xs = X + (size_t(b) * d.V + size_t(shell_ok ? rr : 0) * d.Ne * Na) * CH + c * 8;
-  unsigned char* dst0 = buf + size_t(c) * SBP * 16 + 16;  // data starts at row 1
-  int j = (lt >> 2) / cols, p = (lt >> 2) - j * cols;
-  const int step = nt >> 2;  // buffer rows advanced per loop step
-  for (int i = lt; i < nrows * cols * 4; i += nt) {
+  for (int i = lane; i < pl.nrows * 8; i += 32) {
+    const int c = i & 3, side = (i >> 2) & 1, j = i >> 3;
     const int ee = e_lo + j;
     const bool ok = shell_ok && ee >= 0 && ee < d.Ne;
-    const int aa = p == 0 ? Na - 1 : (p == cols - 1 ? 0 : p - 1);
-    const bf16* src = ok ? Xs + (int64_t(ee) * Na + aa) * CH : X;
-    cp_async16_zfill(dst0 + size_t(j * cols + p) * 16, src, ok ? 16u : 0u);
-    p += step;
-    while (p >= cols) {
-      p -= cols;
-      ++j;
-    }
+    const int aa = side == 0 ? Na - 1 : 0;
+    const bf16* src = ok ? X + (((size_t(b) * d.Nr + rr) * d.Ne + ee) * Na + aa) * CH + c * 8 : X;
+    cp_async16_zfill(buf + size_t(c) * pl.SBP * 16 + size_t(TC_BASE + j * pl.colsP + (side == 0 ? 0 : Na + 1)) * 16,
+                     src, ok ? 16u : 0u);
   }
   cp_async_wait_all();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // halo copies -> tensor-core reads
+  mbar_arrive(bar);
 }
 
 // Epilogue of one step (run by four warps, warp w reading TMEM lane quarter
@@ -223,7 +250,7 @@ __device__ __forceinline__ void tc_epilogue(const Dims& d, int b, int r, int q, 
                                             const bf16* __restrict__ Xres, const float (&bz)[32],
                                             bf16* __restrict__ Y, uint32_t* __restrict__ mask, float* __restrict__ G,
                                             int warp, int lane) {
-  const int Na = d.Na, cols = Na + 2, P = d.Ne * cols;
+  const int Na = d.Na, cols = tc_plan(Na).colsP, P = d.Ne * cols;
   const int o0 = q * 128 * T;
   const int qd = warp & 3;  // TMEM lane quarter this warp may read
   size_t vox[T];
@@ -233,7 +260,7 @@ __device__ __forceinline__ void tc_epilogue(const Dims& d, int b, int r, int q, 
   for (int t = 0; t < T; ++t) {
     const int o = o0 + 128 * t + 32 * qd + lane;
     const int e = o / cols, p = o - e * cols;
-    valid[t] = o < P && p != 0 && p != cols - 1;
+    valid[t] = o < P && p >= 1 && p <= Na;  // p = 0, N_a + 1 halo, beyond: padding
     vox[t] = valid[t] ? ((size_t(b) * d.Nr + r) * d.Ne + e) * Na + (p - 1) : 0;
     if (MODE == 0) {
       const uint4* xr = reinterpret_cast<const uint4*>(Xres + vox[t] * CH);
@@ -294,9 +321,6 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile
   }
   return true;
 }
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 // Warp-collective forms: the whole warp executes them (operands warp-uniform),
 // one elected lane issues the MMA / the commit.
 __device__ __forceinline__ void tc_mma_elect(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
@@ -313,36 +337,35 @@ __device__ __forceinline__ void tc_commit_elect(uint64_t* bar) {
       : "memory");
 }
 
-constexpr int TC_LOADERS = 96;  // warps 1-3
 
 template <int MODE>
-__global__ void __launch_bounds__(256, 1) conv32_tc_kernel(Dims d, int rseg, const bf16* __restrict__ X,
-                                                           const bf16* __restrict__ W, const float* __restrict__ bias,
-                                                           bf16* __restrict__ Y, uint32_t* __restrict__ mask,
-                                                           float* __restrict__ G) {
+__global__ void __launch_bounds__(256, 1) conv32_tc_kernel(const __grid_constant__ CUtensorMap xmap, Dims d, int rseg,
+                                                           const bf16* __restrict__ X, const bf16* __restrict__ W,
+                                                           const float* __restrict__ bias, bf16* __restrict__ Y,
+                                                           uint32_t* __restrict__ mask, float* __restrict__ G) {
   extern __shared__ __align__(128) unsigned char smem[];
-  // full[s]: shell slot s loaded (96 loader arrivals); empty[s]: its last MMA done (commit);
+  // full[s]: shell slot s loaded (32 loader arrivals + TMA bytes); empty[s]: its last MMA done (commit);
   // tfull[j]: TMEM buffer j holds a finished step (commit); tempty[j]: drained (128 epilogue arrivals)
   __shared__ __align__(8) uint64_t full[3], empty[3], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
-  const int Na = d.Na, cols = Na + 2, P = d.Ne * cols;
-  const TcPlan pl = tc_plan(Na);
-  const int T = pl.T, nrows = pl.nrows, SBP = pl.SBP;
+  const TcPlan pl = tc_plan(d.Na);
+  const int cols = pl.colsP, P = d.Ne * cols;
+  const int T = pl.T, SBP = pl.SBP;
   const uint32_t ncols = T == 1 ? 64u : (T == 2 ? 128u : 256u);  // two accumulator buffers of T * 32 columns
   unsigned char* s_w = smem + 3 * size_t(SBP) * 64;           // 4 chunk planes x WROWS rows x 16 B
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nq = (P + 128 * T - 1) / (128 * T), nseg = (d.Nr + rseg - 1) / rseg;
   const int items = d.B * nq * nseg;
 
-  // ---- set-up, all threads: pad rows, weights, barriers, TMEM ----
-  const int pad = SBP - nrows * cols;  // row 0 and the rows past the data stay zero
-  for (int i = tid; i < 3 * pad * 4; i += blockDim.x) {
-    const int k = i >> 2, c = i & 3, slot = k / pad, kr = k - slot * pad;
-    const int row = kr == 0 ? 0 : nrows * cols + kr;
-    *reinterpret_cast<uint4*>(smem + size_t(slot) * SBP * 64 + size_t(c) * SBP * 16 + size_t(row) * 16) =
-        make_uint4(0, 0, 0, 0);
+  if (smem_u32(smem) & 127u) {  // TMA boxes need 128-byte aligned destinations: report, touch nothing
+    if (tid == 0) atomicOr(&g_conv_error_word, 2);
+    return;
   }
+  // ---- set-up, all threads: zero the shell buffers (pad rows and padding columns stay zero), weights,
+  // barriers, TMEM ----
+  for (int i = tid; i < 3 * SBP * 4; i += blockDim.x)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
   for (int i = tid; i < 27 * CH * 4; i += blockDim.x) {  // row = tap * 32 + output channel, K = input channel
     const int row = i >> 2, c = i & 3;
     cp_async16(s_w + size_t(c) * WROWS * 16 + row * 16, W + size_t(row) * CH + c * 8);
@@ -352,7 +375,7 @@ __global__ void __launch_bounds__(256, 1) conv32_tc_kernel(Dims d, int rseg, con
   if (tid == 0) {
     s_abort = 0;
     for (int s = 0; s < 3; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(TC_LOADERS) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 32;" ::"r"(smem_u32(&full[s])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
     }
     for (int j = 0; j < 2; ++j) {
@@ -406,7 +429,7 @@ __global__ void __launch_bounds__(256, 1) conv32_tc_kernel(Dims d, int rseg, con
               for (int dai = 0; dai < 3; ++dai) {
                 const int tap = dri * 9 + dei * 3 + dai;
                 // first A row of this tap's window: input column p + dai - 1, stored one row down
-                const uint32_t srow = uint32_t(orel + (dei - 1) * cols + dai);
+                const uint32_t srow = uint32_t(orel + (dei - 1) * cols + dai + TC_BASE - 1);
 #pragma unroll
                 for (int kk = 0; kk < 2; ++kk) {
                   const uint64_t ad = xd0 + ((srow * 16u + uint32_t(kk) * 2u * lbo_x) >> 4);
@@ -430,8 +453,7 @@ __global__ void __launch_bounds__(256, 1) conv32_tc_kernel(Dims d, int rseg, con
       }
     }
     __syncwarp();
-  } else if (warp < 4) {  // ---- shell loaders ----
-    const int lt = tid - 32;
+  } else if (warp == 1) {  // ---- shell loader ----
     int G0 = 0;
     bool go = true;
     for (int item = blockIdx.x; item < items && go; item += gridDim.x) {
@@ -440,17 +462,15 @@ __global__ void __launch_bounds__(256, 1) conv32_tc_kernel(Dims d, int rseg, con
       const int e_lo = q * 128 * T / cols - 1;
       for (int j = 0; j < n + 2; ++j) {
         const int Gl = G0 + j, slot = Gl % 3;
-        if (Gl >= 3 && !tc_wait(&empty[slot], uint32_t(Gl / 3 - 1) & 1u, &s_abort)) {
+        if (Gl >= 3 && !__all_sync(0xffffffffu, tc_wait(&empty[slot], uint32_t(Gl / 3 - 1) & 1u, &s_abort))) {
           go = false;
           break;
         }
-        tc_load_shell(d, X, b, r0 - 1 + j, e_lo, nrows, SBP, smem + size_t(slot) * SBP * 64, lt, TC_LOADERS);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // copies -> tensor-core reads
-        mbar_arrive(&full[slot]);
+        tc_load_shell(&xmap, d, X, b, r0 - 1 + j, e_lo, pl, smem + size_t(slot) * SBP * 64, &full[slot], lane);
       }
       G0 += n + 2;
     }
-  } else {  // ---- epilogue ----
+  } else if (warp >= 4) {  // ---- epilogue (warps 4-7; warps 2-3 idle) ----
     float bz[32];
 #pragma unroll
     for (int c = 0; c < 32; ++c) bz[c] = MODE == 0 ? bias[c] : 0.0f;
@@ -854,11 +874,38 @@ struct tsp_net_s {
   double* loss = nullptr;
   std::vector<void*> allocs;
   int adam_step = 0;
+  CUtensorMap map_h[5];  // TMA descriptors of the activations h1..h5 (inputs of the 32 -> 32 layers)
+  CUtensorMap map_gz;    // and of the gated gradient (input of dgrad)
 };
 
 namespace {
 
 size_t wgrad_smem(int Na) { return size_t(9 * (Na + 2)) * 64 + size_t(Na) * 64; }
+
+// TMA descriptor of a bf16 activation tensor [B][N_r][N_e][N_a][32]: a 5-D
+// tiled map (channels innermost) whose box is 8 channels x N_a azimuths, i.e.
+// one 16-byte chunk of every voxel of a theta-row; out-of-range theta-rows and
+// shells read as zeros.
+tsp_status encode_act_map(CUtensorMap* m, const bf16* base, const Dims& d) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    TSP_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) return fail(TSP_ECUDA, "cuTensorMapEncodeTiled is not available");
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[5] = {cuuint64_t(CH), cuuint64_t(d.Na), cuuint64_t(d.Ne), cuuint64_t(d.Nr), cuuint64_t(d.B)};
+  const cuuint64_t strides[4] = {cuuint64_t(CH) * 2, cuuint64_t(CH) * 2 * d.Na, cuuint64_t(CH) * 2 * d.Na * d.Ne,
+                                 cuuint64_t(CH) * 2 * d.Na * d.Ne * d.Nr};
+  const cuuint32_t box[5] = {8u, cuuint32_t(d.Na), 1u, 1u, 1u};
+  const cuuint32_t es[5] = {1u, 1u, 1u, 1u, 1u};
+  const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(base), dims, strides, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(TSP_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(int(r)) + ")");
+  return TSP_OK;
+}
 
 template <class T>
 tsp_status net_alloc(tsp_net n, T** p, size_t count) {
@@ -882,8 +929,8 @@ tsp_status set_attrs(int Na) {
 
 // Persistent launch: work items (sample, chunk, run of rseg shells), about
 // four per multiprocessor, one CTA per multiprocessor (its shared memory).
-void conv32(int mode, const Dims& d, int B, const bf16* X, const bf16* W, const float* bias, bf16* Y, uint32_t* mask,
-            float* G, cudaStream_t st) {
+void conv32(int mode, const Dims& d, int B, const CUtensorMap& xmap, const bf16* X, const bf16* W, const float* bias,
+            bf16* Y, uint32_t* mask, float* G, cudaStream_t st) {
   Dims db = d;
   db.B = B;
   const TcPlan pl = tc_plan(d.Na);
@@ -893,8 +940,8 @@ void conv32(int mode, const Dims& d, int B, const bf16* X, const bf16* W, const 
   const int rseg = int(std::max<int64_t>(2, std::min<int64_t>(d.Nr, steps / (4 * int64_t(g_sm_count)))));
   const int64_t items = int64_t(B) * nq * ((d.Nr + rseg - 1) / rseg);
   const unsigned grid = unsigned(std::min<int64_t>(items, g_sm_count));
-  if (mode == 0) conv32_tc_kernel<0><<<grid, 256, pl.smem, st>>>(db, rseg, X, W, bias, Y, mask, G);
-  else conv32_tc_kernel<1><<<grid, 256, pl.smem, st>>>(db, rseg, X, W, bias, Y, mask, G);
+  if (mode == 0) conv32_tc_kernel<0><<<grid, 256, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
+  else conv32_tc_kernel<1><<<grid, 256, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
 }
 
 template <int NA>
@@ -946,7 +993,8 @@ tsp_status net_forward(tsp_net n, const float* a, int B, cudaStream_t st) {
   conv_in_fwd_kernel<<<blocks_for(nv, 128), 128, 0, st>>>(db, n->a16, n->w1r, n->params + n->off_b[0], n->h[0],
                                                           n->mask[0]);
   for (int k = 0; k < 4; ++k)
-    conv32(0, d, B, n->h[k], n->wf[k], n->params + n->off_b[k + 1], n->h[k + 1], n->mask[k + 1], nullptr, st);
+    conv32(0, d, B, n->map_h[k], n->h[k], n->wf[k], n->params + n->off_b[k + 1], n->h[k + 1], n->mask[k + 1], nullptr,
+           st);
   conv_out_fwd_kernel<<<blocks_for(nv, 128), 128, 0, st>>>(db, n->h[4], n->w6r, n->params + n->off_b[5], n->a16,
                                                            n->out);
   TSP_CUDA(cudaGetLastError());
@@ -999,6 +1047,8 @@ extern "C" tsp_status tsp_net_create(int n_r, int n_e, int n_a, int max_batch, t
   if (st == TSP_OK) st = net_alloc(n, &n->gz, nv * CH);
   if (st == TSP_OK) st = net_alloc(n, &n->loss, 1);
   if (st == TSP_OK) st = set_attrs(n_a);
+  for (int k = 0; k < 5 && st == TSP_OK; ++k) st = encode_act_map(&n->map_h[k], n->h[k], n->d);
+  if (st == TSP_OK) st = encode_act_map(&n->map_gz, n->gz, n->d);
   if (st == TSP_OK) {
     switch (n_a) {
       case 32: st = wgrad_attr<32>(); break;
@@ -1094,7 +1144,7 @@ extern "C" tsp_status tsp_net_loss_grad(tsp_net n, const float* a, const float* 
     st = wgrad32(d, batch, n->gz, n->h[k], n->grads + n->off_w[k + 1], cs);
     if (st != TSP_OK) return st;
     colsum32_kernel<<<std::min(blocks_for(nv, 8), 152 * 4), 256, 0, cs>>>(n->gz, nv, n->grads + n->off_b[k + 1]);
-    conv32(1, d, batch, n->gz, n->wd[k], nullptr, nullptr, nullptr, n->gh, cs);
+    conv32(1, d, batch, n->map_gz, n->gz, n->wd[k], nullptr, nullptr, nullptr, n->gh, cs);
   }
   // input layer (ReLU gate applied inside)
   thin_wgrad_kernel<1><<<dim3(chunks, 27), 256, 0, cs>>>(db, nullptr, nullptr, n->gh, n->mask[0], n->a16,
