@@ -8,9 +8,11 @@
 //
 // The 32 -> 32 layers are implicit GEMMs (M = voxels, N = 32, K = 27 taps x 32).
 // Forward and dgrad run on the tcgen05 tensor cores with TMEM accumulators
-// (conv32_tc_kernel): every tap is one 128-row window of a shared-memory slab
-// of the neighbouring rows, so one descriptor per tap addresses it; dgrad is
-// the same kernel with the mirrored, transposed kernel. The weight gradient
+// (conv32_tc_kernel): for each (r, theta) tap pair one 128-row window of a
+// shared-memory slab of the neighbouring rows is the A operand and the three
+// phi taps' weights side by side are B (N = 96), so one MMA computes all three
+// phi taps of a window; the epilogue adds them with a one-row shift each.
+// dgrad is the same kernel with the mirrored, transposed kernel. The weight gradient
 // (M = N = 32 per tap, K = voxels: too narrow for a 128-row tcgen05 tile) uses
 // mma.sync m16n8k16 with ldmatrix.trans on both operands; its shared-memory
 // rows (64 bytes = 32 channels) are XOR-swizzled in 16-byte chunks so that
@@ -135,20 +137,38 @@ constexpr long long TC_WAIT_BUDGET = 2000000000LL;
 // device agree). Slab columns per theta-row: the N_a bins plus the two halo
 // columns, padded to a multiple of 8 so that every TMA box (8 channels x N_a
 // bins of one theta-row, stored from column 1) starts on a 128-byte boundary
-// of its chunk plane; the data start at buffer row TC_BASE.
+// of its chunk plane; the data start at buffer row TC_BASE. A 128-row tile
+// yields TC_TOUT outputs (its first and last rows only feed their neighbours'
+// azimuth taps), T tiles per chunk; a chunk's inputs span nrows theta-rows.
 constexpr int TC_BASE = 7;
+constexpr int TC_TOUT = 126;
+// Epilogue: TC_ESPLIT warps per TMEM lane quarter, each with TC_ECH of the 32
+// output channels; the CTA is an MMA warp, a loader warp, two idle warps and
+// the epilogue warps (2 per quarter measured as fast as 4, fewer threads).
+#ifndef TC_ESPLIT
+#define TC_ESPLIT 2
+#endif
+constexpr int TC_ECH = 32 / TC_ESPLIT;
+constexpr int TC_EPI_THREADS = 128 * TC_ESPLIT;
+constexpr int TC_THREADS = 128 + TC_EPI_THREADS;
+// Most tiles per step (2: two TMEM buffers of 192 columns, measured faster
+// than 1 tile per step with five buffers of 96).
+#ifndef TC_TILES
+#define TC_TILES 2
+#endif
 struct TcPlan {
-  int T, colsP, nrows, SBP;
+  int T, NB, colsP, nrows, SBP;  // NB: accumulator buffers of T x 96 TMEM columns (of 512)
   size_t smem;
 };
 __host__ __device__ inline TcPlan tc_plan(int Na) {
-  TcPlan pl{1, (Na + 2 + 7) / 8 * 8, 0, 0, 0};
-  for (int T = 4; T >= 1; --T) {
+  TcPlan pl{1, 5, (Na + 2 + 7) / 8 * 8, 0, 0, 0};
+  for (int T = TC_TILES; T >= 1; --T) {
     pl.T = T;
-    pl.nrows = (128 * T - 1) / pl.colsP + 4;              // theta-rows the T tiles touch, plus the theta halo
-    pl.SBP = (TC_BASE + pl.nrows * pl.colsP + 2 + 7) / 8 * 8;  // + the largest tap shift; planes 128-byte aligned
+    pl.NB = 512 / (96 * T);
+    pl.nrows = TC_TOUT * T / pl.colsP + 4;
+    pl.SBP = (TC_BASE + pl.nrows * pl.colsP + 2 + 7) / 8 * 8;  // + the largest shift; planes 128-byte aligned
     pl.smem = 3 * size_t(pl.SBP) * 64 + size_t(WROWS) * 64;
-    if (pl.smem <= 232448 - 256) break;
+    if (pl.smem <= 232448 - 1024) break;  // static shared memory: barriers, the epilogue's row exchange
   }
   return pl;
 }
@@ -163,8 +183,8 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint3
          (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
 }
 // Instruction descriptor, kind::f16: f32 accumulator, bf16 A and B, both
-// K-major, N = 32, M = 128.
-constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// K-major, N = 96 (three azimuth taps x 32 output channels), M = 128.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((96u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
@@ -175,20 +195,23 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
-      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+// N consecutive accumulator columns (N = 8 or 16) of this thread's TMEM lane, no wait.
+template <int N>
+__device__ __forceinline__ void tmem_ld_nowait(uint32_t taddr, uint32_t (&r)[N]) {
+  static_assert(N == 8 || N == 16, "8 or 16 columns");
+  if constexpr (N == 16) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+  } else {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+  }
 }
+__device__ __forceinline__ void tmem_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -240,45 +263,101 @@ __device__ __forceinline__ void tc_load_shell(const CUtensorMap* map, const Dims
   mbar_arrive(bar);
 }
 
-// Epilogue of one step (run by four warps, warp w reading TMEM lane quarter
-// w & 3): the accumulators of output shell r, chunk q, sit in TMEM columns
-// [col0, col0 + T * 32). Forward: y = x + relu(z + bias) with x the layer
-// input (the residual), plus the ReLU mask; dgrad: G += z. The residual rows
-// of all T tiles are requested before the first accumulator is read.
+// Epilogue of one step (run by the four epilogue warps, warp w reading TMEM
+// lane quarter w & 3). Tile t's accumulators sit in TMEM columns col0 + 96 t:
+// row m holds, for position c_m = o0 + 126 t - 1 + m, the three azimuth-tap
+// partial sums z_dai(c_m) (32 columns each). The output at c_m is
+// z_0(c_m - 1) + z_1(c_m) + z_2(c_m + 1): rows m - 1 and m + 1 come from the
+// neighbouring lanes by shuffle and, across a warp boundary, through `xch`.
+// Rows m = 1..126 are outputs. Forward: y = x + relu(z + bias) with x the
+// layer input (the residual), plus the ReLU mask; dgrad: G += z.
+// TC_ESPLIT warps share each TMEM lane quarter: channel group `hf` handles
+// output channels TC_ECH hf .. TC_ECH (hf + 1) - 1. The voxel of row m in tile t is vb[t] + roff
+// (vb per work item, roff = r N_e N_a per radial step), if valid[t].
+// Operands read back from memory (the residual x, or the gradient being
+// accumulated) are fetched by tc_epilogue_fetch before the step's
+// accumulators are ready, so their latency overlaps the wait.
+template <int MODE>
+struct EpiIn {
+  uint4 x[2][TC_ECH / 8];   // forward: residual, this warp's channels of each tile's row
+  float4 g[2][TC_ECH / 4];  // dgrad: G, this warp's channels of each tile's row
+};
 template <int MODE, int T>
-__device__ __forceinline__ void tc_epilogue(const Dims& d, int b, int r, int q, uint32_t tmem, uint32_t col0,
-                                            const bf16* __restrict__ Xres, const float (&bz)[32],
-                                            bf16* __restrict__ Y, uint32_t* __restrict__ mask, float* __restrict__ G,
-                                            int warp, int lane) {
-  const int Na = d.Na, cols = tc_plan(Na).colsP, P = d.Ne * cols;
-  const int o0 = q * 128 * T;
-  const int qd = warp & 3;  // TMEM lane quarter this warp may read
-  size_t vox[T];
-  bool valid[T];
-  uint4 xv[MODE == 0 ? T : 1][4];
+__device__ __forceinline__ void tc_epilogue_fetch(size_t roff, const size_t (&vb)[2], const bool (&valid)[2],
+                                                  const bf16* __restrict__ Xres, const float* __restrict__ G, int hf,
+                                                  EpiIn<MODE>& in) {
+  const int c0 = TC_ECH * hf;
 #pragma unroll
   for (int t = 0; t < T; ++t) {
-    const int o = o0 + 128 * t + 32 * qd + lane;
-    const int e = o / cols, p = o - e * cols;
-    valid[t] = o < P && p >= 1 && p <= Na;  // p = 0, N_a + 1 halo, beyond: padding
-    vox[t] = valid[t] ? ((size_t(b) * d.Nr + r) * d.Ne + e) * Na + (p - 1) : 0;
+    const size_t vox = valid[t] ? vb[t] + roff : 0;
     if (MODE == 0) {
-      const uint4* xr = reinterpret_cast<const uint4*>(Xres + vox[t] * CH);
+      const uint4* xr = reinterpret_cast<const uint4*>(Xres + vox * CH + c0);
 #pragma unroll
-      for (int h = 0; h < 4; ++h) xv[MODE == 0 ? t : 0][h] = valid[t] ? xr[h] : make_uint4(0, 0, 0, 0);
+      for (int h = 0; h < TC_ECH / 8; ++h) in.x[t][h] = valid[t] ? xr[h] : make_uint4(0, 0, 0, 0);
+    } else {
+      const float4* gp = reinterpret_cast<const float4*>(G + vox * CH + c0);
+#pragma unroll
+      for (int h = 0; h < TC_ECH / 4; ++h) in.g[t][h] = valid[t] ? gp[h] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
+}
+// Empty asm through which a value passes: the compiler may not compute with
+// it earlier (it would wait for the load there).
+__device__ __forceinline__ void pin(uint4& v) { asm volatile("" : "+r"(v.x), "+r"(v.y), "+r"(v.z), "+r"(v.w)); }
+__device__ __forceinline__ void pin(float4& v) { asm volatile("" : "+f"(v.x), "+f"(v.y), "+f"(v.z), "+f"(v.w)); }
+
+template <int MODE, int T>
+__device__ __forceinline__ void tc_epilogue(size_t roff, const size_t (&vb)[2], const bool (&valid)[2],
+                                            uint32_t tmem, uint32_t col0, EpiIn<MODE>& in, const float (&bz)[TC_ECH],
+                                            bf16* __restrict__ Y, uint32_t* __restrict__ mask, float* __restrict__ G,
+                                            int qd, int hf, int lane, float (*xch)[2][32]) {
+  const int c0 = TC_ECH * hf;
 #pragma unroll
   for (int t = 0; t < T; ++t) {
-    float acc[32];
-    tmem_ld32(tmem + (uint32_t(32 * qd) << 16) + col0 + uint32_t(t) * 32, acc);
+    uint32_t r0[TC_ECH], r1[TC_ECH], r2[TC_ECH];
+    const uint32_t ta = tmem + (uint32_t(32 * qd) << 16) + col0 + uint32_t(t) * 96 + uint32_t(c0);
+    tmem_ld_nowait(ta, r0);
+    tmem_ld_nowait(ta + 32, r1);
+    tmem_ld_nowait(ta + 64, r2);
+    tmem_wait();
+    const size_t vox = valid[t] ? vb[t] + roff : 0;
+    float (*xb)[2][32] = xch + 4 * (t & 1);  // exchange buffer of this tile (alternating)
+    if (lane == 31)
+#pragma unroll
+      for (int j = 0; j < TC_ECH; ++j) xb[qd][0][c0 + j] = __uint_as_float(r0[j]);
+    if (lane == 0)
+#pragma unroll
+      for (int j = 0; j < TC_ECH; ++j) xb[qd][1][c0 + j] = __uint_as_float(r2[j]);
+    asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI_THREADS) : "memory");
+    // neighbours' taps: rows m-1 (columns 0..31) and m+1 (columns 64..95);
+    // all shuffles first so that their latencies overlap
+    float up[TC_ECH], dn[TC_ECH], acc[TC_ECH];
+#pragma unroll
+    for (int j = 0; j < TC_ECH; ++j) up[j] = __shfl_up_sync(0xffffffffu, __uint_as_float(r0[j]), 1);
+#pragma unroll
+    for (int j = 0; j < TC_ECH; ++j) dn[j] = __shfl_down_sync(0xffffffffu, __uint_as_float(r2[j]), 1);
+    if (lane == 0)
+#pragma unroll
+      for (int j = 0; j < TC_ECH; ++j) up[j] = qd > 0 ? xb[qd - 1][0][c0 + j] : 0.0f;
+    if (lane == 31)
+#pragma unroll
+      for (int j = 0; j < TC_ECH; ++j) dn[j] = qd < 3 ? xb[qd + 1][1][c0 + j] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < TC_ECH; ++j) acc[j] = up[j] + __uint_as_float(r1[j]) + dn[j];
     if (!valid[t]) continue;
     if (MODE == 0) {
-      uint32_t bits = 0;
-      uint4* yo = reinterpret_cast<uint4*>(Y + vox[t] * CH);
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const __nv_bfloat162* x2 = reinterpret_cast<const __nv_bfloat162*>(&xv[MODE == 0 ? t : 0][h]);
+      for (int h = 0; h < TC_ECH / 8; ++h) pin(in.x[t][h]);
+    } else {
+#pragma unroll
+      for (int h = 0; h < TC_ECH / 4; ++h) pin(in.g[t][h]);
+    }
+    if (MODE == 0) {
+      uint32_t bits = 0;
+      uint4* yo = reinterpret_cast<uint4*>(Y + vox * CH + c0);
+#pragma unroll
+      for (int h = 0; h < TC_ECH / 8; ++h) {
+        const __nv_bfloat162* x2 = reinterpret_cast<const __nv_bfloat162*>(&in.x[t][h]);
         uint4 ov;
         __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(&ov);
 #pragma unroll
@@ -292,20 +371,35 @@ __device__ __forceinline__ void tc_epilogue(const Dims& d, int b, int r, int q, 
         }
         yo[h] = ov;
       }
-      mask[vox[t]] = bits;
+      // the mask word's 16-bit half for these channels (little-endian words)
+      if (TC_ECH == 16) reinterpret_cast<uint16_t*>(mask)[2 * vox + hf] = uint16_t(bits);
+      else reinterpret_cast<uint8_t*>(mask)[4 * vox + hf] = uint8_t(bits);
     } else {
-      float4* gp = reinterpret_cast<float4*>(G + vox[t] * CH);
+      float4* gp = reinterpret_cast<float4*>(G + vox * CH + c0);
 #pragma unroll
-      for (int h = 0; h < 8; ++h) {
-        float4 gv = gp[h];
-        gv.x += acc[4 * h];
-        gv.y += acc[4 * h + 1];
-        gv.z += acc[4 * h + 2];
-        gv.w += acc[4 * h + 3];
-        gp[h] = gv;
+      for (int h = 0; h < TC_ECH / 4; ++h) {
+        float4 g = in.g[t][h];
+        g.x += acc[4 * h];
+        g.y += acc[4 * h + 1];
+        g.z += acc[4 * h + 2];
+        g.w += acc[4 * h + 3];
+        gp[h] = g;
       }
     }
   }
+}
+
+// AND of `p` over the epilogue threads (named barrier 1): their decision to
+// go on or give up is taken together, so none waits at the epilogue's named
+// barriers for a warp that has left.
+__device__ __forceinline__ bool epilogue_and(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.and.pred po, 1, %2, pi;\n selp.u32 %0, 1, 0, po;\n}"
+      : "=r"(r)
+      : "r"(uint32_t(p)), "n"(TC_EPI_THREADS)
+      : "memory");
+  return r != 0;
 }
 
 // Bounded wait on an mbarrier phase that also gives up when another role of
@@ -339,23 +433,25 @@ __device__ __forceinline__ void tc_commit_elect(uint64_t* bar) {
 
 
 template <int MODE>
-__global__ void __launch_bounds__(256, 1) conv32_tc_kernel(const __grid_constant__ CUtensorMap xmap, Dims d, int rseg,
+__global__ void __launch_bounds__(TC_THREADS, 1) conv32_tc_kernel(const __grid_constant__ CUtensorMap xmap, Dims d, int rseg,
                                                            const bf16* __restrict__ X, const bf16* __restrict__ W,
                                                            const float* __restrict__ bias, bf16* __restrict__ Y,
                                                            uint32_t* __restrict__ mask, float* __restrict__ G) {
   extern __shared__ __align__(128) unsigned char smem[];
   // full[s]: shell slot s loaded (32 loader arrivals + TMA bytes); empty[s]: its last MMA done (commit);
-  // tfull[j]: TMEM buffer j holds a finished step (commit); tempty[j]: drained (128 epilogue arrivals)
-  __shared__ __align__(8) uint64_t full[3], empty[3], tfull[2], tempty[2];
+  // tfull[j]: TMEM buffer j holds a finished step (commit); tempty[j]: drained (one arrival per epilogue thread)
+  __shared__ __align__(8) uint64_t full[3], empty[3], tfull[5], tempty[5];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int s_abort;
+  __shared__ float xch[8][2][32];  // epilogue: accumulator rows that cross a warp boundary (two tiles)
   const TcPlan pl = tc_plan(d.Na);
   const int cols = pl.colsP, P = d.Ne * cols;
   const int T = pl.T, SBP = pl.SBP;
-  const uint32_t ncols = T == 1 ? 64u : (T == 2 ? 128u : 256u);  // two accumulator buffers of T * 32 columns
+  const int NB = pl.NB;
+  const uint32_t ncols = 512u;  // NB accumulator buffers of T x 96 columns
   unsigned char* s_w = smem + 3 * size_t(SBP) * 64;           // 4 chunk planes x WROWS rows x 16 B
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nq = (P + 128 * T - 1) / (128 * T), nseg = (d.Nr + rseg - 1) / rseg;
+  const int nq = (P + TC_TOUT * T - 1) / (TC_TOUT * T), nseg = (d.Nr + rseg - 1) / rseg;
   const int items = d.B * nq * nseg;
 
   if (smem_u32(smem) & 127u) {  // TMA boxes need 128-byte aligned destinations: report, touch nothing
@@ -378,9 +474,10 @@ __global__ void __launch_bounds__(256, 1) conv32_tc_kernel(const __grid_constant
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 32;" ::"r"(smem_u32(&full[s])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
     }
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < NB; ++j) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull[j])) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&tempty[j])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tempty[j])), "n"(TC_EPI_THREADS)
+                   : "memory");
     }
   }
   if (warp == 0) {
@@ -395,24 +492,25 @@ __global__ void __launch_bounds__(256, 1) conv32_tc_kernel(const __grid_constant
   const uint32_t tmem = tmem_base;
 
   // Every role walks the same sequence: items, their steps r = r0..r1-1 (global
-  // step K, TMEM buffer K & 1) and their shell loads r0-1..r1 (global load G,
+  // step K, TMEM buffer K mod NB) and their shell loads r0-1..r1 (global load G,
   // slot G % 3, the n-th use of a slot being phase n of its barriers).
   if (warp == 0) {  // ---- MMA issuer: the warp walks the schedule, one elected lane issues ----
     const uint32_t lbo_x = uint32_t(SBP) * 16, lbo_w = uint32_t(WROWS) * 16;
     const uint64_t wd0 = umma_desc(smem_u32(s_w), lbo_w, 128);
-    int K = 0, G0 = 0;
+    int K = 0, G0 = 0, kb = 0;  // step, shell loads so far, TMEM buffer of step K
+    uint32_t kph = 0;          // phase of buffer kb's barriers for step K
     bool go = true;
     for (int item = blockIdx.x; item < items && go; item += gridDim.x) {
       const int seg = item % nseg, q = (item / nseg) % nq;
       const int r0 = seg * rseg, n = min(rseg, d.Nr - r0);
-      const int o0 = q * 128 * T, e_lo = o0 / cols - 1;
+      const int o0 = q * TC_TOUT * T, e_lo = (o0 - 1 + cols) / cols - 2;  // floor((o0 - 1) / cols) - 1
       for (int i = 0; i < n && go; ++i, ++K) {
-        if (K >= 2 && !__all_sync(0xffffffffu, tc_wait(&tempty[K & 1], uint32_t((K >> 1) - 1) & 1u, &s_abort))) {
+        if (K >= NB && !__all_sync(0xffffffffu, tc_wait(&tempty[kb], kph ^ 1u, &s_abort))) {
           go = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t acc0 = tmem + uint32_t(K & 1) * uint32_t(T) * 32;
+        const uint32_t acc0 = tmem + uint32_t(kb) * uint32_t(T) * 96;
         for (int dri = 0; dri < 3 && go; ++dri) {
           const int Gl = G0 + i + dri, slot = Gl % 3;
           if (!__all_sync(0xffffffffu, tc_wait(&full[slot], uint32_t(Gl / 3) & 1u, &s_abort))) {
@@ -422,28 +520,26 @@ __global__ void __launch_bounds__(256, 1) conv32_tc_kernel(const __grid_constant
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint64_t xd0 = umma_desc(smem_u32(smem + size_t(slot) * SBP * 64), lbo_x, 128);
           for (int t = 0; t < T; ++t) {
-            const int orel = o0 + 128 * t - e_lo * cols;
+            // tile rows m = 0..127 are the positions o0 + 126 t - 1 + m (input column p of each)
+            const int orel = o0 + TC_TOUT * t - 1 - e_lo * cols;
 #pragma unroll
             for (int dei = 0; dei < 3; ++dei) {
+              const uint32_t srow = uint32_t(orel + (dei - 1) * cols + TC_BASE);
 #pragma unroll
-              for (int dai = 0; dai < 3; ++dai) {
-                const int tap = dri * 9 + dei * 3 + dai;
-                // first A row of this tap's window: input column p + dai - 1, stored one row down
-                const uint32_t srow = uint32_t(orel + (dei - 1) * cols + dai + TC_BASE - 1);
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                  const uint64_t ad = xd0 + ((srow * 16u + uint32_t(kk) * 2u * lbo_x) >> 4);
-                  const uint64_t bd = wd0 + ((uint32_t(tap) * CH * 16u + uint32_t(kk) * 2u * lbo_w) >> 4);
-                  tc_mma_elect(acc0 + uint32_t(t) * 32, ad, bd, (tap | kk) != 0);
-                }
+              for (int kk = 0; kk < 2; ++kk) {
+                // B: the three azimuth taps (dri, dei, 0..2) x 32 output channels, contiguous rows
+                const uint64_t ad = xd0 + ((srow * 16u + uint32_t(kk) * 2u * lbo_x) >> 4);
+                const uint64_t bd = wd0 + ((uint32_t(dri * 9 + dei * 3) * CH * 16u + uint32_t(kk) * 2u * lbo_w) >> 4);
+                tc_mma_elect(acc0 + uint32_t(t) * 96, ad, bd, (dri | dei | kk) != 0);
               }
             }
           }
           if (dri == 0 || i == n - 1) tc_commit_elect(&empty[slot]);  // this load's last use
           __syncwarp();
         }
-        if (go) tc_commit_elect(&tfull[K & 1]);
+        if (go) tc_commit_elect(&tfull[kb]);
         __syncwarp();
+        if (++kb == NB) kb = 0, kph ^= 1u;
       }
       G0 += n + 2;
     }
@@ -459,7 +555,7 @@ __global__ void __launch_bounds__(256, 1) conv32_tc_kernel(const __grid_constant
     for (int item = blockIdx.x; item < items && go; item += gridDim.x) {
       const int seg = item % nseg, rest = item / nseg, q = rest % nq, b = rest / nq;
       const int r0 = seg * rseg, n = min(rseg, d.Nr - r0);
-      const int e_lo = q * 128 * T / cols - 1;
+      const int e_lo = (q * TC_TOUT * T - 1 + cols) / cols - 2;
       for (int j = 0; j < n + 2; ++j) {
         const int Gl = G0 + j, slot = Gl % 3;
         if (Gl >= 3 && !__all_sync(0xffffffffu, tc_wait(&empty[slot], uint32_t(Gl / 3 - 1) & 1u, &s_abort))) {
@@ -470,29 +566,47 @@ __global__ void __launch_bounds__(256, 1) conv32_tc_kernel(const __grid_constant
       }
       G0 += n + 2;
     }
-  } else if (warp >= 4) {  // ---- epilogue (warps 4-7; warps 2-3 idle) ----
-    float bz[32];
+  } else if (warp >= 4) {  // ---- epilogue (TC_ESPLIT warps per TMEM lane quarter; warps 2-3 idle) ----
+    const int qd = warp & 3;         // TMEM lane quarter this warp may read
+    const int hf = (warp >> 2) - 1;  // channel group: TC_ECH channels from TC_ECH hf
+    const int m = 32 * qd + lane;    // tile row of this thread
+    const size_t plane = size_t(d.Ne) * d.Na;
+    float bz[TC_ECH];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) bz[c] = MODE == 0 ? bias[c] : 0.0f;
-    int K = 0;
+    for (int c = 0; c < TC_ECH; ++c) bz[c] = MODE == 0 ? bias[TC_ECH * hf + c] : 0.0f;
+    int K = 0, kb = 0;
+    uint32_t kph = 0;
     bool go = true;
     for (int item = blockIdx.x; item < items && go; item += gridDim.x) {
       const int seg = item % nseg, rest = item / nseg, q = rest % nq, b = rest / nq;
       const int r0 = seg * rseg, n = min(rseg, d.Nr - r0);
+      // row m of tile t is position c = o0 + 126 t - 1 + m of the (theta, padded phi) plane
+      size_t vb[2];
+      bool vv[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int c = q * TC_TOUT * T + TC_TOUT * t - 1 + m;
+        const int e = c >= 0 ? c / cols : -1, p = c - e * cols;
+        vv[t] = t < T && m >= 1 && m <= TC_TOUT && c < P && p >= 1 && p <= d.Na;
+        vb[t] = vv[t] ? (size_t(b) * d.Nr * d.Ne + e) * d.Na + (p - 1) : 0;
+      }
       for (int i = 0; i < n; ++i, ++K) {
-        const bool ok = __all_sync(0xffffffffu, tc_wait(&tfull[K & 1], uint32_t(K >> 1) & 1u, &s_abort));
+        const size_t roff = size_t(r0 + i) * plane;
+        EpiIn<MODE> in;
+        if (T == 2) tc_epilogue_fetch<MODE, 2>(roff, vb, vv, X, G, hf, in);
+        else tc_epilogue_fetch<MODE, 1>(roff, vb, vv, X, G, hf, in);
+        const bool ok = epilogue_and(tc_wait(&tfull[kb], kph, &s_abort));
         if (!ok) {
           go = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t col0 = uint32_t(K & 1) * uint32_t(T) * 32;
-        if (T == 4) tc_epilogue<MODE, 4>(d, b, r0 + i, q, tmem, col0, X, bz, Y, mask, G, warp, lane);
-        else if (T == 2) tc_epilogue<MODE, 2>(d, b, r0 + i, q, tmem, col0, X, bz, Y, mask, G, warp, lane);
-        else if (T == 3) tc_epilogue<MODE, 3>(d, b, r0 + i, q, tmem, col0, X, bz, Y, mask, G, warp, lane);
-        else tc_epilogue<MODE, 1>(d, b, r0 + i, q, tmem, col0, X, bz, Y, mask, G, warp, lane);
+        const uint32_t col0 = uint32_t(kb) * uint32_t(T) * 96;
+        if (T == 2) tc_epilogue<MODE, 2>(roff, vb, vv, tmem, col0, in, bz, Y, mask, G, qd, hf, lane, xch);
+        else tc_epilogue<MODE, 1>(roff, vb, vv, tmem, col0, in, bz, Y, mask, G, qd, hf, lane, xch);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        mbar_arrive(&tempty[K & 1]);
+        mbar_arrive(&tempty[kb]);
+        if (++kb == NB) kb = 0, kph ^= 1u;
       }
     }
   }
@@ -935,13 +1049,13 @@ void conv32(int mode, const Dims& d, int B, const CUtensorMap& xmap, const bf16*
   db.B = B;
   const TcPlan pl = tc_plan(d.Na);
   const int P = d.Ne * (d.Na + 2);
-  const int nq = (P + 128 * pl.T - 1) / (128 * pl.T);
+  const int nq = (P + TC_TOUT * pl.T - 1) / (TC_TOUT * pl.T);
   const int64_t steps = int64_t(B) * nq * d.Nr;
   const int rseg = int(std::max<int64_t>(2, std::min<int64_t>(d.Nr, steps / (4 * int64_t(g_sm_count)))));
   const int64_t items = int64_t(B) * nq * ((d.Nr + rseg - 1) / rseg);
   const unsigned grid = unsigned(std::min<int64_t>(items, g_sm_count));
-  if (mode == 0) conv32_tc_kernel<0><<<grid, 256, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
-  else conv32_tc_kernel<1><<<grid, 256, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
+  if (mode == 0) conv32_tc_kernel<0><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
+  else conv32_tc_kernel<1><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
 }
 
 template <int NA>
