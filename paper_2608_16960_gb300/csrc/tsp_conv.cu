@@ -865,100 +865,217 @@ __global__ void conv_out_dgrad_kernel(Dims d, const float* __restrict__ gout, co
   for (int j = 0; j < 8; ++j) dst[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
 }
 
-// Weight gradient of a one-sided layer (one channel on one side, 32 on the other):
-//   mode 0 (output layer): dw[tap][ci] += sum_v g1[v] X32[v + d][ci],  db += sum g1
-//   mode 1 (input layer):  dw[tap][co] += sum_v (gh[v][co] if mask) a1[v + d], db[co] += sum
-// grid (27 taps, chunks); each thread keeps 32 partial sums, then block reduction.
+// ---------------------------------------------------------------------------
+// Weight gradients of the one-sided layers (one channel on one side, 32 on the
+// other), in one pass over the voxels:
+//   mode 0 (output layer 32 -> 1): dw[tap][c] = sum_v g1[v] X[v + d_tap][c]
+//                                            = sum_u X[u][c] g1[u - d_tap],  db = sum g1
+//   mode 1 (input layer 1 -> 32):  dw[tap][c] = sum_v gz[v][c] a1[v + d_tap],
+//                                  gz = g_h where the pre-activation was positive, db[c] = sum gz
+// Both read dw[tap][c] = sum_u P[u][c] s(u + sigma d_tap): P the 32-channel
+// operand (X, or the gated g_h), s the scalar field (g1, or a1), sigma = -1 / +1.
+// A CTA stages a tile of ET theta-rows of P (float) and the 3 x (ET + 2) rows
+// of s around it in shared memory; 16 groups of 16 threads (one channel pair
+// each) walk runs along phi with the 3 x 3 x 3 window of s in registers
+// (27 taps x 2 channels of partial sums per thread). Each CTA writes its sums
+// to its row of `part` (THIN_OUT floats: 27 x 32 weights, then 32 biases);
+// part_reduce_kernel adds the rows in a fixed order (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int THIN_OUT = 27 * CH + CH;
+
+// theta-rows per tile: the largest power of two <= 16 with ET N_a <= 384
+inline int thin_et(int Na) {
+  int et = 1;
+  while (et < 16 && 2 * et * Na <= 384) et *= 2;
+  return et;
+}
+inline size_t thin_smem(int Na) {
+  const int et = thin_et(Na);
+  return size_t(et) * Na * CH * sizeof(float) + size_t(3) * (et + 2) * Na * sizeof(float);
+}
+
 template <int MODE>
-__global__ void thin_wgrad_kernel(Dims d, const float* __restrict__ g1, const bf16* __restrict__ X32,
-                                  const float* __restrict__ gh, const uint32_t* __restrict__ mask,
-                                  const bf16* __restrict__ a1, float* __restrict__ dw, float* __restrict__ db) {
-  const int tap = blockIdx.y;
-  const int dr = tap / 9 - 1, de = (tap / 3) % 3 - 1, da = tap % 3 - 1;
-  float acc[CH], accb[CH];
+__global__ void __launch_bounds__(256, 2) thin_wgrad_kernel(Dims d, int ET, const float* __restrict__ g1,
+                                                            const bf16* __restrict__ X32, const float* __restrict__ gh,
+                                                            const uint32_t* __restrict__ mask,
+                                                            const bf16* __restrict__ a1, float* __restrict__ part) {
+  extern __shared__ __align__(16) float thin_sm[];
+  __shared__ float red[8][THIN_OUT];
+  const int Na = d.Na, ETS = ET + 2;
+  float* sP = thin_sm;                      // [ET * Na][32]
+  float* sS = thin_sm + size_t(ET) * Na * CH;  // [3][ET + 2][Na]
+  const int tid = threadIdx.x, g = tid >> 4, cp = tid & 15;
+  const int runs = 16 / ET, el = g / runs, ri = g % runs;
+  const int L = (Na + runs - 1) / runs, a_s = ri * L, a_e = min(Na, a_s + L);
+  float acc[27][2], bacc[2] = {0.0f, 0.0f};
 #pragma unroll
-  for (int c = 0; c < CH; ++c) acc[c] = accb[c] = 0.0f;
-  const int64_t n = int64_t(d.B) * d.V;
-  for (int64_t gi = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; gi < n; gi += int64_t(gridDim.x) * blockDim.x) {
-    const int b = int(gi / d.V);
-    const int64_t v = gi - int64_t(b) * d.V;
-    const int a_ = int(v % d.Na), e = int((v / d.Na) % d.Ne), r = int(v / (int64_t(d.Na) * d.Ne));
-    const int64_t q = nbr(d, r, e, a_, dr, de, da);
-    if (MODE == 0) {
-      const float gv = g1[gi];
-      if (tap == 0) accb[0] += gv;
-      if (q < 0 || gv == 0.0f) continue;
-      const uint4* src = reinterpret_cast<const uint4*>(X32 + (int64_t(b) * d.V + q) * CH);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint4 u = __ldg(src + j);
-        const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&u);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const float2 f = __bfloat1622float2(p[k]);
-          acc[j * 8 + 2 * k] = fmaf(gv, f.x, acc[j * 8 + 2 * k]);
-          acc[j * 8 + 2 * k + 1] = fmaf(gv, f.y, acc[j * 8 + 2 * k + 1]);
-        }
+  for (int t = 0; t < 27; ++t) acc[t][0] = acc[t][1] = 0.0f;
+  const int nET = (d.Ne + ET - 1) / ET;
+  const int64_t tiles = int64_t(d.B) * d.Nr * nET;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int e0 = int(tile % nET) * ET, r = int((tile / nET) % d.Nr), b = int(tile / (int64_t(nET) * d.Nr));
+    const int ETe = min(ET, d.Ne - e0);
+    const int64_t v0 = ((int64_t(b) * d.Nr + r) * d.Ne + e0) * Na;  // first voxel of the tile (rows are contiguous)
+    __syncthreads();  // the previous tile is no longer read
+    for (int i = tid; i < ETe * Na * 8; i += 256) {
+      const int vi = i >> 3, h = i & 7;
+      float4 f;
+      if (MODE == 1) {
+        f = *reinterpret_cast<const float4*>(gh + (v0 + vi) * CH + 4 * h);
+        const uint32_t m = mask[v0 + vi] >> (4 * h);
+        f.x = (m & 1u) ? f.x : 0.0f;
+        f.y = (m & 2u) ? f.y : 0.0f;
+        f.z = (m & 4u) ? f.z : 0.0f;
+        f.w = (m & 8u) ? f.w : 0.0f;
+      } else {
+        const uint2 u = *reinterpret_cast<const uint2*>(X32 + (v0 + vi) * CH + 4 * h);
+        const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+        const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+        f = make_float4(lo.x, lo.y, hi.x, hi.y);
       }
-    } else {
-      const uint32_t m = mask[gi];
-      const float av = q < 0 ? 0.0f : __bfloat162float(a1[int64_t(b) * d.V + q]);
-      const float4* gp = reinterpret_cast<const float4*>(gh + gi * CH);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const float4 gv = __ldg(gp + j);
-        const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int c = 4 * j + k;
-          const float gz = (m >> c) & 1u ? gg[k] : 0.0f;
-          acc[c] = fmaf(gz, av, acc[c]);
-          if (tap == 0) accb[c] += gz;
-        }
+      reinterpret_cast<float4*>(sP)[i] = f;
+    }
+    for (int i = tid; i < 3 * ETS * Na; i += 256) {
+      const int a_ = i % Na, ee = (i / Na) % ETS, rr = i / (Na * ETS);
+      const int rg = r - 1 + rr, eg = e0 - 1 + ee;
+      float v = 0.0f;
+      if (rg >= 0 && rg < d.Nr && eg >= 0 && eg < d.Ne) {
+        const int64_t q = int64_t(b) * d.V + (int64_t(rg) * d.Ne + eg) * Na + a_;
+        v = MODE == 1 ? __bfloat162float(a1[q]) : g1[q];
       }
+      sS[i] = v;
+    }
+    __syncthreads();
+    if (el >= ETe || a_s >= a_e) continue;
+    // window w[or][oe][k]: s at (r + or - 1, e + oe - 1, a + k - 1)
+    float w[3][3][3];
+    const float* srow = sS + size_t(el + 1) * Na;  // (rr, ee) row = srow + ((rr - 1) * ETS + ee - 1) * Na ...
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      int ak = a_s - 1 + k;
+      ak = ak < 0 ? ak + Na : (ak >= Na ? ak - Na : ak);
+#pragma unroll
+      for (int o = 0; o < 3; ++o)
+#pragma unroll
+        for (int oe = 0; oe < 3; ++oe) w[o][oe][k] = srow[(o * ETS + oe - 1) * Na + ak];
+    }
+    const float* pp = sP + (size_t(el) * Na) * CH + 2 * cp;
+    for (int a_ = a_s; a_ < a_e; ++a_) {
+      const float2 p = *reinterpret_cast<const float2*>(pp + size_t(a_) * CH);
+#pragma unroll
+      for (int o = 0; o < 3; ++o)
+#pragma unroll
+        for (int oe = 0; oe < 3; ++oe)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            // mode 1: the window offset is d_tap; mode 0: it is -d_tap
+            const int tap = MODE == 1 ? o * 9 + oe * 3 + k : (2 - o) * 9 + (2 - oe) * 3 + (2 - k);
+            acc[tap][0] = fmaf(p.x, w[o][oe][k], acc[tap][0]);
+            acc[tap][1] = fmaf(p.y, w[o][oe][k], acc[tap][1]);
+          }
+      if (MODE == 1) {
+        bacc[0] += p.x;
+        bacc[1] += p.y;
+      } else if (cp == 0) {
+        bacc[0] += w[1][1][1];  // g1 of this voxel
+      }
+      int an = a_ + 2;
+      an = an >= Na ? an - Na : an;
+      an = an >= Na ? an - Na : an;
+#pragma unroll
+      for (int o = 0; o < 3; ++o)
+#pragma unroll
+        for (int oe = 0; oe < 3; ++oe) {
+          w[o][oe][0] = w[o][oe][1];
+          w[o][oe][1] = w[o][oe][2];
+          w[o][oe][2] = srow[(o * ETS + oe - 1) * Na + an];
+        }
     }
   }
-  __shared__ float red[CH][33];
+  // groups 2w and 2w + 1 share warp w: fold them, then the 8 warps in order
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int t = 0; t < 27; ++t)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const float v = acc[t][j] + __shfl_xor_sync(0xffffffffu, acc[t][j], 16);
+      if (lane < 16) red[warp][t * CH + 2 * cp + j] = v;
+    }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float v = bacc[j] + __shfl_xor_sync(0xffffffffu, bacc[j], 16);
+    if (lane < 16) red[warp][27 * CH + 2 * cp + j] = v;
+  }
+  __syncthreads();
+  for (int i = tid; i < THIN_OUT; i += 256) {
+    float sum = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += red[k][i];
+    part[size_t(blockIdx.x) * THIN_OUT + i] = sum;
+  }
+}
+
+// out[i] += sum_k part[k][i] for i < n (rows of `stride` floats), k in order:
+// 32 outputs per CTA, warp w takes rows w, w + 32, ...
+__global__ void __launch_bounds__(1024) part_reduce_kernel(const float* __restrict__ part, int rows, int stride, int n,
+                                                           float* __restrict__ out) {
+  __shared__ float s[32][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  float v = 0.0f;
+  if (i < n)
+    for (int k = warp; k < rows; k += 32) v += part[size_t(k) * stride + i];
+  s[warp][lane] = v;
+  __syncthreads();
+  if (warp == 0 && i < n) {
+    float t = 0.0f;
+    for (int w = 0; w < 32; ++w) t += s[w][lane];
+    out[i] += t;
+  }
+}
+
+// g_z = bf16(g_h where the forward pre-activation was positive, else 0), 8
+// channels per thread; each CTA also writes its column sums of g_z (the bias
+// gradient, summed over the bf16 values) to its row of `part` (32 floats).
+__global__ void __launch_bounds__(256) gate_kernel(const float* __restrict__ gh, const uint32_t* __restrict__ mask,
+                                                   bf16* __restrict__ gz, int64_t nvox, float* __restrict__ part) {
+  const int q = threadIdx.x & 3;  // channels 8q .. 8q + 7
+  float cs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int64_t v = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 2; v < nvox;
+       v += (int64_t(gridDim.x) * blockDim.x) >> 2) {
+    const float4 f0 = *reinterpret_cast<const float4*>(gh + v * CH + 8 * q);
+    const float4 f1 = *reinterpret_cast<const float4*>(gh + v * CH + 8 * q + 4);
+    const uint32_t m = mask[v] >> (8 * q);
+    const float f[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+    uint4 o;
+    __nv_bfloat162* o2 = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const __nv_bfloat162 z = __floats2bfloat162_rn((m >> (2 * u)) & 1u ? f[2 * u] : 0.0f,
+                                                     (m >> (2 * u + 1)) & 1u ? f[2 * u + 1] : 0.0f);
+      o2[u] = z;
+      const float2 zf = __bfloat1622float2(z);
+      cs[2 * u] += zf.x;
+      cs[2 * u + 1] += zf.y;
+    }
+    *reinterpret_cast<uint4*>(gz + v * CH + 8 * q) = o;
+  }
+  // fold the 8 threads of each channel group in a warp, then the 8 warps in order
+  __shared__ float red[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    float v = acc[c];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    float vb = accb[c];
-    for (int o = 16; o > 0; o >>= 1) vb += __shfl_down_sync(0xffffffffu, vb, o);
-    if (lane == 0) {
-      atomicAdd(dw + tap * CH + c, v);
-      if (tap == 0 && (MODE == 1 || c == 0)) atomicAdd(db + c, vb);
-    }
+  for (int c = 0; c < 8; ++c) {
+    float t = cs[c];
+    t += __shfl_xor_sync(0xffffffffu, t, 4);
+    t += __shfl_xor_sync(0xffffffffu, t, 8);
+    t += __shfl_xor_sync(0xffffffffu, t, 16);
+    if (lane < 4) red[warp][8 * lane + c] = t;
   }
-  (void)red;
-  (void)warp;
-}
-
-// g_z = bf16(g_h where the forward pre-activation was positive, else 0)
-__global__ void gate_kernel(const float* __restrict__ gh, const uint32_t* __restrict__ mask, bf16* __restrict__ gz,
-                            int64_t nvox) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= nvox * CH) return;
-  const int64_t v = i >> 5;
-  const int c = int(i & 31);
-  gz[i] = __float2bfloat16_rn(((mask[v] >> c) & 1u) ? gh[i] : 0.0f);
-}
-
-// db[c] += sum_v gz[v][c]
-__global__ void colsum32_kernel(const bf16* __restrict__ gz, int64_t nvox, float* __restrict__ db) {
-  const int c = threadIdx.x & 31;
-  float acc = 0.0f;
-  for (int64_t v = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); v < nvox;
-       v += int64_t(gridDim.x) * (blockDim.x >> 5))
-    acc += __bfloat162float(gz[v * CH + c]);
-  __shared__ float part[32][33];
-  part[threadIdx.x >> 5][c] = acc;
   __syncthreads();
   if (threadIdx.x < 32) {
-    float s = 0.0f;
-    for (int w = 0; w < int(blockDim.x >> 5); ++w) s += part[w][threadIdx.x];
-    atomicAdd(db + threadIdx.x, s);
+    float t = 0.0f;
+    for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
+    part[size_t(blockIdx.x) * CH + threadIdx.x] = t;
   }
 }
 
@@ -986,6 +1103,8 @@ struct tsp_net_s {
   float *out = nullptr, *gout = nullptr, *gh = nullptr;
   bf16* gz = nullptr;
   double* loss = nullptr;
+  float* part = nullptr;  // per-CTA partial sums of the weight / bias gradient reductions
+  int part_rows = 0;
   std::vector<void*> allocs;
   int adam_step = 0;
   CUtensorMap map_h[5];  // TMA descriptors of the activations h1..h5 (inputs of the 32 -> 32 layers)
@@ -1038,6 +1157,8 @@ tsp_status set_attrs(int Na) {
   int dev = 0;
   TSP_CUDA(cudaGetDevice(&dev));
   TSP_CUDA(cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev));
+  TSP_CUDA(cudaFuncSetAttribute(thin_wgrad_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(thin_smem(Na))));
+  TSP_CUDA(cudaFuncSetAttribute(thin_wgrad_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(thin_smem(Na))));
   return TSP_OK;
 }
 
@@ -1161,6 +1282,10 @@ extern "C" tsp_status tsp_net_create(int n_r, int n_e, int n_a, int max_batch, t
   if (st == TSP_OK) st = net_alloc(n, &n->gz, nv * CH);
   if (st == TSP_OK) st = net_alloc(n, &n->loss, 1);
   if (st == TSP_OK) st = set_attrs(n_a);
+  if (st == TSP_OK) {  // one row per CTA of the reductions (2 per multiprocessor, THIN_OUT floats)
+    n->part_rows = 2 * g_sm_count;
+    st = net_alloc(n, &n->part, size_t(n->part_rows) * THIN_OUT);
+  }
   for (int k = 0; k < 5 && st == TSP_OK; ++k) st = encode_act_map(&n->map_h[k], n->h[k], n->d);
   if (st == TSP_OK) st = encode_act_map(&n->map_gz, n->gz, n->d);
   if (st == TSP_OK) {
@@ -1231,6 +1356,24 @@ extern "C" tsp_status tsp_net_forward(tsp_net n, const float* a, int batch, floa
   return TSP_OK;
 }
 
+namespace {
+// Weight and bias gradient of a one-sided layer (mode 0: output layer from
+// g_out and h5; mode 1: input layer from the gated g_h and a): per-CTA
+// partial sums, then a fixed-order reduction added to dw (27 x 32) and db (nb).
+void thin_wgrad(tsp_net n, int mode, const Dims& db, float* dw, float* dbias, int nb, cudaStream_t cs) {
+  const int et = thin_et(db.Na);
+  const int64_t tiles = int64_t(db.B) * db.Nr * ((db.Ne + et - 1) / et);
+  const int grid = int(std::min<int64_t>(tiles, n->part_rows));
+  const size_t sm = thin_smem(db.Na);
+  if (mode == 0)
+    thin_wgrad_kernel<0><<<grid, 256, sm, cs>>>(db, et, n->gout, n->h[4], nullptr, nullptr, nullptr, n->part);
+  else
+    thin_wgrad_kernel<1><<<grid, 256, sm, cs>>>(db, et, nullptr, nullptr, n->gh, n->mask[0], n->a16, n->part);
+  part_reduce_kernel<<<(27 * CH + 31) / 32, 1024, 0, cs>>>(n->part, grid, THIN_OUT, 27 * CH, dw);
+  part_reduce_kernel<<<1, 1024, 0, cs>>>(n->part + 27 * CH, grid, THIN_OUT, nb, dbias);
+}
+}  // namespace
+
 extern "C" tsp_status tsp_net_loss_grad(tsp_net n, const float* a, const float* target, int batch, double* loss_host,
                                         void* stream) {
   if (!n || !a || !target || batch <= 0 || batch > n->max_batch)
@@ -1248,21 +1391,19 @@ extern "C" tsp_status tsp_net_loss_grad(tsp_net n, const float* a, const float* 
   TSP_CUDA(cudaMemsetAsync(n->grads, 0, sizeof(float) * n->n_params, cs));
   mse_kernel<<<std::min(blocks_for(nv, 256), 152 * 8), 256, 0, cs>>>(n->out, target, nv, n->gout, n->loss);
   // output layer
-  const int chunks = std::max(1, std::min(blocks_for(nv, 256), 152 * 4 / 27 + 1));
-  thin_wgrad_kernel<0><<<dim3(chunks, 27), 256, 0, cs>>>(db, n->gout, n->h[4], nullptr, nullptr, nullptr,
-                                                         n->grads + n->off_w[5], n->grads + n->off_b[5]);
+  thin_wgrad(n, 0, db, n->grads + n->off_w[5], n->grads + n->off_b[5], 1, cs);
   conv_out_dgrad_kernel<<<blocks_for(nv, 128), 128, 0, cs>>>(db, n->gout, n->w6r, n->gh);
   // residual 32 -> 32 layers, last to first
+  const int ggrid = std::min(blocks_for(nv * 4, 256), n->part_rows);
   for (int k = 3; k >= 0; --k) {
-    gate_kernel<<<blocks_for(nv * CH, 256), 256, 0, cs>>>(n->gh, n->mask[k + 1], n->gz, nv);
+    gate_kernel<<<ggrid, 256, 0, cs>>>(n->gh, n->mask[k + 1], n->gz, nv, n->part);
+    part_reduce_kernel<<<1, 1024, 0, cs>>>(n->part, ggrid, CH, CH, n->grads + n->off_b[k + 1]);
     st = wgrad32(d, batch, n->gz, n->h[k], n->grads + n->off_w[k + 1], cs);
     if (st != TSP_OK) return st;
-    colsum32_kernel<<<std::min(blocks_for(nv, 8), 152 * 4), 256, 0, cs>>>(n->gz, nv, n->grads + n->off_b[k + 1]);
     conv32(1, d, batch, n->map_gz, n->gz, n->wd[k], nullptr, nullptr, nullptr, n->gh, cs);
   }
   // input layer (ReLU gate applied inside)
-  thin_wgrad_kernel<1><<<dim3(chunks, 27), 256, 0, cs>>>(db, nullptr, nullptr, n->gh, n->mask[0], n->a16,
-                                                         n->grads + n->off_w[0], n->grads + n->off_b[0]);
+  thin_wgrad(n, 1, db, n->grads + n->off_w[0], n->grads + n->off_b[0], CH, cs);
   TSP_CUDA(cudaGetLastError());
   if (loss_host) {
     TSP_CUDA(cudaMemcpyAsync(loss_host, n->loss, sizeof(double), cudaMemcpyDeviceToHost, cs));

@@ -97,6 +97,21 @@ def test_gradients_match_oracle(shaped):
             assert np.linalg.norm(gg - rr) <= 2e-2 * np.linalg.norm(rr) + 1e-9, (k, which)
 
 
+def test_one_sided_and_bias_gradients_are_deterministic(shaped):
+    """The one-sided layers' weight gradients and every bias gradient come from
+    per-CTA partial sums added in a fixed order: repeated calls agree bit for bit."""
+    shape, B, params, a, t, net = shaped
+    at, tt = torch.tensor(a, device=DEV), torch.tensor(t, device=DEV)
+    net.loss_grad(at, tt)
+    g1 = _unflat(net.get_grads())
+    net.loss_grad(at, tt)
+    g2 = _unflat(net.get_grads())
+    for k in range(6):
+        assert np.array_equal(g1[k][1], g2[k][1]), k
+    for k in (0, 5):
+        assert np.array_equal(g1[k][0], g2[k][0]), k
+
+
 def test_training_steps_reduce_loss(case):
     """A learnable target (an affine map of the input) is approached by Adam."""
     shape, B, params, a, t, net = case
