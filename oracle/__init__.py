@@ -51,6 +51,8 @@ def lib():
             L.oracle_threads.restype = i
             L.oracle_ray_segments.argtypes = grid + [dp, dp, i, i, lp, dp]
             L.oracle_ray_segments.restype = i
+            L.oracle_ray_pieces.argtypes = grid + [dp, dp, i, lp, dp, dp]
+            L.oracle_ray_pieces.restype = i
             L.oracle_forward.argtypes = grid + [i64, dp, dp, dp, i, dp, i, i]
             L.oracle_forward.restype = i
             L.oracle_adjoint.argtypes = grid + [i64, dp, dp, dp, i, dp, i]
@@ -105,6 +107,25 @@ def ray_segments(edges, x, n, method: int = 0, cap: int = 4096):
     if cnt > cap:
         return ray_segments(edges, x, n, method, cnt)
     return vox[:cnt].copy(), ln[:cnt].copy()
+
+
+def ray_pieces(edges, x, n, cap: int = 4096):
+    """Pieces of one ray by the definition (Eq. 4): flat voxel index, start
+    distance l0 along the normalised direction, and length."""
+    keep, ga = _grid_args(edges)
+    xa, xp = _d(x)
+    na, np_ = _d(n)
+    vox = np.zeros(cap, dtype=np.int64)
+    l0 = np.zeros(cap, dtype=np.float64)
+    ln = np.zeros(cap, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    cnt = lib().oracle_ray_pieces(*ga, xp, np_, cap, vox.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  l0.ctypes.data_as(dp), ln.ctypes.data_as(dp))
+    if cnt < 0:
+        raise ValueError("invalid grid")
+    if cnt > cap:
+        return ray_pieces(edges, x, n, cnt)
+    return vox[:cnt].copy(), l0[:cnt].copy(), ln[:cnt].copy()
 
 
 def forward(edges, starts, dirs, rho, method: int = 0, n_threads: int = 0):

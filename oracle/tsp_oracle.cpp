@@ -128,6 +128,7 @@ int quad_roots(double a, double bh, double c, double out[2]) {
 struct Seg {
   int64_t v;
   double len;
+  double l0 = 0.0;  // start of the piece along the unit-direction line (definition method)
 };
 
 void normalise(const double n_in[3], double n[3]) {
@@ -212,7 +213,7 @@ void trace_definition(const Grid& g, const double x[3], const double n_in[3], st
     int ir, ie, ia;
     regions_of(g, m, &ir, &ie, &ia);
     const int64_t v = flat_index(g, ir, ie, ia);
-    if (v >= 0) out->push_back({v, l1 - l0});
+    if (v >= 0) out->push_back({v, l1 - l0, l0});
   }
 }
 
@@ -325,6 +326,23 @@ int oracle_ray_segments(const double* r, int nr1, const double* th, int ne1, con
   else trace_paper(g, x, n, &segs);
   for (int i = 0; i < int(segs.size()) && i < cap; ++i) {
     vox[i] = segs[i].v;
+    len[i] = segs[i].len;
+  }
+  return int(segs.size());
+}
+
+// Pieces of one ray by the definition (method 0), with their start distance
+// along the normalised direction: vox, start l0, length. Returns the count
+// (may exceed cap; only cap written), or -1 for an invalid grid.
+int oracle_ray_pieces(const double* r, int nr1, const double* th, int ne1, const double* ph, int na1,
+                      const double* x, const double* n, int cap, int64_t* vox, double* l0, double* len) {
+  Grid g;
+  if (!make_grid(r, nr1, th, ne1, ph, na1, &g)) return -1;
+  std::vector<Seg> segs;
+  trace_definition(g, x, n, &segs);
+  for (int i = 0; i < int(segs.size()) && i < cap; ++i) {
+    vox[i] = segs[i].v;
+    l0[i] = segs[i].l0;
     len[i] = segs[i].len;
   }
   return int(segs.size());
