@@ -197,6 +197,51 @@ tsp_status tsp_segments_sirt(tsp_segments s, const float* y, float* x, int n_ite
 void tsp_segments_destroy(tsp_segments s);
 
 /*
+ * Attenuated projection (Sec. 9.3, Eq. 14-18): the optically thin model with
+ * the first-order losses of photons from the sun to the scattering point
+ * (optical depth tau_1, Eq. 14) and from there to the observer (tau_2, Eq. 15):
+ *
+ *   y = sum_i rho[v_i] e^{-tau_1[v_i]} e^{-tau_2,i} dl_i                 (Eq. 17)
+ *   tau_2,i = sum_{j <= i} sigma[v_j] rho[v_j] dl_j  (inclusive cumsum, Eq. 18)
+ *   tau_1 = F_1(sigma rho)                                                (Eq. 17)
+ *
+ * Segments i are the maximal runs of a ray in one voxel, in order from the
+ * ray's start (consecutive pieces of one voxel are joined; pieces separated
+ * by a stretch outside the grid stay apart). F_1 traces one ray per voxel
+ * from its centroid toward the sun (Fig. 16b). sigma (the cross-section) and
+ * rho are device float32 (batch, N_r, N_e, N_a); tau_1 has the same shape.
+ *
+ * tsp_sunward_rays - F_1's rays: for every voxel (flat order) its centroid
+ *   (the point at the midpoints of its r, theta, phi edges) and the unit sun
+ *   direction; sun is a host double[3] pointing toward the sun (non-zero).
+ *   starts, dirs: device float32 [3][N_r N_e N_a], written. Pass them to
+ *   tsp_geom_rays to get F_1's geometry.
+ * tsp_atten_optical_depth - tau_1 = F_1(sigma rho) (one value per voxel);
+ *   `sun` is a geometry with one ray per voxel (TSP_EINVAL otherwise).
+ * tsp_atten_optical_depth_adjoint - g_rho += sigma F_1^T g_tau1 and, if
+ *   g_sigma != NULL, g_sigma += rho F_1^T g_tau1 (accumulated: zero first).
+ * tsp_atten_forward - y (batch, n_rays) by Eq. 17-18, overwritten.
+ * tsp_atten_backward - gradients of sum y gy with respect to rho, sigma and
+ *   tau_1 (tau_1 taken as an independent input), ACCUMULATED into g_rho and,
+ *   when not NULL, g_sigma and g_tau1. y must be tsp_atten_forward's output for
+ *   the same inputs (its running prefix is reused). Chain through tau_1 with
+ *   tsp_atten_optical_depth_adjoint(g_tau1).
+ * All of them traverse on the fly like tsp_forward and scatter with atomic
+ * adds; errors as tsp_forward.
+ */
+tsp_status tsp_sunward_rays(tsp_grid grid, const double* sun, float* starts, float* dirs, void* stream);
+tsp_status tsp_atten_optical_depth(tsp_grid grid, tsp_geom sun, const float* rho, const float* sigma, float* tau1,
+                                   int batch, void* stream);
+tsp_status tsp_atten_optical_depth_adjoint(tsp_grid grid, tsp_geom sun, const float* rho, const float* sigma,
+                                           const float* g_tau1, float* g_rho, float* g_sigma, int batch,
+                                           void* stream);
+tsp_status tsp_atten_forward(tsp_grid grid, tsp_geom geom, const float* rho, const float* sigma, const float* tau1,
+                             float* y, int batch, void* stream);
+tsp_status tsp_atten_backward(tsp_grid grid, tsp_geom geom, const float* rho, const float* sigma,
+                              const float* tau1, const float* y, const float* gy, float* g_rho, float* g_sigma,
+                              float* g_tau1, int batch, void* stream);
+
+/*
  * tsp_autotune - times candidate launch knobs (threads per block 64..512, warp
  * tiles 4..32 pixels wide, and for the adjoint the scatter strategy) for this
  * grid and geometry, and caches the fastest per size class (each grid and

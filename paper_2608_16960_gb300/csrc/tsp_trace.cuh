@@ -332,8 +332,20 @@ TSP_HD void phi_next(const TGrid& G, RayState& s) {
   }
 }
 
+// Ops that define gap() are told of every piece of the ray that holds no
+// voxel (inside the inner sphere, outside a wedge) between valid segments.
+template <class Op, class = void>
+struct op_has_gap {
+  static constexpr bool value = false;
+};
+template <class Op>
+struct op_has_gap<Op, decltype(void(static_cast<Op*>(nullptr)->gap()))> {
+  static constexpr bool value = true;
+};
+
 // Trace one ray from start x along direction d (need not be unit).
-// op(voxel, dl) is called for every valid segment in order along the ray.
+// op(voxel, dl) is called for every valid segment in order along the ray
+// (and op.gap() for the pieces in between that hold no voxel, if Op has it).
 // Returns false if the step cap was hit (an internal inconsistency).
 template <class Op>
 TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d[3], Op& op) {
@@ -460,6 +472,8 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d[3], Op& op) {
     const float tn = fminf(s.tr, fminf(s.tth, s.tph));
     if ((unsigned)s.ir < (unsigned)G.Nr && (unsigned)s.ie < (unsigned)G.Ne && s.ia >= 0) {
       op((s.ir * G.Ne + s.ie) * G.Na + s.ia, T_SUB(tn, tcur));
+    } else {
+      if constexpr (op_has_gap<Op>::value) op.gap();
     }
     tcur = tn;
     if (s.tr <= s.tth && s.tr <= s.tph) {

@@ -20,7 +20,7 @@ SO = os.path.join(BUILD, "libtsp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Translation units whose traversal must round identically in every kernel:
 # no implicit multiply-add contraction (explicit fmaf only).
-NO_FMAD = {"tsp_project.cu", "tsp_sirt.cu", "tsp_batch.cu", "tsp_segments.cu", "tsp_noalloc.cu"}
+NO_FMAD = {"tsp_project.cu", "tsp_sirt.cu", "tsp_batch.cu", "tsp_segments.cu", "tsp_noalloc.cu", "tsp_atten.cu"}
 
 
 def nvcc() -> str:

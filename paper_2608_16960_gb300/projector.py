@@ -434,3 +434,153 @@ class Batch:
             except Exception:
                 pass
             self.handle = None
+
+
+# ---------------------------------------------------------------------------
+# Attenuated projection (Sec. 9.3, Eq. 14-18)
+# ---------------------------------------------------------------------------
+
+def _vol_batch(grid: Grid, t: torch.Tensor, name: str) -> int:
+    _require_cuda(t, name)
+    if tuple(t.shape[-3:]) != grid.shape or t.dim() not in (3, 4):
+        raise ValueError(f"{name} shape {tuple(t.shape)} does not match grid {grid.shape}")
+    return t.shape[0] if t.dim() == 4 else 1
+
+
+def sunward_rays(grid: Grid, sun, device=None):
+    """F_1's rays (Fig. 16b): for every voxel (flat order) its centroid and the
+    unit sun direction, as CUDA float32 (3, V) tensors (starts, dirs)."""
+    L = _lib.load()
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    s = np.ascontiguousarray(np.asarray(sun, dtype=np.float64).reshape(3))
+    starts = torch.empty((3, grid.voxels), device=dev, dtype=torch.float32)
+    dirs = torch.empty((3, grid.voxels), device=dev, dtype=torch.float32)
+    check(L.tsp_sunward_rays(grid.handle, _dptr(s), ctypes.c_void_p(starts.data_ptr()),
+                             ctypes.c_void_p(dirs.data_ptr()), _stream(starts)), "tsp_sunward_rays")
+    return starts, dirs
+
+
+def sunward_geometry(grid: Grid, sun, device=None) -> Geometry:
+    """F_1's geometry: one ray per voxel from its centroid toward the sun
+    (`sun`: 3 numbers pointing toward the sun)."""
+    starts, dirs = sunward_rays(grid, sun, device)
+    return Geometry.rays(starts, dirs, copy=True)
+
+
+def optical_depth(grid: Grid, sun_geom: Geometry, rho: torch.Tensor, sigma: torch.Tensor) -> torch.Tensor:
+    """tau_1 = F_1(sigma rho) (Eq. 14, 17), shaped like rho."""
+    B = _vol_batch(grid, rho, "rho")
+    if _vol_batch(grid, sigma, "sigma") != B or sigma.shape != rho.shape:
+        raise ValueError("sigma must have the shape of rho")
+    tau1 = torch.empty_like(rho)
+    L = _lib.load()
+    check(L.tsp_atten_optical_depth(grid.handle, sun_geom.handle, ctypes.c_void_p(rho.data_ptr()),
+                                    ctypes.c_void_p(sigma.data_ptr()), ctypes.c_void_p(tau1.data_ptr()), B,
+                                    _stream(rho)), "tsp_atten_optical_depth")
+    return tau1
+
+
+def optical_depth_adjoint(grid: Grid, sun_geom: Geometry, rho: torch.Tensor, sigma: torch.Tensor,
+                          g_tau1: torch.Tensor, need_sigma: bool = True):
+    """(sigma F_1^T g, rho F_1^T g): gradients of <g, F_1(sigma rho)>."""
+    B = _vol_batch(grid, rho, "rho")
+    for t, nm in ((sigma, "sigma"), (g_tau1, "g_tau1")):
+        _vol_batch(grid, t, nm)
+        if t.shape != rho.shape:
+            raise ValueError(f"{nm} must have the shape of rho")
+    g_rho = torch.zeros_like(rho)
+    g_sigma = torch.zeros_like(rho) if need_sigma else None
+    L = _lib.load()
+    check(L.tsp_atten_optical_depth_adjoint(
+        grid.handle, sun_geom.handle, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(sigma.data_ptr()),
+        ctypes.c_void_p(g_tau1.data_ptr()), ctypes.c_void_p(g_rho.data_ptr()),
+        ctypes.c_void_p(g_sigma.data_ptr()) if need_sigma else None, B, _stream(rho)),
+        "tsp_atten_optical_depth_adjoint")
+    return g_rho, g_sigma
+
+
+def atten_forward(grid: Grid, geom: Geometry, rho: torch.Tensor, sigma: torch.Tensor,
+                  tau1: torch.Tensor) -> torch.Tensor:
+    """Attenuated y (Eq. 16-18), shaped like tsp_forward's."""
+    B = _vol_batch(grid, rho, "rho")
+    for t, nm in ((sigma, "sigma"), (tau1, "tau1")):
+        _vol_batch(grid, t, nm)
+        if t.shape != rho.shape:
+            raise ValueError(f"{nm} must have the shape of rho")
+    y = torch.empty((B,) + geom.det_shape, device=rho.device, dtype=torch.float32)
+    L = _lib.load()
+    check(L.tsp_atten_forward(grid.handle, geom.handle, ctypes.c_void_p(rho.data_ptr()),
+                              ctypes.c_void_p(sigma.data_ptr()), ctypes.c_void_p(tau1.data_ptr()),
+                              ctypes.c_void_p(y.data_ptr()), B, _stream(rho)), "tsp_atten_forward")
+    return y if rho.dim() == 4 else y[0]
+
+
+def atten_backward(grid: Grid, geom: Geometry, rho, sigma, tau1, y, gy, need_sigma=True, need_tau1=True):
+    """Gradients of <gy, y> (y = atten_forward(rho, sigma, tau1)) with respect
+    to rho, sigma and tau1 (None where not needed)."""
+    B = _vol_batch(grid, rho, "rho")
+    for t, nm in ((y, "y"), (gy, "gy")):
+        _require_cuda(t, nm)
+        if t.numel() != B * geom.n_rays:
+            raise ValueError(f"{nm} has the wrong size")
+    g_rho = torch.zeros_like(rho)
+    g_sigma = torch.zeros_like(rho) if need_sigma else None
+    g_tau1 = torch.zeros_like(rho) if need_tau1 else None
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    L = _lib.load()
+    check(L.tsp_atten_backward(grid.handle, geom.handle, ptr(rho), ptr(sigma), ptr(tau1), ptr(y), ptr(gy),
+                               ptr(g_rho), ptr(g_sigma), ptr(g_tau1), B, _stream(rho)), "tsp_atten_backward")
+    return g_rho, g_sigma, g_tau1
+
+
+class OpticalDepthFn(torch.autograd.Function):
+    """tau_1 = F_1(sigma rho) with its hand-written adjoint as backward."""
+
+    @staticmethod
+    def forward(ctx, rho, sigma, grid, sun_geom):
+        rho, sigma = rho.contiguous(), sigma.contiguous()
+        ctx.save_for_backward(rho, sigma)
+        ctx.grid, ctx.sun = grid, sun_geom
+        return optical_depth(grid, sun_geom, rho, sigma)
+
+    @staticmethod
+    def backward(ctx, g_tau1):
+        rho, sigma = ctx.saved_tensors
+        g_rho, g_sigma = optical_depth_adjoint(ctx.grid, ctx.sun, rho, sigma, g_tau1.contiguous(),
+                                               need_sigma=ctx.needs_input_grad[1])
+        return g_rho, g_sigma, None, None
+
+
+class AttenuatedProjectionFn(torch.autograd.Function):
+    """y = Eq. 17-18 given rho, sigma and tau_1, with the hand-written gradient."""
+
+    @staticmethod
+    def forward(ctx, rho, sigma, tau1, grid, geom):
+        rho, sigma, tau1 = rho.contiguous(), sigma.contiguous(), tau1.contiguous()
+        y = atten_forward(grid, geom, rho, sigma, tau1)
+        ctx.save_for_backward(rho, sigma, tau1, y)
+        ctx.grid, ctx.geom = grid, geom
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        rho, sigma, tau1, y = ctx.saved_tensors
+        g = atten_backward(ctx.grid, ctx.geom, rho, sigma, tau1, y, gy.contiguous(),
+                           need_sigma=ctx.needs_input_grad[1], need_tau1=ctx.needs_input_grad[2])
+        return g[0], g[1], g[2], None, None
+
+
+class AttenuatedOperator:
+    """rho -> y of Eq. 16-17 with tau_1 = F_1(sigma rho) computed from the same
+    rho (Eq. 17), differentiable in rho and sigma."""
+
+    def __init__(self, grid: Grid, geom: Geometry, sun, device=None):
+        self.grid, self.geom = grid, geom
+        self.sun = sunward_geometry(grid, sun, device)
+
+    def optical_depth(self, rho: torch.Tensor, sigma: torch.Tensor) -> torch.Tensor:
+        return OpticalDepthFn.apply(rho, sigma, self.grid, self.sun)
+
+    def __call__(self, rho: torch.Tensor, sigma: torch.Tensor) -> torch.Tensor:
+        tau1 = self.optical_depth(rho, sigma)
+        return AttenuatedProjectionFn.apply(rho, sigma, tau1, self.grid, self.geom)

@@ -1,0 +1,150 @@
+"""Attenuated projection (Sec. 9.3, Eq. 14-18) on the GPU against the FP64
+oracle (oracle/atten.py), through the C ABI.
+
+Tolerances: values (y, tau_1) follow the projector's parity rule (tests/_util:
+per ray 1e-4 relative with a floor of 1e-2 of the largest value); gradients,
+sums of float32 atomics over many rays, within 2e-4 normwise and 1e-3 of the
+largest entry elementwise.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import atten
+from paper_2608_16960_gb300 import synth, workloads
+from paper_2608_16960_gb300.projector import (AttenuatedOperator, Geometry, Grid, atten_backward, atten_forward,
+                                              optical_depth, optical_depth_adjoint, sunward_geometry, sunward_rays,
+                                              tsp_device_status, tsp_forward)
+
+from _util import oracle_rays, parity
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda"
+SUN = (0.61, -0.42, 0.67)
+
+
+def grad_parity(g, ref, what, rel=2e-4, elem=1e-3):
+    g, ref = np.asarray(g, np.float64).reshape(-1), np.asarray(ref, np.float64).reshape(-1)
+    nrm = np.linalg.norm(ref)
+    assert nrm > 0, what
+    assert np.linalg.norm(g - ref) <= rel * nrm, (what, np.linalg.norm(g - ref) / nrm)
+    assert np.max(np.abs(g - ref)) <= elem * np.max(np.abs(ref)), what
+
+
+@pytest.fixture(scope="module")
+def case():
+    wl = workloads.tiny()
+    grid = Grid.from_edges(wl.edges)
+    v = wl.views[0]
+    geom = Geometry.cone(v.pos, v.shape, v.fov_deg) if v.kind == "cone" else Geometry.parallel(v.pos, v.shape, v.size)
+    st, di = oracle_rays(v)
+    rho = wl.rho.astype(np.float32)
+    # cross-section of order 1/(typical rho x path): optical depths of order one
+    sigma = (0.02 + 0.03 * synth.uniform_volume(wl.edges.shape, 77)).astype(np.float32)
+    sun = sunward_geometry(grid, SUN)
+    return wl, grid, geom, st, di, rho, sigma, sun
+
+
+def _sun_rays_host(sun_geom, grid):
+    """The GPU's float32 sunward rays as (V, 3) float64 arrays for the oracle."""
+    s, d = sunward_rays(grid, SUN)
+    return s.cpu().numpy().T.astype(np.float64), d.cpu().numpy().T.astype(np.float64)
+
+
+def test_sunward_rays_are_centroids(case):
+    wl, grid, geom, st, di, rho, sigma, sun = case
+    s, d = _sun_rays_host(sun, grid)
+    ref_s, ref_d = atten.sunward_rays(wl.edges, SUN)
+    assert np.max(np.abs(s - ref_s)) <= 4e-7 * np.max(np.abs(ref_s))
+    assert np.max(np.abs(d - ref_d)) <= 2e-7
+
+
+def test_optical_depth_parity(case):
+    wl, grid, geom, st, di, rho, sigma, sun = case
+    tau = optical_depth(grid, sun, torch.tensor(rho, device=DEV), torch.tensor(sigma, device=DEV)).cpu().numpy()
+    s, d = _sun_rays_host(sun, grid)
+    ref = atten.optical_depth(wl.edges, rho, sigma, s, d)
+    parity(tau, ref, what="tau_1")
+    assert tsp_device_status() == 0
+
+
+def test_forward_parity(case):
+    wl, grid, geom, st, di, rho, sigma, sun = case
+    tau1 = (0.5 * synth.uniform_volume(wl.edges.shape, 5)).astype(np.float32)
+    y = atten_forward(grid, geom, *(torch.tensor(a, device=DEV) for a in (rho, sigma, tau1))).cpu().numpy()
+    ref = atten.forward(wl.edges, st, di, rho, sigma, tau1)
+    parity(y, ref, what="attenuated y")
+    plain = oracle.forward(wl.edges, st, di, rho)
+    assert np.linalg.norm(ref - plain) > 0.05 * np.linalg.norm(plain)  # the attenuation is not negligible
+
+
+def test_no_absorption_is_the_plain_projector(case):
+    wl, grid, geom, st, di, rho, sigma, sun = case
+    r = torch.tensor(rho, device=DEV)
+    z = torch.zeros_like(r)
+    y = atten_forward(grid, geom, r, z, z).cpu().numpy()
+    y0 = tsp_forward(grid, geom, r).cpu().numpy()
+    assert np.max(np.abs(y - y0)) <= 1e-6 * np.max(np.abs(y0))
+
+
+def test_backward_parity(case):
+    wl, grid, geom, st, di, rho, sigma, sun = case
+    tau1 = (0.5 * synth.uniform_volume(wl.edges.shape, 5)).astype(np.float32)
+    gy = synth.SplitMix64(12).uniform(st.shape[0], -1.0, 1.0).astype(np.float32)
+    t = [torch.tensor(a, device=DEV) for a in (rho, sigma, tau1)]
+    y = atten_forward(grid, geom, *t)
+    g = atten_backward(grid, geom, *t, y, torch.tensor(gy, device=DEV).view_as(y))
+    ref = atten.backward(wl.edges, st, di, rho, sigma, tau1, gy.astype(np.float64))
+    for name, a, b in zip(("g_rho", "g_sigma", "g_tau1"), g, ref):
+        grad_parity(a.cpu().numpy(), b, name)
+    assert tsp_device_status() == 0
+
+
+def test_optical_depth_adjoint_parity(case):
+    wl, grid, geom, st, di, rho, sigma, sun = case
+    gt = synth.uniform_volume(wl.edges.shape, 19).astype(np.float32) - 0.5
+    g_rho, g_sig = optical_depth_adjoint(grid, sun, torch.tensor(rho, device=DEV), torch.tensor(sigma, device=DEV),
+                                         torch.tensor(gt, device=DEV))
+    s, d = _sun_rays_host(sun, grid)
+    r_rho, r_sig = atten.optical_depth_backward(wl.edges, rho, sigma, s, d, gt)
+    grad_parity(g_rho.cpu().numpy(), r_rho, "g_rho (tau_1)")
+    grad_parity(g_sig.cpu().numpy(), r_sig, "g_sigma (tau_1)")
+
+
+def test_operator_autograd_chain(case):
+    """AttenuatedOperator: y(rho, sigma) with tau_1 = F_1(sigma rho); torch
+    autograd through both hand-written backwards equals the oracle's chain."""
+    wl, grid, geom, st, di, rho, sigma, sun = case
+    op = AttenuatedOperator(grid, geom, SUN)
+    r = torch.tensor(rho, device=DEV, requires_grad=True)
+    q = torch.tensor(sigma, device=DEV, requires_grad=True)
+    y = op(r, q)
+    gy = synth.SplitMix64(4).uniform(st.shape[0], -1.0, 1.0)
+    (y.reshape(-1) * torch.tensor(gy, device=DEV, dtype=torch.float32)).sum().backward()
+    s, d = _sun_rays_host(sun, grid)
+    tau1 = atten.optical_depth(wl.edges, rho, sigma, s, d)
+    parity(y.detach().cpu().numpy(), atten.forward(wl.edges, st, di, rho, sigma, tau1), what="operator y")
+    g_rho, g_sig, g_tau = atten.backward(wl.edges, st, di, rho, sigma, tau1, gy)
+    c_rho, c_sig = atten.optical_depth_backward(wl.edges, rho, sigma, s, d, g_tau)
+    grad_parity(r.grad.cpu().numpy(), g_rho + c_rho, "d/d rho")
+    grad_parity(q.grad.cpu().numpy(), g_sig + c_sig, "d/d sigma")
+
+
+def test_batched_matches_single(case):
+    wl, grid, geom, st, di, rho, sigma, sun = case
+    r = torch.stack([torch.tensor(rho, device=DEV), 0.5 * torch.tensor(rho, device=DEV)])
+    q = torch.tensor(sigma, device=DEV).expand(2, *sigma.shape).contiguous()
+    t = optical_depth(grid, sun, r, q)
+    y = atten_forward(grid, geom, r, q, t)
+    for b in range(2):
+        tb = optical_depth(grid, sun, r[b].contiguous(), q[b].contiguous())
+        assert torch.equal(tb, t[b])
+        assert torch.equal(atten_forward(grid, geom, r[b].contiguous(), q[b].contiguous(), tb), y[b])
+
+
+def test_bad_sunward_geometry_is_rejected(case):
+    wl, grid, geom, st, di, rho, sigma, sun = case
+    r = torch.tensor(rho, device=DEV)
+    with pytest.raises(Exception):
+        optical_depth(grid, geom, r, r)  # the cone view has no ray per voxel
