@@ -42,6 +42,11 @@ SMS, FP32_LANES_PER_SM = 152, 128
 # ncu capture of a smaller case of the same kernel (4 + 4 views of the paper-scale
 # workload; the traffic grows with the entries streamed), scaled to a full launch.
 STREAM_DRAM_BYTES_PER_ENTRY = 8.38
+# Attenuated projection (Sec. 9.3): FP32 operations per segment on top of the
+# traversal's: the running optical depth (multiply, fma) and the contribution
+# (add, exponential counted as one, multiply, fma).
+ATTEN_EXTRA_OPS = 6.0
+SUN_DIRECTION = (0.61, -0.42, 0.67)
 
 
 def parse():
@@ -53,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-segments", action="store_true", help="skip the stored-segment-list leg")
+    ap.add_argument("--no-atten", action="store_true", help="skip the attenuated-projection leg")
     ap.add_argument("--views", type=int, default=0,
                     help="paper-scale workload: keep only the first N views of each set (small profiling case)")
     ap.add_argument("--workload", choices=["paper_scale", "batched", "differentiation", "warmstart"],
@@ -332,6 +338,9 @@ def run_ours(args):
     seg_leg = None
     if not args.no_segments:
         seg_leg = time_segment_lists(args, grid, geoms, rho, ws, flush, stream, n_rays, n_segs, peaks, dist)
+    att_leg = None
+    if not args.no_atten:
+        att_leg = time_attenuated(args, wl, grid, geoms, rho, ws, flush, stream, n_rays, n_segs, peaks, dist)
     # dominant kernel: whichever of the forward / adjoint traversals takes longer
     dom = "forward" if t_fwd >= t_adj else "adjoint"
     t_dom_launch = (max(t_fwd, t_adj) / args.steps) / len(geoms) / 1e3  # s per launch
@@ -355,13 +364,74 @@ def run_ours(args):
            "adj_rays_per_s": world * n_rays * args.steps / (t_adj / 1e3),
            "segments_per_s": world * 2 * n_segs * args.steps / (t_tot / 1e3),
            "roofline": roofline, "clocks": clocks, "e2e": e2e,
-           "gpu_launches": 2 * len(geoms) * args.steps, "peaks": peak_kind, "segment_lists": seg_leg}
+           "gpu_launches": 2 * len(geoms) * args.steps, "peaks": peak_kind, "segment_lists": seg_leg,
+           "attenuated": att_leg}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def time_attenuated(args, wl, grid, geoms, rho, ws, flush, stream, n_rays, n_segs, peaks, dist):
+    """Attenuated projection (Sec. 9.3, Eq. 14-18) on the same views: forward =
+    tau_1 = F_1(sigma rho) over one sunward ray per voxel, then y of Eq. 17
+    per view; backward = the gradient traversal per view (w = the adjoint
+    leg's detector values) and F_1's adjoint of the tau_1 gradient. The
+    cross-section is a synthetic field giving optical depths of order one."""
+    import torch
+
+    from paper_2608_16960_gb300 import synth
+    from paper_2608_16960_gb300.projector import (atten_backward, atten_forward, optical_depth,
+                                                  optical_depth_adjoint, sunward_geometry, tsp_count_segments)
+
+    sigma = torch.tensor((0.2 + 0.3 * synth.uniform_volume(wl.edges.shape, 77)).astype(np.float32), device="cuda")
+    sun = sunward_geometry(grid, SUN_DIRECTION)
+    sun_segs = int(tsp_count_segments(grid, sun).sum().item())
+    g_rho, g_sig, g_tau = (torch.empty_like(rho) for _ in range(3))
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        tau1 = optical_depth(grid, sun, rho, sigma)
+        ys = [atten_forward(grid, g, rho, sigma, tau1) for g in geoms]
+        if ev:
+            ev[1].record(stream)
+        # gradients of all views summed in place (the first call overwrites)
+        for i, (g, y, w) in enumerate(zip(geoms, ys, ws)):
+            atten_backward(grid, g, rho, sigma, tau1, y, w, out=(g_rho, g_sig, g_tau), accumulate=i > 0)
+        optical_depth_adjoint(grid, sun, rho, sigma, g_tau, out=(g_rho, g_sig), accumulate=True)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        step(evs[k])
+    torch.cuda.synchronize()
+    from paper_2608_16960_gb300.dist import max_over_ranks
+    t_fwd = max_over_ranks(sum(e[0].elapsed_time(e[1]) for e in evs) / 1e3, device="cuda")
+    t_bwd = max_over_ranks(sum(e[1].elapsed_time(e[2]) for e in evs) / 1e3, device="cuda")
+    world = dist.get_world_size() if dist else 1
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    ops = OPS_PER_SEGMENT + ATTEN_EXTRA_OPS
+    fwd_ops = ops * (n_segs + sun_segs) * args.steps / t_fwd / 1e12
+    return {"value": world * n_rays * args.steps / (t_fwd + t_bwd), "unit": UNIT,
+            "fwd_rays_per_s": world * n_rays * args.steps / t_fwd,
+            "bwd_rays_per_s": world * n_rays * args.steps / t_bwd,
+            "ms_per_step": 1e3 * (t_fwd + t_bwd) / args.steps, "ms_fwd": 1e3 * t_fwd / args.steps,
+            "ms_bwd": 1e3 * t_bwd / args.steps, "sunward_rays": grid.voxels, "sunward_segments": sun_segs,
+            "sun_direction": SUN_DIRECTION,
+            "roofline": {"bound": "alu", "achieved": fwd_ops, "peak": peak_ops, "unit": "Tops/s",
+                         "frac": fwd_ops / peak_ops, "kernel": "attenuated forward (tau_1 + y)",
+                         "ops_per_segment": ops},
+            "gpu_launches": (2 + 2 * len(geoms)) * args.steps}
 
 
 def time_segment_lists(args, grid, geoms, rho, ws, flush, stream, n_rays, n_segs, peaks, dist):

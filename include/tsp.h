@@ -218,12 +218,13 @@ void tsp_segments_destroy(tsp_segments s);
  *   tsp_geom_rays to get F_1's geometry.
  * tsp_atten_optical_depth - tau_1 = F_1(sigma rho) (one value per voxel);
  *   `sun` is a geometry with one ray per voxel (TSP_EINVAL otherwise).
- * tsp_atten_optical_depth_adjoint - g_rho += sigma F_1^T g_tau1 and, if
- *   g_sigma != NULL, g_sigma += rho F_1^T g_tau1 (accumulated: zero first).
+ * tsp_atten_optical_depth_adjoint - g_rho (+)= sigma F_1^T g_tau1 and, if
+ *   g_sigma != NULL, g_sigma (+)= rho F_1^T g_tau1; accumulate == 0
+ *   overwrites the outputs, otherwise adds to them.
  * tsp_atten_forward - y (batch, n_rays) by Eq. 17-18, overwritten.
  * tsp_atten_backward - gradients of sum y gy with respect to rho, sigma and
- *   tau_1 (tau_1 taken as an independent input), ACCUMULATED into g_rho and,
- *   when not NULL, g_sigma and g_tau1. y must be tsp_atten_forward's output for
+ *   tau_1 (tau_1 taken as an independent input) into g_rho and, when not NULL,
+ *   g_sigma and g_tau1; accumulate as above. y must be tsp_atten_forward's output for
  *   the same inputs (its running prefix is reused). Chain through tau_1 with
  *   tsp_atten_optical_depth_adjoint(g_tau1).
  * All of them traverse on the fly like tsp_forward and scatter with atomic
@@ -234,12 +235,12 @@ tsp_status tsp_atten_optical_depth(tsp_grid grid, tsp_geom sun, const float* rho
                                    int batch, void* stream);
 tsp_status tsp_atten_optical_depth_adjoint(tsp_grid grid, tsp_geom sun, const float* rho, const float* sigma,
                                            const float* g_tau1, float* g_rho, float* g_sigma, int batch,
-                                           void* stream);
+                                           int accumulate, void* stream);
 tsp_status tsp_atten_forward(tsp_grid grid, tsp_geom geom, const float* rho, const float* sigma, const float* tau1,
                              float* y, int batch, void* stream);
 tsp_status tsp_atten_backward(tsp_grid grid, tsp_geom geom, const float* rho, const float* sigma,
                               const float* tau1, const float* y, const float* gy, float* g_rho, float* g_sigma,
-                              float* g_tau1, int batch, void* stream);
+                              float* g_tau1, int batch, int accumulate, void* stream);
 
 /*
  * tsp_autotune - times candidate launch knobs (threads per block 64..512, warp

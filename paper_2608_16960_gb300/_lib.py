@@ -89,9 +89,9 @@ SIGNATURES = {
     "tsp_sq_residual": (_I, [_P, _P, _I64, _P, _P, _P]),
     "tsp_sunward_rays": (_I, [_P, ctypes.POINTER(ctypes.c_double), _P, _P, _P]),
     "tsp_atten_optical_depth": (_I, [_P, _P, _P, _P, _P, _I, _P]),
-    "tsp_atten_optical_depth_adjoint": (_I, [_P, _P, _P, _P, _P, _P, _P, _I, _P]),
+    "tsp_atten_optical_depth_adjoint": (_I, [_P, _P, _P, _P, _P, _P, _P, _I, _I, _P]),
     "tsp_atten_forward": (_I, [_P, _P, _P, _P, _P, _P, _I, _P]),
-    "tsp_atten_backward": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P]),
+    "tsp_atten_backward": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _I, _P]),
     "tsp_net_create": (_I, [_I, _I, _I, _I, ctypes.POINTER(_P)]),
     "tsp_net_destroy": (None, [_P]),
     "tsp_net_num_params": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),

@@ -229,7 +229,7 @@ extern "C" tsp_status tsp_atten_optical_depth(tsp_grid grid, tsp_geom sun, const
 
 extern "C" tsp_status tsp_atten_optical_depth_adjoint(tsp_grid grid, tsp_geom sun, const float* rho,
                                                       const float* sigma, const float* g_tau1, float* g_rho,
-                                                      float* g_sigma, int batch, void* stream) {
+                                                      float* g_sigma, int batch, int accumulate, void* stream) {
   tsp_status st = check_trace_args(grid, sun, g_tau1, g_rho, batch, nullptr, "tsp_atten_optical_depth_adjoint");
   if (st != TSP_OK) return st;
   if (!rho || !sigma) return fail(TSP_EINVAL, "tsp_atten_optical_depth_adjoint: NULL array");
@@ -237,6 +237,11 @@ extern "C" tsp_status tsp_atten_optical_depth_adjoint(tsp_grid grid, tsp_geom su
   if (st != TSP_OK) return st;
   const tsp_launch l = preferred_launch(grid, sun, true);
   const int64_t V = grid->voxels();
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  if (!accumulate) {
+    TSP_CUDA(cudaMemsetAsync(g_rho, 0, sizeof(float) * size_t(V) * batch, cs));
+    if (g_sigma) TSP_CUDA(cudaMemsetAsync(g_sigma, 0, sizeof(float) * size_t(V) * batch, cs));
+  }
   for (int b = 0; b < batch; ++b) {
     ProductScatterOp op;
     op.rho = rho + b * V;
@@ -244,7 +249,7 @@ extern "C" tsp_status tsp_atten_optical_depth_adjoint(tsp_grid grid, tsp_geom su
     op.g_tau1 = g_tau1 + b * V;
     op.g_rho = g_rho + b * V;
     op.g_sigma = g_sigma ? g_sigma + b * V : nullptr;
-    launch_trace(grid, sun, l, op, static_cast<cudaStream_t>(stream));
+    launch_trace(grid, sun, l, op, cs);
   }
   TSP_CUDA(cudaGetLastError());
   return TSP_OK;
@@ -271,12 +276,19 @@ extern "C" tsp_status tsp_atten_forward(tsp_grid grid, tsp_geom geom, const floa
 
 extern "C" tsp_status tsp_atten_backward(tsp_grid grid, tsp_geom geom, const float* rho, const float* sigma,
                                          const float* tau1, const float* y, const float* gy, float* g_rho,
-                                         float* g_sigma, float* g_tau1, int batch, void* stream) {
+                                         float* g_sigma, float* g_tau1, int batch, int accumulate, void* stream) {
   tsp_status st = check_trace_args(grid, geom, gy, g_rho, batch, nullptr, "tsp_atten_backward");
   if (st != TSP_OK) return st;
   if (!rho || !sigma || !tau1 || !y) return fail(TSP_EINVAL, "tsp_atten_backward: NULL array");
   const tsp_launch l = preferred_launch(grid, geom, true);
   const int64_t V = grid->voxels(), n = geom->n_rays;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  if (!accumulate) {
+    const size_t bytes = sizeof(float) * size_t(V) * batch;
+    TSP_CUDA(cudaMemsetAsync(g_rho, 0, bytes, cs));
+    if (g_sigma) TSP_CUDA(cudaMemsetAsync(g_sigma, 0, bytes, cs));
+    if (g_tau1) TSP_CUDA(cudaMemsetAsync(g_tau1, 0, bytes, cs));
+  }
   for (int b = 0; b < batch; ++b) {
     AttenBwdOp op;
     op.rho = rho + b * V;
@@ -287,7 +299,7 @@ extern "C" tsp_status tsp_atten_backward(tsp_grid grid, tsp_geom geom, const flo
     op.g_rho = g_rho + b * V;
     op.g_sigma = g_sigma ? g_sigma + b * V : nullptr;
     op.g_tau1 = g_tau1 ? g_tau1 + b * V : nullptr;
-    launch_trace(grid, geom, l, op, static_cast<cudaStream_t>(stream));
+    launch_trace(grid, geom, l, op, cs);
   }
   TSP_CUDA(cudaGetLastError());
   return TSP_OK;

@@ -481,20 +481,25 @@ def optical_depth(grid: Grid, sun_geom: Geometry, rho: torch.Tensor, sigma: torc
 
 
 def optical_depth_adjoint(grid: Grid, sun_geom: Geometry, rho: torch.Tensor, sigma: torch.Tensor,
-                          g_tau1: torch.Tensor, need_sigma: bool = True):
-    """(sigma F_1^T g, rho F_1^T g): gradients of <g, F_1(sigma rho)>."""
+                          g_tau1: torch.Tensor, need_sigma: bool = True, out=None, accumulate: bool = False):
+    """(sigma F_1^T g, rho F_1^T g): gradients of <g, F_1(sigma rho)>, written
+    to (or, with accumulate, added to) out = (g_rho, g_sigma or None) if given."""
     B = _vol_batch(grid, rho, "rho")
     for t, nm in ((sigma, "sigma"), (g_tau1, "g_tau1")):
         _vol_batch(grid, t, nm)
         if t.shape != rho.shape:
             raise ValueError(f"{nm} must have the shape of rho")
-    g_rho = torch.zeros_like(rho)
-    g_sigma = torch.zeros_like(rho) if need_sigma else None
+    if out is not None:
+        g_rho, g_sigma = out
+    else:
+        g_rho = torch.empty_like(rho)
+        g_sigma = torch.empty_like(rho) if need_sigma else None
+        accumulate = False
     L = _lib.load()
     check(L.tsp_atten_optical_depth_adjoint(
         grid.handle, sun_geom.handle, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(sigma.data_ptr()),
         ctypes.c_void_p(g_tau1.data_ptr()), ctypes.c_void_p(g_rho.data_ptr()),
-        ctypes.c_void_p(g_sigma.data_ptr()) if need_sigma else None, B, _stream(rho)),
+        ctypes.c_void_p(g_sigma.data_ptr()) if g_sigma is not None else None, B, int(accumulate), _stream(rho)),
         "tsp_atten_optical_depth_adjoint")
     return g_rho, g_sigma
 
@@ -515,21 +520,29 @@ def atten_forward(grid: Grid, geom: Geometry, rho: torch.Tensor, sigma: torch.Te
     return y if rho.dim() == 4 else y[0]
 
 
-def atten_backward(grid: Grid, geom: Geometry, rho, sigma, tau1, y, gy, need_sigma=True, need_tau1=True):
+def atten_backward(grid: Grid, geom: Geometry, rho, sigma, tau1, y, gy, need_sigma=True, need_tau1=True, out=None,
+                   accumulate: bool = False):
     """Gradients of <gy, y> (y = atten_forward(rho, sigma, tau1)) with respect
-    to rho, sigma and tau1 (None where not needed)."""
+    to rho, sigma and tau1 (None where not needed), written to (or, with
+    accumulate, added to) out = (g_rho, g_sigma, g_tau1) if given (entries of
+    out may be None)."""
     B = _vol_batch(grid, rho, "rho")
     for t, nm in ((y, "y"), (gy, "gy")):
         _require_cuda(t, nm)
         if t.numel() != B * geom.n_rays:
             raise ValueError(f"{nm} has the wrong size")
-    g_rho = torch.zeros_like(rho)
-    g_sigma = torch.zeros_like(rho) if need_sigma else None
-    g_tau1 = torch.zeros_like(rho) if need_tau1 else None
+    if out is not None:
+        g_rho, g_sigma, g_tau1 = out
+    else:
+        g_rho = torch.empty_like(rho)
+        g_sigma = torch.empty_like(rho) if need_sigma else None
+        g_tau1 = torch.empty_like(rho) if need_tau1 else None
+        accumulate = False
     ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
     L = _lib.load()
     check(L.tsp_atten_backward(grid.handle, geom.handle, ptr(rho), ptr(sigma), ptr(tau1), ptr(y), ptr(gy),
-                               ptr(g_rho), ptr(g_sigma), ptr(g_tau1), B, _stream(rho)), "tsp_atten_backward")
+                               ptr(g_rho), ptr(g_sigma), ptr(g_tau1), B, int(accumulate), _stream(rho)),
+          "tsp_atten_backward")
     return g_rho, g_sigma, g_tau1
 
 

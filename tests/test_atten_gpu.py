@@ -41,20 +41,14 @@ def case():
     st, di = oracle_rays(v)
     rho = wl.rho.astype(np.float32)
     # cross-section of order 1/(typical rho x path): optical depths of order one
-    sigma = (0.02 + 0.03 * synth.uniform_volume(wl.edges.shape, 77)).astype(np.float32)
+    sigma = (0.2 + 0.3 * synth.uniform_volume(wl.edges.shape, 77)).astype(np.float32)
     sun = sunward_geometry(grid, SUN)
     return wl, grid, geom, st, di, rho, sigma, sun
 
 
-def _sun_rays_host(sun_geom, grid):
-    """The GPU's float32 sunward rays as (V, 3) float64 arrays for the oracle."""
-    s, d = sunward_rays(grid, SUN)
-    return s.cpu().numpy().T.astype(np.float64), d.cpu().numpy().T.astype(np.float64)
-
-
 def test_sunward_rays_are_centroids(case):
     wl, grid, geom, st, di, rho, sigma, sun = case
-    s, d = _sun_rays_host(sun, grid)
+    s, d = (t.cpu().numpy().T.astype(np.float64) for t in sunward_rays(grid, SUN))
     ref_s, ref_d = atten.sunward_rays(wl.edges, SUN)
     assert np.max(np.abs(s - ref_s)) <= 4e-7 * np.max(np.abs(ref_s))
     assert np.max(np.abs(d - ref_d)) <= 2e-7
@@ -63,7 +57,7 @@ def test_sunward_rays_are_centroids(case):
 def test_optical_depth_parity(case):
     wl, grid, geom, st, di, rho, sigma, sun = case
     tau = optical_depth(grid, sun, torch.tensor(rho, device=DEV), torch.tensor(sigma, device=DEV)).cpu().numpy()
-    s, d = _sun_rays_host(sun, grid)
+    s, d = atten.sunward_rays(wl.edges, SUN)  # the oracle's own FP64 rays
     ref = atten.optical_depth(wl.edges, rho, sigma, s, d)
     parity(tau, ref, what="tau_1")
     assert tsp_device_status() == 0
@@ -106,7 +100,7 @@ def test_optical_depth_adjoint_parity(case):
     gt = synth.uniform_volume(wl.edges.shape, 19).astype(np.float32) - 0.5
     g_rho, g_sig = optical_depth_adjoint(grid, sun, torch.tensor(rho, device=DEV), torch.tensor(sigma, device=DEV),
                                          torch.tensor(gt, device=DEV))
-    s, d = _sun_rays_host(sun, grid)
+    s, d = atten.sunward_rays(wl.edges, SUN)  # the oracle's own FP64 rays
     r_rho, r_sig = atten.optical_depth_backward(wl.edges, rho, sigma, s, d, gt)
     grad_parity(g_rho.cpu().numpy(), r_rho, "g_rho (tau_1)")
     grad_parity(g_sig.cpu().numpy(), r_sig, "g_sigma (tau_1)")
@@ -122,7 +116,7 @@ def test_operator_autograd_chain(case):
     y = op(r, q)
     gy = synth.SplitMix64(4).uniform(st.shape[0], -1.0, 1.0)
     (y.reshape(-1) * torch.tensor(gy, device=DEV, dtype=torch.float32)).sum().backward()
-    s, d = _sun_rays_host(sun, grid)
+    s, d = atten.sunward_rays(wl.edges, SUN)  # the oracle's own FP64 rays
     tau1 = atten.optical_depth(wl.edges, rho, sigma, s, d)
     parity(y.detach().cpu().numpy(), atten.forward(wl.edges, st, di, rho, sigma, tau1), what="operator y")
     g_rho, g_sig, g_tau = atten.backward(wl.edges, st, di, rho, sigma, tau1, gy)
@@ -148,3 +142,32 @@ def test_bad_sunward_geometry_is_rejected(case):
     r = torch.tensor(rho, device=DEV)
     with pytest.raises(Exception):
         optical_depth(grid, geom, r, r)  # the cone view has no ray per voxel
+
+
+def test_paper_scale_sampled():
+    """The bench's workload (100 x 60 x 120 grid, 32 cone + 32 parallel views
+    of 256^2), default launch: tau_1 on every 97th voxel and the attenuated y
+    on every 1021st ray of each view set against the oracle (whose tau_1 is
+    its own, over all voxels)."""
+    wl = workloads.paper_scale()
+    grid = Grid.from_edges(wl.edges)
+    rho = wl.rho.astype(np.float32)
+    sigma = (0.2 + 0.3 * synth.uniform_volume(wl.edges.shape, 77)).astype(np.float32)
+    sun = sunward_geometry(grid, SUN)
+    r, q = torch.tensor(rho, device=DEV), torch.tensor(sigma, device=DEV)
+    tau = optical_depth(grid, sun, r, q)
+    s, d = atten.sunward_rays(wl.edges, SUN)
+    ref_tau = atten.optical_depth(wl.edges, rho, sigma, s, d)
+    iv = np.arange(0, grid.voxels, 97)
+    parity(tau.cpu().numpy().reshape(-1)[iv], ref_tau.reshape(-1)[iv], what="paper-scale tau_1")
+    for v in wl.views:
+        g = Geometry.cone(v.pos, v.shape, v.fov_deg) if v.kind == "cone" else Geometry.parallel(v.pos, v.shape, v.size)
+        y = atten_forward(grid, g, r, q, tau).cpu().numpy().reshape(-1)
+        st, di = oracle_rays(v)
+        idx = np.arange(0, v.n_rays, 1021)
+        ref = atten.forward(wl.edges, st[idx], di[idx], rho, sigma, ref_tau)
+        big = np.max(np.abs(ref))
+        err = np.abs(y[idx] - ref)
+        assert np.all(err <= 1e-4 * np.maximum(np.abs(ref), 1e-2 * big)), (v.kind, err.max())
+        assert np.all(np.isfinite(y)) and np.all(y >= 0)
+    assert tsp_device_status() == 0
