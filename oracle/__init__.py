@@ -166,6 +166,24 @@ def adjoint(edges, starts, dirs, y, n_threads: int = 0):
     return g if batched else g[0]
 
 
+def forward_dynamic(edges, starts, dirs, rho, n_views: int):
+    """Dynamic object (Sec. 4.4): the rays are n_views equal consecutive
+    blocks (one per view of a collection) and block k sees rho[k]. The
+    definition written out: Eq. 5 per view on its own volume."""
+    starts = np.asarray(starts).reshape(n_views, -1, 3)
+    dirs = np.asarray(dirs).reshape(n_views, -1, 3)
+    rho = np.asarray(rho, dtype=np.float64).reshape((n_views,) + tuple(edges.shape))
+    return np.stack([forward(edges, starts[k], dirs[k], rho[k]) for k in range(n_views)])
+
+
+def adjoint_dynamic(edges, starts, dirs, y, n_views: int):
+    """Adjoint of forward_dynamic: volume k = F_k^T y[k]."""
+    starts = np.asarray(starts).reshape(n_views, -1, 3)
+    dirs = np.asarray(dirs).reshape(n_views, -1, 3)
+    y = np.asarray(y, dtype=np.float64).reshape(n_views, -1)
+    return np.stack([adjoint(edges, starts[k], dirs[k], y[k]) for k in range(n_views)])
+
+
 def cone_rays(pos, H, W, fov_deg, look_at=None, up=None):
     """Cone-beam rays: pinhole at each pos, flat raster uniform in tangent space
     over the full field of view (Sec. 4.2, 4.6). Returns (V*H*W, 3) starts, dirs."""
