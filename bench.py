@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-segments", action="store_true", help="skip the stored-segment-list leg")
     ap.add_argument("--no-atten", action="store_true", help="skip the attenuated-projection leg")
+    ap.add_argument("--no-dynamic", action="store_true", help="skip the dynamic-object leg")
     ap.add_argument("--views", type=int, default=0,
                     help="paper-scale workload: keep only the first N views of each set (small profiling case)")
     ap.add_argument("--workload", choices=["paper_scale", "batched", "differentiation", "warmstart"],
@@ -341,6 +342,9 @@ def run_ours(args):
     att_leg = None
     if not args.no_atten:
         att_leg = time_attenuated(args, wl, grid, geoms, rho, ws, flush, stream, n_rays, n_segs, peaks, dist)
+    dyn_leg = None
+    if not args.no_dynamic:
+        dyn_leg = time_dynamic(args, wl, grid, geoms, ws, flush, stream, n_rays, dist)
     # dominant kernel: whichever of the forward / adjoint traversals takes longer
     dom = "forward" if t_fwd >= t_adj else "adjoint"
     t_dom_launch = (max(t_fwd, t_adj) / args.steps) / len(geoms) / 1e3  # s per launch
@@ -365,7 +369,7 @@ def run_ours(args):
            "segments_per_s": world * 2 * n_segs * args.steps / (t_tot / 1e3),
            "roofline": roofline, "clocks": clocks, "e2e": e2e,
            "gpu_launches": 2 * len(geoms) * args.steps, "peaks": peak_kind, "segment_lists": seg_leg,
-           "attenuated": att_leg}
+           "attenuated": att_leg, "dynamic": dyn_leg}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -432,6 +436,55 @@ def time_attenuated(args, wl, grid, geoms, rho, ws, flush, stream, n_rays, n_seg
                          "frac": fwd_ops / peak_ops, "kernel": "attenuated forward (tau_1 + y)",
                          "ops_per_segment": ops},
             "gpu_launches": (2 + 2 * len(geoms)) * args.steps}
+
+
+def time_dynamic(args, wl, grid, geoms, ws, flush, stream, n_rays, dist):
+    """Dynamic object (Sec. 4.4): each view set's views are the time steps of
+    a drifting object (view k sees volume k, the phantom scaled by
+    0.5 + k / n_views), F and F^T of every view set from scratch per step.
+    The volumes (32 x 2.9 MB per view set) no longer fit L1; they stay in L2."""
+    import torch
+
+    from paper_2608_16960_gb300.projector import tsp_adjoint_dynamic, tsp_forward_dynamic
+
+    vols = []
+    for g in geoms:
+        nv = g.det_shape[0]
+        scale = torch.tensor(0.5 + np.arange(nv) / nv, dtype=torch.float32, device="cuda")
+        vols.append((scale[:, None, None, None] * torch.tensor(wl.rho, device="cuda")[None]).contiguous())
+    outs = [torch.empty_like(v) for v in vols]
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        for g, v in zip(geoms, vols):
+            tsp_forward_dynamic(grid, g, v)
+        if ev:
+            ev[1].record(stream)
+        for g, w, o in zip(geoms, ws, outs):
+            tsp_adjoint_dynamic(grid, g, w, out=o)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        step(evs[k])
+    torch.cuda.synchronize()
+    from paper_2608_16960_gb300.dist import max_over_ranks
+    t_fwd = max_over_ranks(sum(e[0].elapsed_time(e[1]) for e in evs) / 1e3, device="cuda")
+    t_adj = max_over_ranks(sum(e[1].elapsed_time(e[2]) for e in evs) / 1e3, device="cuda")
+    world = dist.get_world_size() if dist else 1
+    return {"value": world * n_rays * args.steps / (t_fwd + t_adj), "unit": UNIT,
+            "fwd_rays_per_s": world * n_rays * args.steps / t_fwd,
+            "adj_rays_per_s": world * n_rays * args.steps / t_adj,
+            "ms_per_step": 1e3 * (t_fwd + t_adj) / args.steps,
+            "volumes": [int(v.shape[0]) for v in vols], "volume_bytes": int(sum(v.numel() * 4 for v in vols)),
+            "gpu_launches": 2 * len(geoms) * args.steps}
 
 
 def time_segment_lists(args, grid, geoms, rho, ws, flush, stream, n_rays, n_segs, peaks, dist):

@@ -123,6 +123,20 @@ tsp_status tsp_adjoint_ex(tsp_grid grid, tsp_geom geom, const float* y, float* r
                           int accumulate, const tsp_launch* launch, void* stream);
 
 /*
+ * Dynamic objects (Sec. 4.4: an Operator called with a 4D object; Sec. 4.3,
+ * 4.6: a collection of views taken in sequence while the grid stays fixed):
+ * view k of geom (k = 0 .. n_views - 1, each H x W rays; free-form rays are
+ * one view) sees volume k.
+ * tsp_forward_dynamic - y[k] = F_k rho[k]. rho: device float32 (n_views, N_r,
+ *   N_e, N_a); y: device float32 (n_views, H, W), overwritten.
+ * tsp_adjoint_dynamic - rho[k] (+)= F_k^T y[k]; accumulate as tsp_adjoint.
+ * Same traversal as tsp_forward / tsp_adjoint (bit-identical segments).
+ */
+tsp_status tsp_forward_dynamic(tsp_grid grid, tsp_geom geom, const float* rho, float* y, void* stream);
+tsp_status tsp_adjoint_dynamic(tsp_grid grid, tsp_geom geom, const float* y, float* rho, int accumulate,
+                               void* stream);
+
+/*
  * tsp_count_segments - counts[i] = number of valid segments of ray i (pieces
  * of the ray inside the grid with an in-range voxel index: the non-zero rows
  * of Table 2c). counts: device int32 [n_rays], overwritten.

@@ -87,6 +87,8 @@ SIGNATURES = {
     "tsp_adam": (_I, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                       ctypes.c_float, _I, _P]),
     "tsp_sq_residual": (_I, [_P, _P, _I64, _P, _P, _P]),
+    "tsp_forward_dynamic": (_I, [_P, _P, _P, _P, _P]),
+    "tsp_adjoint_dynamic": (_I, [_P, _P, _P, _P, _I, _P]),
     "tsp_sunward_rays": (_I, [_P, ctypes.POINTER(ctypes.c_double), _P, _P, _P]),
     "tsp_atten_optical_depth": (_I, [_P, _P, _P, _P, _P, _I, _P]),
     "tsp_atten_optical_depth_adjoint": (_I, [_P, _P, _P, _P, _P, _P, _P, _I, _I, _P]),

@@ -49,8 +49,23 @@ struct ProductGatherOp {
   __device__ __forceinline__ void end(int64_t ray) { out[ray] = acc; }
 };
 
+// Add x to *p; with AGG the active lanes of the warp that add to the same
+// address first combine their values and one of them adds the sum.
+template <bool AGG>
+__device__ __forceinline__ void scatter_add(float* p, int key, float x) {
+  if (AGG) {
+    cooperative_groups::coalesced_group act = cooperative_groups::coalesced_threads();
+    cooperative_groups::coalesced_group grp = cooperative_groups::labeled_partition(act, key);
+    const float sum = cooperative_groups::reduce(grp, x, cooperative_groups::plus<float>());
+    if (grp.thread_rank() == 0) atomicAdd(p, sum);
+  } else {
+    atomicAdd(p, x);
+  }
+}
+
 // Adjoint of ProductGatherOp: with w = g_tau1[ray], g_rho[v] += w sigma[v] dl
 // and g_sigma[v] += w rho[v] dl.
+template <bool AGG>
 struct ProductScatterOp {
   const float* __restrict__ rho;
   const float* __restrict__ sigma;
@@ -64,8 +79,8 @@ struct ProductScatterOp {
   }
   __device__ __forceinline__ void operator()(int v, float dl) {
     const float wd = __fmul_rn(w, dl);
-    atomicAdd(g_rho + v, __fmul_rn(wd, __ldg(sigma + v)));
-    if (g_sigma) atomicAdd(g_sigma + v, __fmul_rn(wd, __ldg(rho + v)));
+    scatter_add<AGG>(g_rho + v, v, __fmul_rn(wd, __ldg(sigma + v)));
+    if (g_sigma) scatter_add<AGG>(g_sigma + v, v, __fmul_rn(wd, __ldg(rho + v)));
   }
   __device__ __forceinline__ void end(int64_t) {}
 };
@@ -113,7 +128,8 @@ struct AttenFwdOp {
 // S_i = sum_{k >= i} c_k = Y - (c_0 + ... + c_{i-1}) (Y = the forward's y):
 //   dy/d(e^{-tau_1} rho)[v_i] = e^{-tau_2,i} dl_i,  dy/d(sigma rho)[v_i] = -dl_i S_i.
 // The running prefix repeats the forward's arithmetic, so S of the last
-// segment is that segment's own contribution.
+// segment is that segment's own contribution. AGG: warp-aggregated adds.
+template <bool AGG>
 struct AttenBwdOp {
   const float* __restrict__ rho;
   const float* __restrict__ sigma;
@@ -133,9 +149,9 @@ struct AttenBwdOp {
     const float e1 = expf(-t1);
     const float ga = __fmul_rn(__fmul_rn(w, expf(-tau2)), dl);  // d/d(e^{-tau_1} rho)
     const float gb = -__fmul_rn(__fmul_rn(w, dl), S);           // d/d(sigma rho)
-    atomicAdd(g_rho + v, fmaf(ga, e1, __fmul_rn(gb, s)));
-    if (g_sigma) atomicAdd(g_sigma + v, __fmul_rn(gb, r));
-    if (g_tau1) atomicAdd(g_tau1 + v, -__fmul_rn(__fmul_rn(ga, r), e1));
+    scatter_add<AGG>(g_rho + v, v, fmaf(ga, e1, __fmul_rn(gb, s)));
+    if (g_sigma) scatter_add<AGG>(g_sigma + v, v, __fmul_rn(gb, r));
+    if (g_tau1) scatter_add<AGG>(g_tau1 + v, v, -__fmul_rn(__fmul_rn(ga, r), e1));
   }
   __device__ __forceinline__ void flush() {
     if (run.pv >= 0) step(run.pv, run.pdl);
@@ -179,6 +195,36 @@ __global__ void sunward_rays_kernel(const float* __restrict__ centres, int Nr, i
     dirs[V + v] = sy;
     dirs[2 * V + v] = sz;
   }
+}
+
+template <bool AGG>
+void launch_product_scatter(tsp_grid grid, tsp_geom sun, const tsp_launch& l, const float* rho, const float* sigma,
+                            const float* g_tau1, float* g_rho, float* g_sigma, int b, cudaStream_t cs) {
+  const int64_t V = grid->voxels();
+  ProductScatterOp<AGG> op;
+  op.rho = rho + b * V;
+  op.sigma = sigma + b * V;
+  op.g_tau1 = g_tau1 + b * V;
+  op.g_rho = g_rho + b * V;
+  op.g_sigma = g_sigma ? g_sigma + b * V : nullptr;
+  launch_trace(grid, sun, l, op, cs);
+}
+
+template <bool AGG>
+void launch_atten_bwd(tsp_grid grid, tsp_geom geom, const tsp_launch& l, const float* rho, const float* sigma,
+                      const float* tau1, const float* y, const float* gy, float* g_rho, float* g_sigma,
+                      float* g_tau1, int b, cudaStream_t cs) {
+  const int64_t V = grid->voxels(), n = geom->n_rays;
+  AttenBwdOp<AGG> op;
+  op.rho = rho + b * V;
+  op.sigma = sigma + b * V;
+  op.tau1 = tau1 + b * V;
+  op.y = y + b * n;
+  op.gy = gy + b * n;
+  op.g_rho = g_rho + b * V;
+  op.g_sigma = g_sigma ? g_sigma + b * V : nullptr;
+  op.g_tau1 = g_tau1 ? g_tau1 + b * V : nullptr;
+  launch_trace(grid, geom, l, op, cs);
 }
 
 tsp_status check_sunward(tsp_grid grid, tsp_geom sun, const char* who) {
@@ -243,13 +289,8 @@ extern "C" tsp_status tsp_atten_optical_depth_adjoint(tsp_grid grid, tsp_geom su
     if (g_sigma) TSP_CUDA(cudaMemsetAsync(g_sigma, 0, sizeof(float) * size_t(V) * batch, cs));
   }
   for (int b = 0; b < batch; ++b) {
-    ProductScatterOp op;
-    op.rho = rho + b * V;
-    op.sigma = sigma + b * V;
-    op.g_tau1 = g_tau1 + b * V;
-    op.g_rho = g_rho + b * V;
-    op.g_sigma = g_sigma ? g_sigma + b * V : nullptr;
-    launch_trace(grid, sun, l, op, cs);
+    if (l.scatter == 1) launch_product_scatter<true>(grid, sun, l, rho, sigma, g_tau1, g_rho, g_sigma, b, cs);
+    else launch_product_scatter<false>(grid, sun, l, rho, sigma, g_tau1, g_rho, g_sigma, b, cs);
   }
   TSP_CUDA(cudaGetLastError());
   return TSP_OK;
@@ -290,16 +331,8 @@ extern "C" tsp_status tsp_atten_backward(tsp_grid grid, tsp_geom geom, const flo
     if (g_tau1) TSP_CUDA(cudaMemsetAsync(g_tau1, 0, bytes, cs));
   }
   for (int b = 0; b < batch; ++b) {
-    AttenBwdOp op;
-    op.rho = rho + b * V;
-    op.sigma = sigma + b * V;
-    op.tau1 = tau1 + b * V;
-    op.y = y + b * n;
-    op.gy = gy + b * n;
-    op.g_rho = g_rho + b * V;
-    op.g_sigma = g_sigma ? g_sigma + b * V : nullptr;
-    op.g_tau1 = g_tau1 ? g_tau1 + b * V : nullptr;
-    launch_trace(grid, geom, l, op, cs);
+    if (l.scatter == 1) launch_atten_bwd<true>(grid, geom, l, rho, sigma, tau1, y, gy, g_rho, g_sigma, g_tau1, b, cs);
+    else launch_atten_bwd<false>(grid, geom, l, rho, sigma, tau1, y, gy, g_rho, g_sigma, g_tau1, b, cs);
   }
   TSP_CUDA(cudaGetLastError());
   return TSP_OK;

@@ -22,6 +22,51 @@ struct CountOp {
   __device__ __forceinline__ void end(int64_t ray) { counts[ray] = n; }
 };
 
+// Dynamic object (Sec. 4.4: a 4D object seen by a collection of sequential
+// views): view k of the geometry sees volume k. The ray's view is its index
+// divided by the rays per view; all lanes of a warp share a view.
+struct DynGatherOp {
+  const float* __restrict__ rho;
+  float* __restrict__ y;
+  int64_t V, per_view;
+  const float* base;
+  float acc;
+  __device__ __forceinline__ bool begin(int64_t ray) {
+    base = rho + (ray / per_view) * V;
+    acc = 0.0f;
+    return true;
+  }
+  __device__ __forceinline__ void operator()(int v, float dl) { acc = fmaf(__ldg(base + v), dl, acc); }
+  __device__ __forceinline__ void end(int64_t ray) { y[ray] = acc; }
+};
+
+// Adjoint of DynGatherOp: g[view][v] += y dl, one atomic add per segment, or
+// (AGG) one per group of lanes of a warp that hit the same voxel in a step.
+template <bool AGG>
+struct DynScatterOp {
+  const float* __restrict__ y;
+  float* __restrict__ g;
+  int64_t V, per_view;
+  float* base;
+  float w;
+  __device__ __forceinline__ bool begin(int64_t ray) {
+    base = g + (ray / per_view) * V;
+    w = __ldg(y + ray);
+    return AGG || w != 0.0f;  // the aggregated form needs every lane in the combine
+  }
+  __device__ __forceinline__ void operator()(int v, float dl) {
+    if (AGG) {
+      cooperative_groups::coalesced_group act = cooperative_groups::coalesced_threads();
+      cooperative_groups::coalesced_group grp = cooperative_groups::labeled_partition(act, v);
+      const float s = cooperative_groups::reduce(grp, __fmul_rn(w, dl), cooperative_groups::plus<float>());
+      if (grp.thread_rank() == 0) atomicAdd(base + v, s);
+    } else {
+      atomicAdd(base + v, __fmul_rn(w, dl));
+    }
+  }
+  __device__ __forceinline__ void end(int64_t) {}
+};
+
 template <int NB>
 void forward_chunk(tsp_grid grid, tsp_geom geom, const tsp_launch& l, const float* rho, float* y, int nb,
                    cudaStream_t st) {
@@ -115,6 +160,48 @@ extern "C" tsp_status tsp_count_segments(tsp_grid grid, tsp_geom geom, int* coun
   CountOp op;
   op.counts = counts;
   launch_trace(grid, geom, default_launch(), op, static_cast<cudaStream_t>(stream));
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_forward_dynamic(tsp_grid grid, tsp_geom geom, const float* rho, float* y, void* stream) {
+  tsp_status st = check_trace_args(grid, geom, rho, y, 1, nullptr, "tsp_forward_dynamic");
+  if (st != TSP_OK) return st;
+  const tsp_launch l = preferred_launch(grid, geom, false);
+  DynGatherOp op;
+  op.rho = rho;
+  op.y = y;
+  op.V = grid->voxels();
+  op.per_view = geom->n_rays / std::max(1, geom->n_views);
+  launch_trace(grid, geom, l, op, static_cast<cudaStream_t>(stream));
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_adjoint_dynamic(tsp_grid grid, tsp_geom geom, const float* y, float* rho, int accumulate,
+                                          void* stream) {
+  tsp_status st = check_trace_args(grid, geom, y, rho, 1, nullptr, "tsp_adjoint_dynamic");
+  if (st != TSP_OK) return st;
+  const tsp_launch l = preferred_launch(grid, geom, true);
+  const int64_t V = grid->voxels();
+  const int nv = std::max(1, geom->n_views);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  if (!accumulate) TSP_CUDA(cudaMemsetAsync(rho, 0, sizeof(float) * size_t(V) * nv, cs));
+  if (l.scatter == 1) {
+    DynScatterOp<true> op;
+    op.y = y;
+    op.g = rho;
+    op.V = V;
+    op.per_view = geom->n_rays / nv;
+    launch_trace(grid, geom, l, op, cs);
+  } else {
+    DynScatterOp<false> op;
+    op.y = y;
+    op.g = rho;
+    op.V = V;
+    op.per_view = geom->n_rays / nv;
+    launch_trace(grid, geom, l, op, cs);
+  }
   TSP_CUDA(cudaGetLastError());
   return TSP_OK;
 }

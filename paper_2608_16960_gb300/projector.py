@@ -364,16 +364,73 @@ class ProjectorFn(torch.autograd.Function):
         return g, None, None, None
 
 
-class Operator:
-    """Operator(grid, geom): callable F with autograd (Sec. 4.4, Listing 6)."""
+def _views(geom: Geometry) -> int:
+    return geom.det_shape[0] if len(geom.det_shape) == 3 else 1
 
-    def __init__(self, grid: Grid, geom: Geometry, launch=None):
-        self.grid, self.geom, self.launch = grid, geom, launch
+
+def tsp_forward_dynamic(grid: Grid, geom: Geometry, rho: torch.Tensor) -> torch.Tensor:
+    """Dynamic object (Sec. 4.4): y[k] = F_k rho[k], view k of the collection
+    seeing volume k. rho: (n_views, N_r, N_e, N_a); y shaped like the detector."""
+    _require_cuda(rho, "rho")
+    nv = _views(geom)
+    if tuple(rho.shape) != (nv,) + grid.shape:
+        raise ValueError(f"rho shape {tuple(rho.shape)} must be (views={nv},) + {grid.shape}")
+    y = torch.empty(geom.det_shape, device=rho.device, dtype=torch.float32)
+    check(_lib.load().tsp_forward_dynamic(grid.handle, geom.handle, ctypes.c_void_p(rho.data_ptr()),
+                                          ctypes.c_void_p(y.data_ptr()), _stream(rho)), "tsp_forward_dynamic")
+    return y
+
+
+def tsp_adjoint_dynamic(grid: Grid, geom: Geometry, y: torch.Tensor, out: torch.Tensor | None = None,
+                        accumulate: bool = False) -> torch.Tensor:
+    """rho[k] (+)= F_k^T y[k]; returns (n_views, N_r, N_e, N_a)."""
+    _require_cuda(y, "y")
+    if tuple(y.shape) != geom.det_shape:
+        raise ValueError(f"y shape {tuple(y.shape)} does not match geometry {geom.det_shape}")
+    shape = (_views(geom),) + grid.shape
+    if out is None:
+        out = torch.empty(shape, device=y.device, dtype=torch.float32)
+        accumulate = False
+    else:
+        _require_cuda(out, "out")
+        if tuple(out.shape) != shape:
+            raise ValueError("out has the wrong shape")
+    check(_lib.load().tsp_adjoint_dynamic(grid.handle, geom.handle, ctypes.c_void_p(y.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), int(accumulate), _stream(y)),
+          "tsp_adjoint_dynamic")
+    return out
+
+
+class DynamicProjectorFn(torch.autograd.Function):
+    """Autograd function of the dynamic projection: backward = tsp_adjoint_dynamic."""
+
+    @staticmethod
+    def forward(ctx, rho, grid, geom):
+        ctx.grid, ctx.geom = grid, geom
+        return tsp_forward_dynamic(grid, geom, rho.contiguous())
+
+    @staticmethod
+    def backward(ctx, gy):
+        return tsp_adjoint_dynamic(ctx.grid, ctx.geom, gy.contiguous()), None, None
+
+
+class Operator:
+    """Operator(grid, geom): callable F with autograd (Sec. 4.4, Listing 6).
+    Called with a 3D object it projects it through every view; a 4D object
+    is a batch of independent objects, or, with dynamic=True, a dynamic
+    object whose k-th volume is seen by the k-th view (Sec. 4.4)."""
+
+    def __init__(self, grid: Grid, geom: Geometry, launch=None, dynamic: bool = False):
+        self.grid, self.geom, self.launch, self.dynamic = grid, geom, launch, dynamic
 
     def __call__(self, rho: torch.Tensor) -> torch.Tensor:
+        if self.dynamic and rho.dim() == 4:
+            return DynamicProjectorFn.apply(rho, self.grid, self.geom)
         return ProjectorFn.apply(rho, self.grid, self.geom, self.launch)
 
     def T(self, y: torch.Tensor) -> torch.Tensor:
+        if self.dynamic:
+            return tsp_adjoint_dynamic(self.grid, self.geom, y)
         return tsp_adjoint(self.grid, self.geom, y, launch=self.launch)
 
 
