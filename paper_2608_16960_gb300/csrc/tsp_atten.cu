@@ -22,13 +22,24 @@
 namespace tsp {
 namespace {
 
-// Joins consecutive pieces of one voxel; Step(v, dl) is applied per run.
+// Joins consecutive pieces of one voxel into runs. The voxel's rho, sigma
+// and tau_1 are gathered when its run starts and used when it ends (at the
+// next traversal step at the earliest), so the gathers overlap the search
+// for the next crossing.
 struct RunJoin {
   int pv;
-  float pdl;
+  float pdl, r, s, t1;
   __device__ __forceinline__ void reset() {
     pv = -1;
     pdl = 0.0f;
+  }
+  __device__ __forceinline__ void start(int v, float dl, const float* __restrict__ rho,
+                                        const float* __restrict__ sigma, const float* __restrict__ tau1) {
+    pv = v;
+    pdl = dl;
+    r = __ldg(rho + v);
+    s = __ldg(sigma + v);
+    t1 = __ldg(tau1 + v);
   }
 };
 
@@ -93,13 +104,12 @@ struct AttenFwdOp {
   float* __restrict__ y;
   RunJoin run;
   float tau2, acc;
-  __device__ __forceinline__ void step(int v, float dl) {
-    const float r = __ldg(rho + v);
-    tau2 = fmaf(__fmul_rn(__ldg(sigma + v), r), dl, tau2);
-    acc = fmaf(__fmul_rn(r, expf(-__fadd_rn(__ldg(tau1 + v), tau2))), dl, acc);
-  }
   __device__ __forceinline__ void flush() {
-    if (run.pv >= 0) step(run.pv, run.pdl);
+    if (run.pv >= 0) {
+      const float r = run.r, dl = run.pdl;
+      tau2 = fmaf(__fmul_rn(run.s, r), dl, tau2);
+      acc = fmaf(__fmul_rn(r, expf(-__fadd_rn(run.t1, tau2))), dl, acc);
+    }
     run.reset();
   }
   __device__ __forceinline__ bool begin(int64_t) {
@@ -112,8 +122,7 @@ struct AttenFwdOp {
       run.pdl = __fadd_rn(run.pdl, dl);
     } else {
       flush();
-      run.pv = v;
-      run.pdl = dl;
+      run.start(v, dl, rho, sigma, tau1);
     }
   }
   __device__ __forceinline__ void gap() { flush(); }
@@ -141,8 +150,7 @@ struct AttenBwdOp {
   float* __restrict__ g_tau1;   // may be null
   RunJoin run;
   float tau2, pre, Y, w;
-  __device__ __forceinline__ void step(int v, float dl) {
-    const float r = __ldg(rho + v), s = __ldg(sigma + v), t1 = __ldg(tau1 + v);
+  __device__ __forceinline__ void step(int v, float dl, float r, float s, float t1) {
     tau2 = fmaf(__fmul_rn(s, r), dl, tau2);
     const float S = __fsub_rn(Y, pre);  // contributions from this segment on
     pre = fmaf(__fmul_rn(r, expf(-__fadd_rn(t1, tau2))), dl, pre);
@@ -154,7 +162,7 @@ struct AttenBwdOp {
     if (g_tau1) scatter_add<AGG>(g_tau1 + v, v, -__fmul_rn(__fmul_rn(ga, r), e1));
   }
   __device__ __forceinline__ void flush() {
-    if (run.pv >= 0) step(run.pv, run.pdl);
+    if (run.pv >= 0) step(run.pv, run.pdl, run.r, run.s, run.t1);
     run.reset();
   }
   __device__ __forceinline__ bool begin(int64_t ray) {
@@ -169,8 +177,7 @@ struct AttenBwdOp {
       run.pdl = __fadd_rn(run.pdl, dl);
     } else {
       flush();
-      run.pv = v;
-      run.pdl = dl;
+      run.start(v, dl, rho, sigma, tau1);
     }
   }
   __device__ __forceinline__ void gap() { flush(); }
