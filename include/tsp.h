@@ -90,6 +90,18 @@ tsp_status tsp_geom_parallel(int n_views, const double* pos, const double* up, i
  */
 tsp_status tsp_geom_rays(int64_t n_rays, const float* starts, const float* dirs, int copy,
                          tsp_geom* out);
+/*
+ * tsp_geom_polar - polar-binned detectors (Sec. 6: images binned to n_rad
+ * radial x n_az azimuthal polar pixels of an equivalent field of view): per
+ * view a pinhole at pos looking at look_at (origin if NULL) with up hint up
+ * (+Z if NULL; frame as tsp_geom_cone). Pixel (i, j) looks at the angle
+ * (i + 1/2) / n_rad * fov_deg / 2 from the boresight, at azimuth
+ * 2 pi (j + 1/2) / n_az from the right axis toward up. Rays are ordered
+ * (view, i, j); the geometry has n_views views of n_rad x n_az rays, so the
+ * dynamic projections see one volume per view. fov_deg in (0, 180).
+ */
+tsp_status tsp_geom_polar(int n_views, const double* pos, const double* look_at, const double* up, int n_rad,
+                          int n_az, double fov_deg, tsp_geom* out);
 tsp_status tsp_geom_num_rays(tsp_geom geom, int64_t* n_rays);
 void tsp_geom_destroy(tsp_geom geom);
 
@@ -370,6 +382,14 @@ tsp_status tsp_shbs_create(int n_basis_r, int L, const double* r_centres, int n_
 tsp_status tsp_shbs_tables(tsp_shbs model, float* B, float* Yt);
 tsp_status tsp_shbs_render(tsp_shbs model, const float* coeffs, float* rho, void* stream);
 tsp_status tsp_shbs_render_adjoint(tsp_shbs model, const float* grad_rho, float* grad_coeffs, void* stream);
+/*
+ * tsp_shbs_create_shells - the per-shell model of Eq. 10:
+ * rho[ir, ie, ia] = sum_q coeffs[ir][q] Y_q(theta_ie, phi_ia), one harmonic
+ * series per shell (the same handle type with the identity as radial basis:
+ * coeffs is [N_r][(L+1)^2]; render / render_adjoint / tables as above).
+ */
+tsp_status tsp_shbs_create_shells(int L, int n_r, const double* theta_centres, int n_e, const double* phi_centres,
+                                  int n_a, tsp_shbs* out);
 void tsp_shbs_destroy(tsp_shbs model);
 
 /*
@@ -386,6 +406,32 @@ tsp_status tsp_adam(float* params, const float* grads, float* m, float* v, int64
  * grad = 2 (yhat - y) (device float32, n values).
  */
 tsp_status tsp_sq_residual(const float* yhat, const float* y, int64_t n, float* grad, double* loss, void* stream);
+
+/*
+ * tsp_tikhonov_radial - the regulariser of Eq. 10, lambda ||D_r c||^2 with
+ * D_r the first difference between neighbouring shells of every
+ * coefficient: coeffs device float32 [n_r][n_q]; loss += the value (device
+ * double, accumulated; may be NULL); grad += its gradient (device float32
+ * [n_r][n_q], accumulated; may be NULL). lambda >= 0.
+ * tsp_sq_residual_weighted - the data term of Eq. 10 with Eq. 9's known
+ * per-ray factor w = (g / 4 pi) phi(n): loss += sum (w yhat - y)^2 (device
+ * double, accumulated) and, if grad != NULL, grad = 2 w (w yhat - y), where
+ * yhat = F rho is the plain line integral.
+ */
+tsp_status tsp_tikhonov_radial(const float* coeffs, int n_r, int n_q, float lambda, float* grad, double* loss,
+                               void* stream);
+tsp_status tsp_sq_residual_weighted(const float* yhat, const float* w, const float* y, int64_t n, float* grad,
+                                    double* loss, void* stream);
+
+/*
+ * Vector kernels of the iterative solvers (device float32 vectors of n
+ * values): tsp_vec_dot - out += sum x y (device double, accumulated: zero it
+ * first); tsp_vec_axpby - y = a x + b y; tsp_vec_mul - out = w x
+ * (elementwise; out may alias x).
+ */
+tsp_status tsp_vec_dot(const float* x, const float* y, int64_t n, double* out, void* stream);
+tsp_status tsp_vec_axpby(float a, const float* x, float b, float* y, int64_t n, void* stream);
+tsp_status tsp_vec_mul(const float* w, const float* x, float* out, int64_t n, void* stream);
 
 /*
  * Learned warm start: a residual 3D convolutional network on the spherical grid

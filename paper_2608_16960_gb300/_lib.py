@@ -87,6 +87,15 @@ SIGNATURES = {
     "tsp_adam": (_I, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                       ctypes.c_float, _I, _P]),
     "tsp_sq_residual": (_I, [_P, _P, _I64, _P, _P, _P]),
+    "tsp_geom_polar": (_I, [_I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double), _I, _I, ctypes.c_double, ctypes.POINTER(_P)]),
+    "tsp_shbs_create_shells": (_I, [_I, _I, ctypes.POINTER(ctypes.c_double), _I, ctypes.POINTER(ctypes.c_double), _I,
+                                    ctypes.POINTER(_P)]),
+    "tsp_tikhonov_radial": (_I, [_P, _I, _I, ctypes.c_float, _P, _P, _P]),
+    "tsp_sq_residual_weighted": (_I, [_P, _P, _P, ctypes.c_int64, _P, _P, _P]),
+    "tsp_vec_dot": (_I, [_P, _P, ctypes.c_int64, _P, _P]),
+    "tsp_vec_axpby": (_I, [ctypes.c_float, _P, ctypes.c_float, _P, ctypes.c_int64, _P]),
+    "tsp_vec_mul": (_I, [_P, _P, _P, ctypes.c_int64, _P]),
     "tsp_forward_dynamic": (_I, [_P, _P, _P, _P, _P]),
     "tsp_adjoint_dynamic": (_I, [_P, _P, _P, _P, _I, _P]),
     "tsp_sunward_rays": (_I, [_P, ctypes.POINTER(ctypes.c_double), _P, _P, _P]),

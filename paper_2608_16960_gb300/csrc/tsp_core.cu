@@ -327,6 +327,92 @@ extern "C" tsp_status tsp_geom_cone(int n_views, const double* pos, const double
   return TSP_OK;
 }
 
+namespace {
+// Polar-binned detector rays (Sec. 6): tab = per view [pos | look | right | up]
+// (12 floats), then cos/sin of the n_rad bin angles and of the n_az bin
+// azimuths. Ray (v, i, j) = pos_v + l (cos t_i look + sin t_i (cos p_j right
+// + sin p_j up)); out = starts [3][n] | dirs [3][n].
+__global__ void polar_rays_kernel(const float* __restrict__ tab, int n_views, int n_rad, int n_az,
+                                  float* __restrict__ out) {
+  const int64_t n = int64_t(n_views) * n_rad * n_az;
+  const float* ct = tab + 12 * n_views;
+  const float* st = ct + n_rad;
+  const float* cp = st + n_rad;
+  const float* sp = cp + n_az;
+  for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+    const int j = int(k % n_az), i = int((k / n_az) % n_rad), v = int(k / (int64_t(n_az) * n_rad));
+    const float* f = tab + 12 * v;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float side = fmaf(cp[j], f[6 + c], __fmul_rn(sp[j], f[9 + c]));
+      out[c * n + k] = f[c];
+      out[(3 + c) * n + k] = fmaf(ct[i], f[3 + c], __fmul_rn(st[i], side));
+    }
+  }
+}
+}  // namespace
+
+extern "C" tsp_status tsp_geom_polar(int n_views, const double* pos, const double* look_at, const double* up,
+                                     int n_rad, int n_az, double fov_deg, tsp_geom* out) {
+  if (!out) return fail(TSP_EINVAL, "tsp_geom_polar: out is NULL");
+  *out = nullptr;
+  if (n_views <= 0 || n_rad <= 0 || n_az <= 0 || !pos) return fail(TSP_EINVAL, "tsp_geom_polar: bad size or NULL pos");
+  if (!(fov_deg > 0 && fov_deg < 180)) return fail(TSP_EINVAL, "tsp_geom_polar: field of view must be in (0, 180)");
+  const int64_t n = int64_t(n_views) * n_rad * n_az;
+  if (n >= (int64_t(1) << 40)) return fail(TSP_ENOTSUP, "tsp_geom_polar: too many rays");
+  std::vector<float> tab(size_t(12) * n_views + 2 * size_t(n_rad) + 2 * size_t(n_az));
+  for (int v = 0; v < n_views; ++v) {
+    double look[3], right[3], upv[3];
+    if (!view_frame(pos + 3 * v, look_at ? look_at + 3 * v : nullptr, up ? up + 3 * v : nullptr, look, right, upv))
+      return fail(TSP_EINVAL, "tsp_geom_polar: degenerate view (pos equals look_at?)");
+    for (int c = 0; c < 3; ++c) {
+      tab[12 * v + c] = float(pos[3 * v + c]);
+      tab[12 * v + 3 + c] = float(look[c]);
+      tab[12 * v + 6 + c] = float(right[c]);
+      tab[12 * v + 9 + c] = float(upv[c]);
+    }
+  }
+  const double half = 0.5 * fov_deg * kPi / 180.0;
+  float* t = tab.data() + 12 * size_t(n_views);
+  for (int i = 0; i < n_rad; ++i) {
+    const double a = (i + 0.5) / n_rad * half;
+    t[i] = float(std::cos(a));
+    t[n_rad + i] = float(std::sin(a));
+  }
+  for (int j = 0; j < n_az; ++j) {
+    const double a = 2.0 * kPi * (j + 0.5) / n_az;
+    t[2 * n_rad + j] = float(std::cos(a));
+    t[2 * n_rad + n_az + j] = float(std::sin(a));
+  }
+  tsp_geom g = new (std::nothrow) tsp_geom_s();
+  if (!g) return fail(TSP_ENOMEM, "tsp_geom_polar: host allocation");
+  g->kind = GEOM_RAYS;
+  g->n_views = n_views;
+  g->H = n_rad;
+  g->W = n_az;
+  g->n_rays = n;
+  float* d_tab = nullptr;
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e == cudaSuccess) e = cudaMalloc(&g->owned, sizeof(float) * 6 * size_t(n));
+  if (e == cudaSuccess) e = cudaMalloc(&d_tab, sizeof(float) * tab.size());
+  if (e == cudaSuccess) e = cudaMemcpy(d_tab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const unsigned blocks = unsigned(std::min<int64_t>((n + 255) / 256, 152 * 16));
+    polar_rays_kernel<<<blocks, 256>>>(d_tab, n_views, n_rad, n_az, g->owned);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (d_tab) cudaFree(d_tab);
+  if (e != cudaSuccess) {
+    tsp_geom_destroy(g);
+    return tsp::cuda_fail(e, "tsp_geom_polar");
+  }
+  g->starts = g->owned;
+  g->dirs = g->owned + 3 * n;
+  *out = g;
+  return TSP_OK;
+}
+
 extern "C" tsp_status tsp_geom_parallel(int n_views, const double* pos, const double* up, int H, int W,
                                         double size_h, double size_w, tsp_geom* out) {
   if (!out) return fail(TSP_EINVAL, "tsp_geom_parallel: out is NULL");

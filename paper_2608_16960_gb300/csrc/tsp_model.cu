@@ -170,6 +170,82 @@ __global__ void sq_residual_kernel(const float* __restrict__ yhat, const float* 
   }
 }
 
+// loss += lambda sum_{ir < Nr-1, q} (c[ir+1][q] - c[ir][q])^2 (double) and
+// grad[ir][q] += its derivative: one thread per coefficient.
+__global__ void tikhonov_radial_kernel(const float* __restrict__ c, int Nr, int nq, float lambda,
+                                       float* __restrict__ grad, double* __restrict__ loss) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double part = 0.0;
+  if (i < Nr * nq) {
+    const int ir = i / nq;
+    const float here = c[i];
+    float g = 0.0f;
+    if (ir > 0) g = fmaf(2.0f * lambda, here - c[i - nq], g);
+    if (ir + 1 < Nr) {
+      const float d = c[i + nq] - here;
+      g = fmaf(-2.0f * lambda, d, g);
+      part = double(lambda) * double(d) * double(d);
+    }
+    if (grad) grad[i] += g;
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, part);
+}
+
+// loss += sum (w yhat - y)^2 (double); grad = 2 w (w yhat - y).
+__global__ void weighted_residual_kernel(const float* __restrict__ yhat, const float* __restrict__ w,
+                                         const float* __restrict__ y, int64_t n, float* __restrict__ grad,
+                                         double* __restrict__ loss) {
+  double acc = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const float wi = w[i];
+    const float r = fmaf(wi, yhat[i], -y[i]);
+    if (grad) grad[i] = 2.0f * wi * r;
+    acc += double(r) * double(r);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0 && loss) atomicAdd(loss, v);
+  }
+}
+
+// out += sum x y (double), grid-stride with a block reduction.
+__global__ void vec_dot_kernel(const float* __restrict__ x, const float* __restrict__ y, int64_t n,
+                               double* __restrict__ out) {
+  double acc = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    acc += double(x[i]) * double(y[i]);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) atomicAdd(out, v);
+  }
+}
+
+// y = a x + b y
+__global__ void vec_axpby_kernel(float a, const float* __restrict__ x, float b, float* __restrict__ y, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = fmaf(a, x[i], b * y[i]);
+}
+
+// out = w x (elementwise)
+__global__ void vec_mul_kernel(const float* __restrict__ w, const float* __restrict__ x, float* __restrict__ out,
+                               int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = w[i] * x[i];
+}
+
+int vec_blocks(int64_t n) { return int(std::min<int64_t>((n + 255) / 256, 152 * 8)); }
+
 }  // namespace
 }  // namespace tsp
 
@@ -211,6 +287,42 @@ extern "C" tsp_status tsp_shbs_create(int n_basis_r, int L, const double* r_cent
   if (e != cudaSuccess) {
     tsp_shbs_destroy(h);
     return cuda_fail(e, "tsp_shbs_create: upload");
+  }
+  *out = h;
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_shbs_create_shells(int L, int Nr, const double* theta_centres, int Ne,
+                                             const double* phi_centres, int Na, tsp_shbs* out) {
+  if (!out) return fail(TSP_EINVAL, "tsp_shbs_create_shells: out is NULL");
+  *out = nullptr;
+  if (L < 0 || L > 32 || Nr <= 0 || Ne <= 0 || Na <= 0 || !theta_centres || !phi_centres)
+    return fail(TSP_EINVAL, "tsp_shbs_create_shells: bad argument");
+  tsp_shbs h = new (std::nothrow) tsp_shbs_s();
+  if (!h) return fail(TSP_ENOMEM, "tsp_shbs_create_shells: host allocation");
+  h->Nr = Nr;
+  h->nang = Ne * Na;
+  h->nb = Nr;
+  h->L = L;
+  h->nq = (L + 1) * (L + 1);
+  std::vector<float> B(size_t(Nr) * Nr, 0.0f), Yt(size_t(h->nq) * h->nang);
+  for (int ir = 0; ir < Nr; ++ir) B[size_t(ir) * Nr + ir] = 1.0f;  // one coefficient set per shell
+  std::vector<double> row(h->nq);
+  for (int ie = 0; ie < Ne; ++ie) {
+    for (int ia = 0; ia < Na; ++ia) {
+      sh_row(theta_centres[ie], phi_centres[ia], L, row.data());
+      for (int q = 0; q < h->nq; ++q) Yt[size_t(q) * h->nang + ie * Na + ia] = float(row[q]);
+    }
+  }
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaMalloc(&h->B, sizeof(float) * B.size());
+  if (e == cudaSuccess) e = cudaMalloc(&h->Yt, sizeof(float) * Yt.size());
+  if (e == cudaSuccess) e = cudaMalloc(&h->T, sizeof(float) * size_t(Nr) * h->nq);
+  if (e == cudaSuccess) e = cudaMemcpy(h->B, B.data(), sizeof(float) * B.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->Yt, Yt.data(), sizeof(float) * Yt.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    tsp_shbs_destroy(h);
+    return cuda_fail(e, "tsp_shbs_create_shells: upload");
   }
   *out = h;
   return TSP_OK;
@@ -273,6 +385,50 @@ extern "C" tsp_status tsp_sq_residual(const float* yhat, const float* y, int64_t
   if (!yhat || !y || n <= 0) return fail(TSP_EINVAL, "tsp_sq_residual: bad argument");
   const int blocks = int(std::min<int64_t>((n + 255) / 256, 152 * 8));
   sq_residual_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(yhat, y, n, grad, loss);
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_tikhonov_radial(const float* coeffs, int n_r, int n_q, float lambda, float* grad,
+                                          double* loss, void* stream) {
+  if (!coeffs || n_r <= 0 || n_q <= 0 || !(lambda >= 0.0f))
+    return fail(TSP_EINVAL, "tsp_tikhonov_radial: bad argument");
+  const int n = n_r * n_q;
+  tikhonov_radial_kernel<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(coeffs, n_r, n_q, lambda,
+                                                                                          grad, loss);
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_sq_residual_weighted(const float* yhat, const float* w, const float* y, int64_t n,
+                                               float* grad, double* loss, void* stream) {
+  if (!yhat || !w || !y || n <= 0) return fail(TSP_EINVAL, "tsp_sq_residual_weighted: bad argument");
+  const int blocks = int(std::min<int64_t>((n + 255) / 256, 152 * 8));
+  weighted_residual_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(yhat, w, y, n, grad, loss);
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_vec_dot(const float* x, const float* y, int64_t n, double* out, void* stream) {
+  if (!x || !y || !out || n < 0) return fail(TSP_EINVAL, "tsp_vec_dot: bad argument");
+  if (n == 0) return TSP_OK;
+  vec_dot_kernel<<<vec_blocks(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(x, y, n, out);
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_vec_axpby(float a, const float* x, float b, float* y, int64_t n, void* stream) {
+  if (!x || !y || n < 0) return fail(TSP_EINVAL, "tsp_vec_axpby: bad argument");
+  if (n == 0) return TSP_OK;
+  vec_axpby_kernel<<<vec_blocks(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(a, x, b, y, n);
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_vec_mul(const float* w, const float* x, float* out, int64_t n, void* stream) {
+  if (!w || !x || !out || n < 0) return fail(TSP_EINVAL, "tsp_vec_mul: bad argument");
+  if (n == 0) return TSP_OK;
+  vec_mul_kernel<<<vec_blocks(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(w, x, out, n);
   TSP_CUDA(cudaGetLastError());
   return TSP_OK;
 }

@@ -61,6 +61,26 @@ class SHBSpline:
             self.handle = None
 
 
+class ShellSH(SHBSpline):
+    """Eq. 10's model: one real spherical-harmonic series of degree <= L per
+    shell, rho[ir] = sum_q c[ir][q] Y_q at the voxel centres (the SHBSpline
+    handle with the identity as radial basis; coefficients (N_r, (L+1)^2))."""
+
+    def __init__(self, edges, L: int = 3):
+        L_ = _lib.load()
+        tc = np.ascontiguousarray(0.5 * (edges.theta[:-1] + edges.theta[1:]), dtype=np.float64)
+        pc = np.ascontiguousarray(0.5 * (edges.phi[:-1] + edges.phi[1:]), dtype=np.float64)
+        nr = len(edges.r) - 1
+        h = ctypes.c_void_p()
+        check(L_.tsp_shbs_create_shells(L, nr, _dp(tc), len(tc), _dp(pc), len(pc), ctypes.byref(h)),
+              "tsp_shbs_create_shells")
+        self.handle = h
+        self.n_basis_r, self.L = nr, L
+        self.nq = (L + 1) ** 2
+        self.shape = (nr, len(tc), len(pc))
+        self.coeff_shape = (nr, self.nq)
+
+
 class ShbsRenderFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, coeffs, model):
@@ -105,6 +125,50 @@ class SquaredErrorFn(torch.autograd.Function):
 
 def squared_error(yhat, y):
     return SquaredErrorFn.apply(yhat, y)
+
+
+class WeightedSquaredErrorFn(torch.autograd.Function):
+    """Eq. 10's data term with Eq. 9's per-ray factor: sum (w yhat - y)^2,
+    the gradient 2 w (w yhat - y) from one kernel (tsp_sq_residual_weighted)."""
+
+    @staticmethod
+    def forward(ctx, yhat, w, y):
+        yhat, w, y = yhat.contiguous(), w.contiguous(), y.contiguous()
+        _require_cuda(yhat, "yhat")
+        grad = torch.empty_like(yhat)
+        loss = torch.zeros((), dtype=torch.float64, device=yhat.device)
+        check(_lib.load().tsp_sq_residual_weighted(ctypes.c_void_p(yhat.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+                                                   ctypes.c_void_p(y.data_ptr()), yhat.numel(),
+                                                   ctypes.c_void_p(grad.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                                                   _stream(yhat)), "tsp_sq_residual_weighted")
+        ctx.save_for_backward(grad)
+        return loss
+
+    @staticmethod
+    def backward(ctx, gl):
+        (grad,) = ctx.saved_tensors
+        return grad * gl.to(grad.dtype), None, None
+
+
+class TikhonovRadialFn(torch.autograd.Function):
+    """Eq. 10's regulariser lambda ||D_r c||^2 (tsp_tikhonov_radial)."""
+
+    @staticmethod
+    def forward(ctx, c, lam):
+        c = c.contiguous()
+        _require_cuda(c, "c")
+        grad = torch.zeros_like(c)
+        loss = torch.zeros((), dtype=torch.float64, device=c.device)
+        check(_lib.load().tsp_tikhonov_radial(ctypes.c_void_p(c.data_ptr()), c.shape[0], c.shape[1], float(lam),
+                                              ctypes.c_void_p(grad.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                                              _stream(c)), "tsp_tikhonov_radial")
+        ctx.save_for_backward(grad)
+        return loss
+
+    @staticmethod
+    def backward(ctx, gl):
+        (grad,) = ctx.saved_tensors
+        return grad * gl.to(grad.dtype), None
 
 
 class Adam:

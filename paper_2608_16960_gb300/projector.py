@@ -120,6 +120,22 @@ class Geometry:
         return cls(h, "parallel", (nv, H, W), nv * H * W)
 
     @classmethod
+    def polar(cls, pos, shape, fov_deg, look_at=None, up=None):
+        """Polar-binned detectors (Sec. 6): per view n_rad x n_az polar pixels
+        over the field of view fov_deg; shape = (n_rad, n_az)."""
+        L = _lib.load()
+        pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3))
+        nv = pos.shape[0]
+        la = None if look_at is None else np.ascontiguousarray(np.asarray(look_at, np.float64).reshape(nv, 3))
+        uh = None if up is None else np.ascontiguousarray(np.asarray(up, np.float64).reshape(nv, 3))
+        nr, na = shape
+        h = ctypes.c_void_p()
+        check(L.tsp_geom_polar(nv, _dptr(pos), _dptr(la) if la is not None else None,
+                               _dptr(uh) if uh is not None else None, nr, na, float(fov_deg), ctypes.byref(h)),
+              "tsp_geom_polar")
+        return cls(h, "polar", (nv, nr, na), nv * nr * na)
+
+    @classmethod
     def rays(cls, starts: torch.Tensor, dirs: torch.Tensor, copy: bool = True):
         """Free-form rays; starts and dirs are CUDA float32 (3, n) tensors."""
         L = _lib.load()

@@ -126,3 +126,62 @@ def differentiation(shape=(128, 64, 128), n_views=64, det=512, n_basis=20, L=8) 
     c[:, 1:] = 0.2 * c[:, :1] * rng.normal(n_basis * (nq - 1)).reshape(n_basis, nq - 1) / (ell[1:] + 1.0)
     pos = synth.circular_orbit(n_views, 60.0, incline_deg=30.0, phase=float(synth.SplitMix64(5).uniform(1)[0]))
     return Differentiation(e, ViewSet("cone", pos, (det, det), 50.0), n_basis, L, c.astype(np.float32), 44, 0.01)
+
+
+class Exosphere:
+    edges: synth.GridEdges
+    pos: np.ndarray        # (n_views, 3) spacecraft positions
+    shape: tuple           # (n_rad, n_az) polar bins
+    fov_deg: float
+    L: int
+    coeffs: np.ndarray     # true per-shell coefficients (N_r, (L+1)^2)
+    weights: np.ndarray    # (n_views, n_rad, n_az): Eq. 9's (g / 4 pi) phi(n)
+    snr_db: float
+    noise_seed: int
+    threshold: float       # density above which the retrieval error is scored
+
+
+def exosphere(shape=(50, 45, 90), n_views=10, bins=(100, 50), fov_deg=18.0, L=3) -> Exosphere:
+    """Synthetic stand-in for the Sec. 6 experiment (the [33] model and the
+    Carruthers ephemeris are not available): a hydrogen exosphere from 3 to
+    25 Earth radii (log-spaced shells) with density 10 (3 / r)^3 in units of
+    1000 atoms/cm^3, times (1 + 0.3 sin(t) cos(p) + 0.1 P_2(cos t)) (a
+    day-night and a polar asymmetry, exact in degree <= 2); 10 views spread
+    evenly over a circle of radius 60 around the sun-Earth line at 235 Earth
+    radii (within 15 deg of the line, a stand-in for the unavailable
+    ephemeris), looking at the Earth, +z up, 18 deg field of view
+    polar-binned to 100 x 50; the
+    known factor (g / 4 pi) phi(n) with g / 4 pi = 1 and a Rayleigh-like
+    phase function 3/4 (1 + cos^2 T), T the angle between the pixel's nominal
+    line of sight and the sun direction +x; 45 dB additive white Gaussian
+    noise; errors scored where the density exceeds 25 atoms/cm^3."""
+    e = synth.grid_edges(*shape)
+    nq = (L + 1) ** 2
+    rc = 0.5 * (e.r[1:] + e.r[:-1])
+    n = 10.0 * (3.0 / rc) ** 3
+    c = np.zeros((shape[0], nq))
+    c[:, 0] = n * 2.0 * np.sqrt(np.pi)                       # 1 = 2 sqrt(pi) Y_00
+    c[:, 3] = 0.3 * n * np.sqrt(4.0 * np.pi / 3.0)           # sin t cos p = sqrt(4 pi / 3) Y_11
+    c[:, 6] = 0.1 * n * np.sqrt(4.0 * np.pi / 5.0)           # P_2(cos t) = sqrt(4 pi / 5) Y_20
+    ang = 2.0 * np.pi * np.arange(n_views) / n_views
+    pos = np.stack([np.full(n_views, 235.0), 60.0 * np.cos(ang), 60.0 * np.sin(ang)], 1)
+    half = 0.5 * np.radians(fov_deg)
+    th = (np.arange(bins[0]) + 0.5) / bins[0] * half
+    ps = 2.0 * np.pi * (np.arange(bins[1]) + 0.5) / bins[1]
+    w = np.zeros((n_views,) + tuple(bins))
+    for v in range(n_views):
+        look = -pos[v] / np.linalg.norm(pos[v])
+        right = np.cross(look, [0.0, 0.0, 1.0])
+        right /= np.linalg.norm(right)
+        up = np.cross(right, look)
+        T, P = np.meshgrid(th, ps, indexing="ij")
+        d = np.cos(T)[..., None] * look + np.sin(T)[..., None] * (np.cos(P)[..., None] * right
+                                                                  + np.sin(P)[..., None] * up)
+        cos_t = d[..., 0]  # sun along +x
+        w[v] = 0.75 * (1.0 + cos_t ** 2)
+    ex = Exosphere()
+    ex.edges, ex.pos, ex.shape, ex.fov_deg, ex.L = e, pos, tuple(bins), fov_deg, L
+    ex.coeffs = c.astype(np.float32)
+    ex.weights = w.astype(np.float32)
+    ex.snr_db, ex.noise_seed, ex.threshold = 45.0, 61, 0.025
+    return ex
