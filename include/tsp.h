@@ -363,6 +363,22 @@ tsp_status tsp_batch_info(tsp_batch batch, int64_t* total_rays, int64_t* total_v
 void tsp_batch_destroy(tsp_batch batch);
 
 /*
+ * tsp_sirt_chunked - SIRT (as tsp_segments_sirt, n_iter iterations from the
+ * x given, flags 0 or TSP_SIRT_NONNEG) over n_items independent
+ * reconstructions (grid, geom, y, x as in tsp_batch_item) from stored lists
+ * whose total exceeds device memory: lists (with the transpose) are built
+ * for a chunk of consecutive items that fits budget_bytes (0: 80% of the
+ * free device memory), every iteration of those items runs from them, and
+ * they are freed before the next chunk (an item whose lists do not fit next
+ * to the chunk starts a new one). Synchronous (the builds read segment
+ * counts back). n_chunks, peak_bytes (either may be NULL) receive the
+ * number of chunks and the largest list memory held at once.
+ * TSP_ENOMEM if one item's lists alone do not fit.
+ */
+tsp_status tsp_sirt_chunked(const tsp_batch_item* items, int n_items, int n_iter, int flags, size_t budget_bytes,
+                            int* n_chunks, size_t* peak_bytes, void* stream);
+
+/*
  * Parametric density model for reconstructions that differentiate through F
  * (Sec. 4.5 Eq. 7 and Listing 8; Sec. 6 Eq. 10 uses spherical harmonics per
  * shell): rho[ir][ie][ia] = sum_j sum_q B[ir][j] c[j][q] Y[ie,ia][q] with B the

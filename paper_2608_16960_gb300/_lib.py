@@ -96,6 +96,7 @@ SIGNATURES = {
     "tsp_vec_dot": (_I, [_P, _P, ctypes.c_int64, _P, _P]),
     "tsp_vec_axpby": (_I, [ctypes.c_float, _P, ctypes.c_float, _P, ctypes.c_int64, _P]),
     "tsp_vec_mul": (_I, [_P, _P, _P, ctypes.c_int64, _P]),
+    "tsp_sirt_chunked": (_I, [_P, _I, _I, _I, ctypes.c_size_t, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t), _P]),
     "tsp_forward_dynamic": (_I, [_P, _P, _P, _P, _P]),
     "tsp_adjoint_dynamic": (_I, [_P, _P, _P, _P, _I, _P]),
     "tsp_sunward_rays": (_I, [_P, ctypes.POINTER(ctypes.c_double), _P, _P, _P]),

@@ -644,10 +644,14 @@ extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int trans
     tsp_segments_destroy(s);
     return r;
   };
-#define SEG_TRY(call)                                     \
-  do {                                                    \
-    cudaError_t e__ = (call);                             \
-    if (e__ != cudaSuccess) return bail(cuda_fail(e__, #call)); \
+#define SEG_TRY(call)                                                                        \
+  do {                                                                                       \
+    cudaError_t e__ = (call);                                                                \
+    if (e__ == cudaErrorMemoryAllocation) {                                                  \
+      cudaGetLastError(); /* not sticky: clear it */                                         \
+      return bail(fail(TSP_ENOMEM, std::string("tsp_segments_build: out of device memory at ") + #call)); \
+    }                                                                                        \
+    if (e__ != cudaSuccess) return bail(cuda_fail(e__, #call));                              \
   } while (0)
   SegList& f = s->fwd;
   f.n_rows = s->n_rays;
@@ -803,4 +807,99 @@ extern "C" tsp_status tsp_segments_sirt(tsp_segments s, const float* y, float* x
   }
   TSP_CUDA(cudaGetLastError());
   return TSP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Chunked segment lists: SIRT over many independent reconstructions whose
+// stored lists together exceed device memory. Lists are built for one chunk
+// of instances at a time (as many, in order, as fit the byte budget), every
+// iteration of those instances runs from the lists, and the chunk's lists
+// are freed before the next chunk is built. Each instance gets the same
+// iterates as tsp_segments_sirt on its own lists.
+// ---------------------------------------------------------------------------
+extern "C" tsp_status tsp_sirt_chunked(const tsp_batch_item* items, int n_items, int n_iter, int flags,
+                                       size_t budget_bytes, int* n_chunks, size_t* peak_bytes, void* stream) {
+  if (!items || n_items <= 0) return fail(TSP_EINVAL, "tsp_sirt_chunked: no items");
+  if (n_iter < 0) return fail(TSP_EINVAL, "tsp_sirt_chunked: n_iter < 0");
+  if (flags & ~TSP_SIRT_NONNEG) return fail(TSP_EINVAL, "tsp_sirt_chunked: unknown flags");
+  for (int i = 0; i < n_items; ++i)
+    if (!items[i].grid || !items[i].geom || !items[i].y || !items[i].x)
+      return fail(TSP_EINVAL, "tsp_sirt_chunked: item " + std::to_string(i) + " has a NULL member");
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  if (budget_bytes == 0) {  // default: 80% of what is free now
+    size_t free_b = 0, total_b = 0;
+    TSP_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    budget_bytes = free_b / 10 * 8;
+  }
+  std::vector<tsp_segments> chunk;
+  size_t used = 0, peak = 0, ws_bytes = 0;
+  void* ws = nullptr;
+  int chunks = 0;
+  auto release = [&]() {
+    for (tsp_segments s : chunk) tsp_segments_destroy(s);
+    chunk.clear();
+    used = 0;
+  };
+  auto run_chunk = [&](int first) -> tsp_status {  // items first .. first + chunk.size() - 1
+    for (size_t k = 0; k < chunk.size(); ++k) {
+      size_t need = 0;
+      tsp_segments_sirt_workspace_bytes(chunk[k], &need);
+      if (need > ws_bytes) {
+        if (ws) cudaFree(ws);
+        ws = nullptr;
+        ws_bytes = 0;
+        cudaError_t e = cudaMalloc(&ws, need);
+        if (e != cudaSuccess) return cuda_fail(e, "tsp_sirt_chunked: workspace");
+        ws_bytes = need;
+      }
+      const tsp_batch_item& it = items[first + int(k)];
+      tsp_status st = tsp_segments_sirt(chunk[k], it.y, it.x, n_iter, flags, ws, ws_bytes, stream);
+      if (st != TSP_OK) return st;
+    }
+    ++chunks;
+    return TSP_OK;
+  };
+  tsp_status st = TSP_OK;
+  int first = 0;
+  for (int i = 0; i < n_items && st == TSP_OK; ++i) {
+    tsp_segments s = nullptr;
+    st = tsp_segments_build(items[i].grid, items[i].geom, 1, &s, stream);
+    if (st == TSP_ENOMEM && !chunk.empty()) {  // no room next to the chunk: finish it, then retry alone
+      st = run_chunk(first);
+      if (st == TSP_OK) {
+        cudaError_t e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) st = cuda_fail(e, "tsp_sirt_chunked: sync");
+      }
+      release();
+      first = i;
+      if (st == TSP_OK) st = tsp_segments_build(items[i].grid, items[i].geom, 1, &s, stream);
+    }
+    if (st != TSP_OK) break;
+    size_t b = 0;
+    tsp_segments_info(s, nullptr, nullptr, &b);
+    if (!chunk.empty() && used + b > budget_bytes) {  // over budget: run the chunk built so far first
+      st = run_chunk(first);
+      if (st == TSP_OK) {
+        cudaError_t e = cudaStreamSynchronize(cs);
+        if (e != cudaSuccess) st = cuda_fail(e, "tsp_sirt_chunked: sync");
+      }
+      release();
+      first = i;
+    }
+    chunk.push_back(s);
+    used += b;
+    peak = std::max(peak, used);
+  }
+  if (st == TSP_OK && !chunk.empty()) {
+    st = run_chunk(first);
+    if (st == TSP_OK) {
+      cudaError_t e = cudaStreamSynchronize(cs);
+      if (e != cudaSuccess) st = cuda_fail(e, "tsp_sirt_chunked: sync");
+    }
+  }
+  release();
+  if (ws) cudaFree(ws);
+  if (n_chunks) *n_chunks = chunks;
+  if (peak_bytes) *peak_bytes = peak;
+  return st;
 }

@@ -356,6 +356,26 @@ class Segments:
             self.handle = None
 
 
+def sirt_chunked(items, n_iter: int, nonneg: bool = False, budget_bytes: int = 0):
+    """SIRT over independent (grid, geom, y, x) items from stored segment
+    lists built one memory-bounded chunk at a time (tsp_sirt_chunked); x is
+    updated in place. Returns (chunks, peak list bytes)."""
+    L = _lib.load()
+    items = list(items)
+    arr = (_lib.tsp_batch_item * len(items))()
+    for i, (grid, geom, y, x) in enumerate(items):
+        _require_cuda(y, "y")
+        _require_cuda(x, "x")
+        if y.numel() != geom.n_rays or x.numel() != grid.voxels:
+            raise ValueError(f"item {i}: y or x has the wrong size")
+        arr[i] = _lib.tsp_batch_item(grid.handle.value, geom.handle.value, y.data_ptr(), x.data_ptr())
+    nc = ctypes.c_int()
+    peak = ctypes.c_size_t()
+    check(L.tsp_sirt_chunked(arr, len(items), n_iter, 1 if nonneg else 0, int(budget_bytes), ctypes.byref(nc),
+                             ctypes.byref(peak), _stream(items[0][2])), "tsp_sirt_chunked")
+    return nc.value, peak.value
+
+
 def tsp_device_status(device_tensor: torch.Tensor | None = None) -> int:
     L = _lib.load()
     code = ctypes.c_int(0)

@@ -230,3 +230,29 @@ def test_list_sirt_follows_traversal_sirt_and_is_reproducible():
     c = torch.zeros(grid.shape, device=DEV)
     tsp_sirt(grid, geom, y, c, 10, nonneg=True, workspace=sirt_workspace(grid, geom))
     assert torch.allclose(a, c, rtol=1e-4, atol=1e-4 * c.abs().max().item())
+
+
+def test_chunked_sirt_matches_oracle_and_respects_the_budget():
+    """Four independent reconstructions with a list budget below their total:
+    the lists are built in several chunks, each item's iterates follow the
+    oracle's SIRT, and no more than the budget (plus one item) is held."""
+    from oracle import sirt as osirt
+    from paper_2608_16960_gb300.projector import sirt_chunked
+    items, refs = [], []
+    for k in range(4):
+        e = synth.grid_edges(8 + 2 * k, 6 + k, 12 + 4 * k)
+        pos = synth.circular_orbit(3 + k, 60.0, incline_deg=10.0 * k, phase=0.3 * k)
+        grid = Grid.from_edges(e)
+        geom = Geometry.cone(pos, (24, 24), 40.0)
+        st, di = oracle.cone_rays(pos, 24, 24, 40.0)
+        rho = synth.blob_phantom(e, seed=500 + k)
+        y = oracle.forward(e, st, di, rho).astype(np.float32)
+        items.append((grid, geom, torch.tensor(y.reshape(geom.det_shape), device=DEV), torch.zeros(grid.shape, device=DEV)))
+        refs.append(osirt.sirt(e, st, di, y, np.zeros(e.shape), 4, nonneg=True))
+    sizes = [Segments(g, m).info()[2] for g, m, _, _ in items]
+    budget = int(sum(sizes) * 0.45)
+    chunks, peak = sirt_chunked(items, 4, nonneg=True, budget_bytes=budget)
+    assert chunks >= 2 and peak <= budget + max(sizes)
+    for (grid, geom, y, x), ref in zip(items, refs):
+        parity(x.cpu().numpy(), ref, what="chunked sirt")
+    assert tsp_device_status() == 0
