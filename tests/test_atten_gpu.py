@@ -171,3 +171,42 @@ def test_paper_scale_sampled():
         assert np.all(err <= 1e-4 * np.maximum(np.abs(ref), 1e-2 * big)), (v.kind, err.max())
         assert np.all(np.isfinite(y)) and np.all(y >= 0)
     assert tsp_device_status() == 0
+
+
+def test_wedge_grid_and_rays_starting_inside():
+    """A wedge (theta in [0.5, 2.6], phi in [0.3, 2.5]) and free-form rays,
+    some starting inside the grid: rays leave and re-enter the wedge, so
+    runs of one voxel are split by gaps; y and the gradients against the
+    oracle."""
+    e = synth.GridEdges(np.geomspace(3.0, 25.0, 9), np.linspace(0.5, 2.6, 7), np.linspace(0.3, 2.5, 10))
+    grid = Grid.from_edges(e)
+    g = synth.SplitMix64(71)
+    n = 600
+    s_out, d_out = synth.random_rays(n // 2, 5, start_radius=60.0, aim_radius=25.0)
+    s_in = (g.uniform(3 * (n // 2), -15.0, 15.0).reshape(3, n // 2)).astype(np.float32)
+    d_in = g.unit_vectors(n // 2).T.astype(np.float32)
+    st = np.concatenate([s_out, s_in], 1).astype(np.float32)
+    di = np.concatenate([d_out, d_in], 1).astype(np.float32)
+    geom = Geometry.rays(torch.tensor(st, device=DEV), torch.tensor(di, device=DEV))
+    rho = (0.2 + synth.uniform_volume(e.shape, 2)).astype(np.float32)
+    sigma = (0.2 + 0.3 * synth.uniform_volume(e.shape, 3)).astype(np.float32)
+    tau1 = (0.5 * synth.uniform_volume(e.shape, 4)).astype(np.float32)
+    t = [torch.tensor(a, device=DEV) for a in (rho, sigma, tau1)]
+    y = atten_forward(grid, geom, *t)
+    st64, di64 = st.T.astype(np.float64), di.T.astype(np.float64)
+    parity(y.cpu().numpy(), atten.forward(e, st64, di64, rho, sigma, tau1), what="wedge attenuated y")
+    gy = g.uniform(n, -1.0, 1.0).astype(np.float32)
+    grads = atten_backward(grid, geom, *t, y, torch.tensor(gy, device=DEV))
+    refs = atten.backward(e, st64, di64, rho, sigma, tau1, gy.astype(np.float64))
+    for name, a, b in zip(("g_rho", "g_sigma", "g_tau1"), grads, refs):
+        grad_parity(a.cpu().numpy(), b, "wedge " + name)
+    assert tsp_device_status() == 0
+
+
+def test_invalid_arguments_are_rejected(case):
+    wl, grid, geom, st, di, rho, sigma, sun = case
+    r = torch.tensor(rho, device=DEV)
+    with pytest.raises(ValueError):
+        atten_forward(grid, geom, r, r[:-1].contiguous(), r)  # sigma of the wrong shape
+    with pytest.raises(Exception):
+        sunward_geometry(grid, (0.0, 0.0, 0.0))  # no sun direction

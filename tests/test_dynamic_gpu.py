@@ -91,3 +91,19 @@ def test_paper_scale_sampled():
             ref = oracle.forward(wl.edges, st[idx], di[idx], rho[k])
             parity(y[k][idx - k * per], ref, what=f"{v.kind} view {k}")
     assert tsp_device_status() == 0
+
+
+def test_dynamic_over_polar_views():
+    """Polar-binned views (Sec. 6) keep their view structure: view k of a
+    polar geometry sees volume k."""
+    from oracle import retrieval as orr
+    e = synth.grid_edges(8, 6, 12)
+    grid = Grid.from_edges(e)
+    pos = np.array([[70.0, 5.0, 3.0], [60.0, -25.0, 15.0], [20.0, 65.0, -10.0]])
+    geom = Geometry.polar(pos, (10, 6), 40.0)
+    rho = np.stack([synth.blob_phantom(e, seed=800 + k) for k in range(3)]).astype(np.float32)
+    y = tsp_forward_dynamic(grid, geom, torch.tensor(rho, device=DEV)).cpu().numpy()
+    st, di = orr.polar_rays(pos, np.zeros((3, 3)), [[0.0, 0.0, 1.0]] * 3, 10, 6, 40.0)
+    ref = oracle.forward_dynamic(e, st, di, rho, 3)
+    for k in range(3):
+        parity(y[k].reshape(-1), ref[k], what=f"polar dynamic view {k}")
