@@ -12,11 +12,10 @@
 // shared-memory slab of the neighbouring rows is the A operand and the three
 // phi taps' weights side by side are B (N = 96), so one MMA computes all three
 // phi taps of a window; the epilogue adds them with a one-row shift each.
-// dgrad is the same kernel with the mirrored, transposed kernel. The weight gradient
-// (M = N = 32 per tap, K = voxels: too narrow for a 128-row tcgen05 tile) uses
-// mma.sync m16n8k16 with ldmatrix.trans on both operands; its shared-memory
-// rows (64 bytes = 32 channels) are XOR-swizzled in 16-byte chunks so that
-// eight consecutive rows hit disjoint banks.
+// dgrad is the same kernel with the mirrored, transposed kernel. The weight
+// gradient (wgrad32_tc_kernel) also runs on tcgen05: K = the voxels, M = four
+// neighbouring (r, theta) rows x 32 input channels, N = 32 output channels,
+// both operands MN-major, accumulated in TMEM over all of a CTA's rows.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -68,10 +67,6 @@ __device__ __forceinline__ int64_t nbr(const Dims& d, int r, int e, int a, int d
   return (int64_t(rr) * d.Ne + ee) * d.Na + aa;
 }
 
-__device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t chunk) {
-  return row * 64u + ((chunk ^ ((row >> 1) & 3u)) << 4);
-}
-
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
@@ -83,24 +78,6 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, uint32_t src_bytes) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
-}
-
-__device__ __forceinline__ void mma16816(float* c, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // ---------------------------------------------------------------------------
@@ -618,106 +595,197 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv32_tc_kernel(const __grid_c
 }
 
 // ---------------------------------------------------------------------------
-// 32 -> 32 weight gradient: dW[tap][co][ci] += sum_v Gz[v][co] H[v + d_tap][ci].
-// 9 warps, warp w owns taps 3w..3w+2; a CTA walks `rows` consecutive phi-rows.
+// 32 -> 32 weight gradient on the tcgen05 tensor cores:
+//   dW[tap][co][ci] = sum_v Gz[v][co] H[v + d_tap][ci],  tap = (dr+1) 9 + (de+1) 3 + (da+1).
+// One stage per output theta-row (b, r, e): the 9 neighbouring H rows
+// (r + dr, e + de) as 36 chunk planes (row j = (dr+1) 3 + (de+1), chunk c:
+// plane 4 j + c) of WG_PS bytes, position p at byte (WG_TB + p) 16 holding
+// azimuth p - 1 (p = 0 and N_a + 1: the periodic halo), then the row's Gz as
+// 4 chunk planes of N_a positions. A = H (M = 128: 4 consecutive rows x 32
+// input channels, MN-major: core matrices along M one plane apart, along K
+// 128 bytes apart; for MN-major the descriptor's leading offset is the K
+// step and its stride offset the M / N step), B = Gz (N = 32 output channels, MN-major), K = 16
+// positions per MMA; the azimuth tap shifts A's start by one position. Row
+// groups start at rows 0, 4 and 5: the third covers row 8, and its blocks for
+// rows 5-7 repeat the second group's and are not read back. Nine TMEM tiles
+// of 32 columns (group x azimuth tap) accumulate over every row the CTA
+// processes; at the end the epilogue writes the CTA's partial dW, which
+// part_reduce_kernel sums in a fixed order.
 // ---------------------------------------------------------------------------
-template <int NA>
-__global__ void __launch_bounds__(288) wgrad32_kernel(Dims d, const bf16* __restrict__ Gz, const bf16* __restrict__ H,
-                                                      float* __restrict__ dW, int rows_per_cta) {
+constexpr int WG_TB = 7;  // position 1 of a plane starts 128-byte aligned (TMA destination)
+__host__ __device__ inline int wg_ps(int Na) { return ((WG_TB + Na + 2) * 16 + 127) / 128 * 128; }
+__host__ __device__ inline int wg_stage(int Na) { return 36 * wg_ps(Na) + 4 * Na * 16; }
+// stages in flight (up to 3; each has its own loader warp, warps 1..3)
+__host__ __device__ inline int wg_stages(int Na) {
+  return 3 * wg_stage(Na) + 2048 <= 232448 ? 3 : (2 * wg_stage(Na) + 2048 <= 232448 ? 2 : 1);
+}
+__host__ __device__ inline int wg_gstart(int g) { return g == 0 ? 0 : (g == 1 ? 4 : 5); }
+// Dynamic shared memory of a launch: the stages, at least 116 KB so that one
+// CTA (which allocates all 512 TMEM columns) holds a multiprocessor.
+inline int wg_smem(int Na) { return std::max(wg_stages(Na) * wg_stage(Na), 116 * 1024); }
+// kind::f16: f32 accumulator, bf16 A and B, both MN-major, N = 32, M = 128.
+constexpr uint32_t WG_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((32u >> 3) << 17) |
+                              ((128u >> 4) << 24);
+
+__device__ __forceinline__ void wg_mma_elect(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p, e;\n elect.sync _|e, 0xffffffff;\n setp.ne.u32 p, %4, 0;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(WG_IDESC), "r"(accumulate)
+      : "memory");
+}
+
+// Load the stage of output row (b, r, e) (one warp): lane 0 registers the
+// bytes, the lanes issue the 40 TMA boxes (zeros outside the grid) and copy
+// the 72 halo chunks with cp.async (zero-filled outside the grid), then arrive.
+__device__ __forceinline__ void wg_load_stage(const CUtensorMap* hmap, const CUtensorMap* gmap, const Dims& d,
+                                              const bf16* __restrict__ H, int b, int r, int e, unsigned char* buf,
+                                              int PS, uint64_t* bar, int lane) {
+  const int Na = d.Na;
+  if (lane == 0) mbar_expect_tx(bar, uint32_t(40 * Na * 16));
+  __syncwarp();
+  for (int t = lane; t < 40; t += 32) {  // boxes issued from all lanes: 36 of H, 4 of Gz
+    const int j = t >> 2, c = t & 3;
+    if (j < 9)
+      tma_load_5d(buf + size_t(t) * PS + (WG_TB + 1) * 16, hmap, 8 * c, 0, e + j % 3 - 1, r + j / 3 - 1, b, bar);
+    else
+      tma_load_5d(buf + size_t(36) * PS + size_t(c) * Na * 16, gmap, 8 * c, 0, e, r, b, bar);
+  }
+  for (int i = lane; i < 72; i += 32) {
+    const int c = i & 3, side = (i >> 2) & 1, j = i >> 3;
+    const int rr = r + j / 3 - 1, ee = e + j % 3 - 1;
+    const bool ok = rr >= 0 && rr < d.Nr && ee >= 0 && ee < d.Ne;
+    const int aa = side == 0 ? Na - 1 : 0;
+    const bf16* src = ok ? H + (((size_t(b) * d.Nr + rr) * d.Ne + ee) * Na + aa) * CH + c * 8 : H;
+    cp_async16_zfill(buf + size_t(4 * j + c) * PS + size_t(WG_TB + (side == 0 ? 0 : Na + 1)) * 16, src, ok ? 16u : 0u);
+  }
+  cp_async_wait_all();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // halo copies -> tensor-core reads
+  mbar_arrive(bar);
+}
+
+// AND of p over the 128 epilogue threads of wgrad32_tc_kernel (named barrier 2).
+__device__ __forceinline__ bool wg_epilogue_and(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.and.pred po, 2, 128, pi;\n selp.u32 %0, 1, 0, po;\n}"
+      : "=r"(r)
+      : "r"(uint32_t(p))
+      : "memory");
+  return r != 0;
+}
+
+// Warp 0 issues the MMAs, warps 1..NS each load one stage slot (their global
+// halo copies wait in parallel), warps 4-7 read the accumulators back at the
+// end. part: [gridDim.x][27][32][32].
+__global__ void __launch_bounds__(256, 1) wgrad32_tc_kernel(const __grid_constant__ CUtensorMap hmap,
+                                                            const __grid_constant__ CUtensorMap gmap, Dims d,
+                                                            const bf16* __restrict__ H, float* __restrict__ part) {
   extern __shared__ __align__(128) unsigned char smem[];
-  constexpr int cols = NA + 2;
-  unsigned char* s_h = smem;                         // 9 rows x cols
-  unsigned char* s_g = smem + size_t(9) * cols * 64;  // NA rows
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mat = lane >> 3, rr8 = lane & 7;
-  float acc[3][2][4][4];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[a][i][j][k] = 0.0f;
-  const uint32_t sh = static_cast<uint32_t>(__cvta_generic_to_shared(s_h));
-  const uint32_t sg = static_cast<uint32_t>(__cvta_generic_to_shared(s_g));
-  const int64_t total_rows = int64_t(d.B) * d.Nr * d.Ne;
-  const int64_t row0 = int64_t(blockIdx.x) * rows_per_cta;
-  for (int64_t R = row0; R < row0 + rows_per_cta && R < total_rows; ++R) {
-    const int b = int(R / (int64_t(d.Nr) * d.Ne));
-    const int r = int((R / d.Ne) % d.Nr), e = int(R % d.Ne);
-    const bf16* Hb = H + size_t(b) * d.V * CH;
-    const bf16* Gb = Gz + size_t(b) * d.V * CH;
-    __syncthreads();  // previous row's operands are no longer read
-    for (int i = threadIdx.x; i < 9 * cols * 4; i += blockDim.x) {
-      const int cell = i >> 2, ch = i & 3;
-      const int c = cell % cols, j = cell / cols;
-      const int rr = r + j / 3 - 1, ee = e + j % 3 - 1;
-      unsigned char* dst = s_h + swz(cell, ch);
-      if (rr < 0 || rr >= d.Nr || ee < 0 || ee >= d.Ne) {
-        *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
-      } else {
-        int aa = c - 1;
-        aa = aa < 0 ? aa + NA : (aa >= NA ? aa - NA : aa);
-        cp_async16(dst, Hb + ((int64_t(rr) * d.Ne + ee) * NA + aa) * CH + ch * 8);
-      }
+  // full[s]: stage s loaded (32 loader arrivals + TMA bytes); empty[s]: its MMAs done (commit);
+  // done: every MMA of the CTA done (commit)
+  __shared__ __align__(8) uint64_t full[3], empty[3], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int s_abort;
+  const int Na = d.Na, PS = wg_ps(Na), ST = wg_stage(Na), NS = wg_stages(Na);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t rows = int64_t(d.B) * d.Nr * d.Ne;
+  if (smem_u32(smem) & 127u) {  // TMA boxes need 128-byte aligned destinations: report, touch nothing
+    if (tid == 0) atomicOr(&g_conv_error_word, 2);
+    return;
+  }
+  if (tid == 0) {
+    s_abort = 0;
+    for (int k = 0; k < 3; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 32;" ::"r"(smem_u32(&full[k])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[k])) : "memory");
     }
-    const int64_t gbase = (int64_t(r) * d.Ne + e) * NA;
-    for (int i = threadIdx.x; i < NA * 4; i += blockDim.x) {
-      const int v = i >> 2, ch = i & 3;
-      cp_async16(s_g + swz(v, ch), Gb + (gbase + v) * CH + ch * 8);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-#pragma unroll 1
-    for (int k0 = 0; k0 < NA; k0 += 16) {
-      // A = Gz^T (co x v): two m16 tiles (co 0-15, 16-31)
-      uint32_t a[2][4];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const uint32_t v = k0 + rr8 + 8 * (mat >> 1);
-        ldsm_x4_t(sg + swz(v, 2 * mt + (mat & 1)), a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const bool any = int64_t(blockIdx.x) < rows;
+
+  if (warp == 0) {  // ---- MMA issuer ----
+    bool go = true;
+    uint32_t started = 0;
+    int i = 0;
+    for (int64_t row = blockIdx.x; row < rows && go; row += gridDim.x, ++i) {
+      const int slot = i % NS;
+      if (!__all_sync(0xffffffffu, tc_wait(&full[slot], uint32_t(i / NS) & 1u, &s_abort))) {
+        go = false;
+        break;
       }
-#pragma unroll
-      for (int tt = 0; tt < 3; ++tt) {
-        const int tap = warp * 3 + tt;
-        const int dri = tap / 9, dei = (tap / 3) % 3, dai = tap % 3;
-        const int hrow = (dri * 3 + dei) * cols + dai;  // slab column = phi + dai
-        uint32_t bfr[4][2];
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-          // B (v x ci) for n-tiles 2p, 2p+1: rows v, chunks 2p + (mat >> 1)
-          const uint32_t v = hrow + k0 + rr8 + 8 * (mat & 1);
-          uint32_t q0, q1, q2, q3;
-          ldsm_x4_t(sh + swz(v, 2 * p + (mat >> 1)), q0, q1, q2, q3);
-          bfr[2 * p][0] = q0;
-          bfr[2 * p][1] = q1;
-          bfr[2 * p + 1][0] = q2;
-          bfr[2 * p + 1][1] = q3;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(smem + size_t(slot) * ST), b0 = a0 + uint32_t(36 * PS);
+      for (int g = 0; g < 3; ++g) {
+        for (int dp = 0; dp < 3; ++dp) {
+          const uint32_t dt = tmem + uint32_t(g * 3 + dp) * 32;
+          for (int k = 0; k < Na / 16; ++k) {
+            // MN-major, no swizzle: leading offset = between core matrices along K (128 bytes),
+            // stride offset = between core matrices along M / N (one chunk plane)
+            const uint64_t ad =
+                umma_desc(a0 + uint32_t(4 * wg_gstart(g) * PS + (WG_TB + 16 * k + dp) * 16), 128, uint32_t(PS));
+            const uint64_t bd = umma_desc(b0 + uint32_t(16 * k * 16), 128, uint32_t(Na * 16));
+            wg_mma_elect(dt, ad, bd, started | uint32_t(k));
+          }
         }
+      }
+      started = 1;
+      tc_commit_elect(&empty[slot]);
+      __syncwarp();
+    }
+    if (go) {
+      tc_commit_elect(&done);
+    } else if (lane == 0) {  // let issued MMAs land before TMEM is released
+      const long long t0 = clock64();
+      while (clock64() - t0 < TC_WAIT_BUDGET / 8) {
+      }
+    }
+    __syncwarp();
+  } else if (warp >= 1 && warp <= NS) {  // ---- stage loaders: warp w fills slot w - 1 ----
+    const int slot = warp - 1;
+    int i = slot;
+    for (int64_t row = blockIdx.x + int64_t(slot) * gridDim.x; row < rows; row += int64_t(NS) * gridDim.x, i += NS) {
+      if (i >= NS && !__all_sync(0xffffffffu, tc_wait(&empty[slot], uint32_t(i / NS - 1) & 1u, &s_abort))) break;
+      const int e = int(row % d.Ne), r = int((row / d.Ne) % d.Nr), b = int(row / (int64_t(d.Ne) * d.Nr));
+      wg_load_stage(&hmap, &gmap, d, H, b, r, e, smem + size_t(slot) * ST, PS, &full[slot], lane);
+    }
+  } else if (warp >= 4) {  // ---- epilogue: the CTA's partial dW ----
+    const int q = warp & 3;
+    float* out = part + size_t(blockIdx.x) * 27 * CH * CH;
+    const bool ok = wg_epilogue_and(!any || tc_wait(&done, 0u, &s_abort));
+    if (ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int t = 0; t < 9; ++t) {
+        const int g = t / 3, dp = t % 3;
+        if (g == 2 && q < 3) continue;  // rows 5-7 again
+        const int tap = 3 * (wg_gstart(g) + q) + dp;
+        uint32_t v[16];
+        for (int h = 0; h < 2; ++h) {  // output channels 16 h .. 16 h + 15 of input channel ci = lane
+          if (any) {
+            tmem_ld_nowait<16>(tmem + (uint32_t(32 * q) << 16) + uint32_t(t * 32 + 16 * h), v);
+            tmem_wait();
+          }
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-          for (int nt = 0; nt < 4; ++nt) mma16816(acc[tt][mt][nt], a[mt], bfr[nt][0], bfr[nt][1]);
+          for (int j = 0; j < 16; ++j) out[(size_t(tap) * CH + 16 * h + j) * CH + lane] = any ? __uint_as_float(v[j]) : 0.0f;
+        }
       }
     }
   }
-  const int g = lane >> 2, t = lane & 3;
-#pragma unroll
-  for (int tt = 0; tt < 3; ++tt) {
-    const int tap = warp * 3 + tt;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int co = mt * 16 + g, ci = nt * 8 + 2 * t;
-        float* base = dW + (size_t(tap) * CH + co) * CH + ci;
-        atomicAdd(base, acc[tt][mt][nt][0]);
-        atomicAdd(base + 1, acc[tt][mt][nt][1]);
-        atomicAdd(base + 8 * CH, acc[tt][mt][nt][2]);
-        atomicAdd(base + 8 * CH + 1, acc[tt][mt][nt][3]);
-      }
-  }
+  __syncthreads();
+  if (tid == 0 && s_abort) atomicOr(&g_conv_error_word, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -1105,6 +1173,7 @@ struct tsp_net_s {
   double* loss = nullptr;
   float* part = nullptr;  // per-CTA partial sums of the weight / bias gradient reductions
   int part_rows = 0;
+  float* wpart = nullptr;  // per-CTA partial 32 -> 32 weight gradients [SMs][27][32][32]
   std::vector<void*> allocs;
   int adam_step = 0;
   CUtensorMap map_h[5];  // TMA descriptors of the activations h1..h5 (inputs of the 32 -> 32 layers)
@@ -1113,7 +1182,6 @@ struct tsp_net_s {
 
 namespace {
 
-size_t wgrad_smem(int Na) { return size_t(9 * (Na + 2)) * 64 + size_t(Na) * 64; }
 
 // TMA descriptor of a bf16 activation tensor [B][N_r][N_e][N_a][32]: a 5-D
 // tiled map (channels innermost) whose box is 8 channels x N_a azimuths, i.e.
@@ -1150,16 +1218,34 @@ tsp_status net_alloc(tsp_net n, T** p, size_t count) {
 
 int g_sm_count = 152;  // multiprocessors of the device the network lives on (set at creation)
 
+// Allow f the most dynamic shared memory a block may have on this device
+// (the opt-in limit less f's static shared memory). The attribute belongs to
+// the function, not to a net, so it is set to the largest value once instead
+// of to one net's need (nets of several azimuth counts may coexist).
+template <class F>
+tsp_status allow_max_smem(F* f, int dev) {
+  int optin = 0;
+  TSP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa{};
+  TSP_CUDA(cudaFuncGetAttributes(&fa, f));
+  TSP_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - int(fa.sharedSizeBytes)));
+  return TSP_OK;
+}
+
 tsp_status set_attrs(int Na) {
-  const int sm = int(tc_plan(Na).smem);
-  TSP_CUDA(cudaFuncSetAttribute(conv32_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  TSP_CUDA(cudaFuncSetAttribute(conv32_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   int dev = 0;
   TSP_CUDA(cudaGetDevice(&dev));
   TSP_CUDA(cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev));
-  TSP_CUDA(cudaFuncSetAttribute(thin_wgrad_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(thin_smem(Na))));
-  TSP_CUDA(cudaFuncSetAttribute(thin_wgrad_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(thin_smem(Na))));
-  return TSP_OK;
+  int optin = 0;
+  TSP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (int(tc_plan(Na).smem) + 4096 > optin || wg_smem(Na) + 4096 > optin || int(thin_smem(Na)) + 32768 > optin)
+    return fail(TSP_ENOTSUP, "tsp_net_create: the azimuth count needs more shared memory than a block may have");
+  tsp_status st = allow_max_smem(conv32_tc_kernel<0>, dev);
+  if (st == TSP_OK) st = allow_max_smem(conv32_tc_kernel<1>, dev);
+  if (st == TSP_OK) st = allow_max_smem(wgrad32_tc_kernel, dev);
+  if (st == TSP_OK) st = allow_max_smem(thin_wgrad_kernel<0>, dev);
+  if (st == TSP_OK) st = allow_max_smem(thin_wgrad_kernel<1>, dev);
+  return st;
 }
 
 // Persistent launch: work items (sample, chunk, run of rseg shells), about
@@ -1177,35 +1263,6 @@ void conv32(int mode, const Dims& d, int B, const CUtensorMap& xmap, const bf16*
   const unsigned grid = unsigned(std::min<int64_t>(items, g_sm_count));
   if (mode == 0) conv32_tc_kernel<0><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
   else conv32_tc_kernel<1><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
-}
-
-template <int NA>
-void launch_wgrad(const Dims& d, int B, const bf16* Gz, const bf16* H, float* dW, cudaStream_t st) {
-  Dims db = d;
-  db.B = B;
-  const int64_t rows = int64_t(B) * d.Nr * d.Ne;
-  const int rows_per = int(std::max<int64_t>(1, (rows + 4 * 152 - 1) / (4 * 152)));
-  const int grid = int((rows + rows_per - 1) / rows_per);
-  wgrad32_kernel<NA><<<grid, 288, wgrad_smem(NA), st>>>(db, Gz, H, dW, rows_per);
-}
-
-tsp_status wgrad32(const Dims& d, int B, const bf16* Gz, const bf16* H, float* dW, cudaStream_t st) {
-  switch (d.Na) {
-    case 32: launch_wgrad<32>(d, B, Gz, H, dW, st); break;
-    case 64: launch_wgrad<64>(d, B, Gz, H, dW, st); break;
-    case 96: launch_wgrad<96>(d, B, Gz, H, dW, st); break;
-    case 128: launch_wgrad<128>(d, B, Gz, H, dW, st); break;
-    case 160: launch_wgrad<160>(d, B, Gz, H, dW, st); break;
-    case 192: launch_wgrad<192>(d, B, Gz, H, dW, st); break;
-    default: return fail(TSP_ENOTSUP, "wgrad: azimuth count must be a multiple of 32 up to 192");
-  }
-  return TSP_OK;
-}
-
-template <int NA>
-tsp_status wgrad_attr() {
-  TSP_CUDA(cudaFuncSetAttribute(wgrad32_kernel<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(wgrad_smem(NA))));
-  return TSP_OK;
 }
 
 tsp_status prepare_weights(tsp_net n, cudaStream_t st) {
@@ -1285,19 +1342,10 @@ extern "C" tsp_status tsp_net_create(int n_r, int n_e, int n_a, int max_batch, t
   if (st == TSP_OK) {  // one row per CTA of the reductions (2 per multiprocessor, THIN_OUT floats)
     n->part_rows = 2 * g_sm_count;
     st = net_alloc(n, &n->part, size_t(n->part_rows) * THIN_OUT);
+    if (st == TSP_OK) st = net_alloc(n, &n->wpart, size_t(g_sm_count) * 27 * CH * CH);
   }
   for (int k = 0; k < 5 && st == TSP_OK; ++k) st = encode_act_map(&n->map_h[k], n->h[k], n->d);
   if (st == TSP_OK) st = encode_act_map(&n->map_gz, n->gz, n->d);
-  if (st == TSP_OK) {
-    switch (n_a) {
-      case 32: st = wgrad_attr<32>(); break;
-      case 64: st = wgrad_attr<64>(); break;
-      case 96: st = wgrad_attr<96>(); break;
-      case 128: st = wgrad_attr<128>(); break;
-      case 160: st = wgrad_attr<160>(); break;
-      default: st = wgrad_attr<192>(); break;
-    }
-  }
   if (st == TSP_OK) {
     cudaError_t e = cudaMemset(n->params, 0, sizeof(float) * off);
     if (e == cudaSuccess) e = cudaMemset(n->m, 0, sizeof(float) * off);
@@ -1357,6 +1405,18 @@ extern "C" tsp_status tsp_net_forward(tsp_net n, const float* a, int batch, floa
 }
 
 namespace {
+// dW (27 x 32 x 32, added) of 32 -> 32 layer k + 1 from its input h[k] and
+// the gated gradient gz: the tcgen05 kernel's per-CTA partials, then their
+// fixed-order sum.
+void wgrad32_tc(tsp_net n, int k, int batch, float* dW, cudaStream_t cs) {
+  Dims db = n->d;
+  db.B = batch;
+  const int64_t rows = int64_t(batch) * db.Nr * db.Ne;
+  const int grid = int(std::min<int64_t>(rows, g_sm_count));
+  wgrad32_tc_kernel<<<grid, 256, wg_smem(db.Na), cs>>>(n->map_h[k], n->map_gz, db, n->h[k], n->wpart);
+  part_reduce_kernel<<<27 * CH * CH / 32, 1024, 0, cs>>>(n->wpart, grid, 27 * CH * CH, 27 * CH * CH, dW);
+}
+
 // Weight and bias gradient of a one-sided layer (mode 0: output layer from
 // g_out and h5; mode 1: input layer from the gated g_h and a): per-CTA
 // partial sums, then a fixed-order reduction added to dw (27 x 32) and db (nb).
@@ -1398,7 +1458,7 @@ extern "C" tsp_status tsp_net_loss_grad(tsp_net n, const float* a, const float* 
   for (int k = 3; k >= 0; --k) {
     gate_kernel<<<ggrid, 256, 0, cs>>>(n->gh, n->mask[k + 1], n->gz, nv, n->part);
     part_reduce_kernel<<<1, 1024, 0, cs>>>(n->part, ggrid, CH, CH, n->grads + n->off_b[k + 1]);
-    st = wgrad32(d, batch, n->gz, n->h[k], n->grads + n->off_w[k + 1], cs);
+    wgrad32_tc(n, k, batch, n->grads + n->off_w[k + 1], cs);
     if (st != TSP_OK) return st;
     conv32(1, d, batch, n->map_gz, n->gz, n->wd[k], nullptr, nullptr, nullptr, n->gh, cs);
   }
