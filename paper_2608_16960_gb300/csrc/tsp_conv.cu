@@ -83,7 +83,9 @@ __device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, u
 // ---------------------------------------------------------------------------
 // 32 -> 32 implicit GEMM on the 5th-generation tensor cores (tcgen05, TMEM).
 // MODE 0 forward (bias, ReLU, residual, mask, bf16 out), MODE 1 dgrad
-// (accumulate into float32 G).
+// (accumulate into float32 G), MODE 2 the 32 -> 1 output layer (weights in
+// output channel 0, the others zero; out = a + z_0 + b into float32 G, with
+// the one-channel input a passed as Y).
 //
 // Output positions of one shell are flattened with the two periodic halo
 // columns of every theta-row, o = e * (N_a + 2) + p, p = 1..N_a the azimuth
@@ -258,6 +260,7 @@ template <int MODE>
 struct EpiIn {
   uint4 x[2][TC_ECH / 8];   // forward: residual, this warp's channels of each tile's row
   float4 g[2][TC_ECH / 4];  // dgrad: G, this warp's channels of each tile's row
+  float a[2];               // output layer: the network input a at each tile's row
 };
 template <int MODE, int T>
 __device__ __forceinline__ void tc_epilogue_fetch(size_t roff, const size_t (&vb)[2], const bool (&valid)[2],
@@ -271,6 +274,8 @@ __device__ __forceinline__ void tc_epilogue_fetch(size_t roff, const size_t (&vb
       const uint4* xr = reinterpret_cast<const uint4*>(Xres + vox * CH + c0);
 #pragma unroll
       for (int h = 0; h < TC_ECH / 8; ++h) in.x[t][h] = valid[t] ? xr[h] : make_uint4(0, 0, 0, 0);
+    } else if (MODE == 2) {  // Xres: the one-channel input a
+      in.a[t] = valid[t] && hf == 0 ? __bfloat162float(Xres[vox]) : 0.0f;
     } else {
       const float4* gp = reinterpret_cast<const float4*>(G + vox * CH + c0);
 #pragma unroll
@@ -325,6 +330,8 @@ __device__ __forceinline__ void tc_epilogue(size_t roff, const size_t (&vb)[2], 
     if (MODE == 0) {
 #pragma unroll
       for (int h = 0; h < TC_ECH / 8; ++h) pin(in.x[t][h]);
+    } else if (MODE == 2) {
+      asm volatile("" : "+f"(in.a[t]));
     } else {
 #pragma unroll
       for (int h = 0; h < TC_ECH / 4; ++h) pin(in.g[t][h]);
@@ -351,6 +358,8 @@ __device__ __forceinline__ void tc_epilogue(size_t roff, const size_t (&vb)[2], 
       // the mask word's 16-bit half for these channels (little-endian words)
       if (TC_ECH == 16) reinterpret_cast<uint16_t*>(mask)[2 * vox + hf] = uint16_t(bits);
       else reinterpret_cast<uint8_t*>(mask)[4 * vox + hf] = uint8_t(bits);
+    } else if (MODE == 2) {  // output layer (32 -> 1, output channel 0): out = a + z_0 + b
+      if (hf == 0) G[vox] = in.a[t] + (acc[0] + bz[0]);
     } else {
       float4* gp = reinterpret_cast<float4*>(G + vox * CH + c0);
 #pragma unroll
@@ -550,7 +559,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv32_tc_kernel(const __grid_c
     const size_t plane = size_t(d.Ne) * d.Na;
     float bz[TC_ECH];
 #pragma unroll
-    for (int c = 0; c < TC_ECH; ++c) bz[c] = MODE == 0 ? bias[TC_ECH * hf + c] : 0.0f;
+    for (int c = 0; c < TC_ECH; ++c)  // mode 2 has one bias value (output channel 0)
+      bz[c] = MODE == 0 ? bias[TC_ECH * hf + c] : (MODE == 2 && hf == 0 && c == 0 ? bias[0] : 0.0f);
     int K = 0, kb = 0;
     uint32_t kph = 0;
     bool go = true;
@@ -570,8 +580,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv32_tc_kernel(const __grid_c
       for (int i = 0; i < n; ++i, ++K) {
         const size_t roff = size_t(r0 + i) * plane;
         EpiIn<MODE> in;
-        if (T == 2) tc_epilogue_fetch<MODE, 2>(roff, vb, vv, X, G, hf, in);
-        else tc_epilogue_fetch<MODE, 1>(roff, vb, vv, X, G, hf, in);
+        const bf16* xres = MODE == 2 ? Y : X;  // mode 2: Y carries the input a
+        if (T == 2) tc_epilogue_fetch<MODE, 2>(roff, vb, vv, xres, G, hf, in);
+        else tc_epilogue_fetch<MODE, 1>(roff, vb, vv, xres, G, hf, in);
         const bool ok = epilogue_and(tc_wait(&tfull[kb], kph, &s_abort));
         if (!ok) {
           go = false;
@@ -808,6 +819,15 @@ __global__ void prep_weights_kernel(const float* __restrict__ w, bf16* __restric
   wd[(size_t(26 - tap) * CH + ci) * CH + co] = v;
 }
 
+// Output layer weights w6 [27][32] in the 32 -> 32 layout [27][co][ci]:
+// output channel 0 holds them, the other 31 are zero.
+__global__ void pad_w6_kernel(const float* __restrict__ w6, bf16* __restrict__ wf6) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 27 * CH * CH) return;
+  const int tap = i / (CH * CH), co = (i / CH) % CH, ci = i % CH;
+  wf6[i] = __float2bfloat16_rn(co == 0 ? w6[tap * CH + ci] : 0.0f);
+}
+
 __global__ void round_bf16_kernel(const float* __restrict__ w, float* __restrict__ out, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = __bfloat162float(__float2bfloat16_rn(w[i]));
@@ -851,38 +871,6 @@ __global__ void conv_in_fwd_kernel(Dims d, const bf16* __restrict__ a, const flo
 #pragma unroll
   for (int j = 0; j < 4; ++j) dst[j] = src[j];
   mask[gi] = bits;
-}
-
-// out = a + b6 + conv(h5; w6)
-__global__ void conv_out_fwd_kernel(Dims d, const bf16* __restrict__ h, const float* __restrict__ w6r,
-                                    const float* __restrict__ b6p, const bf16* __restrict__ a, float* __restrict__ out) {
-  __shared__ float sw[27 * CH];
-  for (int i = threadIdx.x; i < 27 * CH; i += blockDim.x) sw[i] = w6r[i];
-  __syncthreads();
-  const int64_t gi = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (gi >= int64_t(d.B) * d.V) return;
-  const int b = int(gi / d.V);
-  const int64_t v = gi - int64_t(b) * d.V;
-  const int a_ = int(v % d.Na), e = int((v / d.Na) % d.Ne), r = int(v / (int64_t(d.Na) * d.Ne));
-  float acc = __ldg(b6p);
-#pragma unroll 1
-  for (int tap = 0; tap < 27; ++tap) {
-    const int64_t q = nbr(d, r, e, a_, tap / 9 - 1, (tap / 3) % 3 - 1, tap % 3 - 1);
-    if (q < 0) continue;
-    const uint4* src = reinterpret_cast<const uint4*>(h + (int64_t(b) * d.V + q) * CH);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint4 u = __ldg(src + j);
-      const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&u);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float2 f = __bfloat1622float2(p[k]);
-        acc = fmaf(sw[tap * CH + j * 8 + 2 * k], f.x, acc);
-        acc = fmaf(sw[tap * CH + j * 8 + 2 * k + 1], f.y, acc);
-      }
-    }
-  }
-  out[gi] = __bfloat162float(a[gi]) + acc;
 }
 
 // g_out = 2 (out - target) / n; loss += sum (out - target)^2 / n (double).
@@ -1165,6 +1153,7 @@ struct tsp_net_s {
   float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
   bf16 *wf[4] = {nullptr, nullptr, nullptr, nullptr}, *wd[4] = {nullptr, nullptr, nullptr, nullptr};
   float *w1r = nullptr, *w6r = nullptr;
+  bf16* wf6 = nullptr;  // output layer weights in the 32 -> 32 layout (tensor-core forward)
   bf16* a16 = nullptr;
   bf16* h[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   uint32_t* mask[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -1242,6 +1231,7 @@ tsp_status set_attrs(int Na) {
     return fail(TSP_ENOTSUP, "tsp_net_create: the azimuth count needs more shared memory than a block may have");
   tsp_status st = allow_max_smem(conv32_tc_kernel<0>, dev);
   if (st == TSP_OK) st = allow_max_smem(conv32_tc_kernel<1>, dev);
+  if (st == TSP_OK) st = allow_max_smem(conv32_tc_kernel<2>, dev);
   if (st == TSP_OK) st = allow_max_smem(wgrad32_tc_kernel, dev);
   if (st == TSP_OK) st = allow_max_smem(thin_wgrad_kernel<0>, dev);
   if (st == TSP_OK) st = allow_max_smem(thin_wgrad_kernel<1>, dev);
@@ -1262,7 +1252,8 @@ void conv32(int mode, const Dims& d, int B, const CUtensorMap& xmap, const bf16*
   const int64_t items = int64_t(B) * nq * ((d.Nr + rseg - 1) / rseg);
   const unsigned grid = unsigned(std::min<int64_t>(items, g_sm_count));
   if (mode == 0) conv32_tc_kernel<0><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
-  else conv32_tc_kernel<1><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
+  else if (mode == 1) conv32_tc_kernel<1><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
+  else conv32_tc_kernel<2><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
 }
 
 tsp_status prepare_weights(tsp_net n, cudaStream_t st) {
@@ -1270,6 +1261,7 @@ tsp_status prepare_weights(tsp_net n, cudaStream_t st) {
     prep_weights_kernel<<<(27 * CH * CH + 255) / 256, 256, 0, st>>>(n->params + n->off_w[k + 1], n->wf[k], n->wd[k]);
   round_bf16_kernel<<<(27 * CH + 255) / 256, 256, 0, st>>>(n->params + n->off_w[0], n->w1r, 27 * CH);
   round_bf16_kernel<<<(27 * CH + 255) / 256, 256, 0, st>>>(n->params + n->off_w[5], n->w6r, 27 * CH);
+  pad_w6_kernel<<<(27 * CH * CH + 255) / 256, 256, 0, st>>>(n->params + n->off_w[5], n->wf6);
   TSP_CUDA(cudaGetLastError());
   return TSP_OK;
 }
@@ -1287,8 +1279,7 @@ tsp_status net_forward(tsp_net n, const float* a, int B, cudaStream_t st) {
   for (int k = 0; k < 4; ++k)
     conv32(0, d, B, n->map_h[k], n->h[k], n->wf[k], n->params + n->off_b[k + 1], n->h[k + 1], n->mask[k + 1], nullptr,
            st);
-  conv_out_fwd_kernel<<<blocks_for(nv, 128), 128, 0, st>>>(db, n->h[4], n->w6r, n->params + n->off_b[5], n->a16,
-                                                           n->out);
+  conv32(2, d, B, n->map_h[4], n->h[4], n->wf6, n->params + n->off_b[5], n->a16, nullptr, n->out, st);
   TSP_CUDA(cudaGetLastError());
   return TSP_OK;
 }
@@ -1328,6 +1319,7 @@ extern "C" tsp_status tsp_net_create(int n_r, int n_e, int n_a, int max_batch, t
   }
   if (st == TSP_OK) st = net_alloc(n, &n->w1r, 27 * CH);
   if (st == TSP_OK) st = net_alloc(n, &n->w6r, 27 * CH);
+  if (st == TSP_OK) st = net_alloc(n, &n->wf6, 27 * CH * CH);
   if (st == TSP_OK) st = net_alloc(n, &n->a16, nv);
   for (int k = 0; k < 5 && st == TSP_OK; ++k) {
     st = net_alloc(n, &n->h[k], nv * CH);
