@@ -4,7 +4,7 @@
 //
 //   h1 = relu(conv(a; w1) + b1)                   1 -> 32   CUDA cores
 //   h_k = h_{k-1} + relu(conv(h_{k-1}; wk) + bk)  32 -> 32  tensor cores (k = 2..5)
-//   out = a + conv(h5; w6) + b6                   32 -> 1   CUDA cores
+//   out = a + conv(h5; w6) + b6                   32 -> 1   tensor cores (forward; dgrad on CUDA cores)
 //
 // The 32 -> 32 layers are implicit GEMMs (M = voxels, N = 32, K = 27 taps x 32).
 // Forward and dgrad run on the tcgen05 tensor cores with TMEM accumulators
