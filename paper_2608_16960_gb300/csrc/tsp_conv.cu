@@ -1165,6 +1165,7 @@ struct tsp_net_s {
   float* wpart = nullptr;  // per-CTA partial 32 -> 32 weight gradients [SMs][27][32][32]
   std::vector<void*> allocs;
   int adam_step = 0;
+  bool prepared = false;  // wf / wd / w1r / w6r / wf6 hold the current parameters
   CUtensorMap map_h[5];  // TMA descriptors of the activations h1..h5 (inputs of the 32 -> 32 layers)
   CUtensorMap map_gz;    // and of the gated gradient (input of dgrad)
 };
@@ -1271,8 +1272,11 @@ tsp_status net_forward(tsp_net n, const float* a, int B, cudaStream_t st) {
   Dims db = d;
   db.B = B;
   const int64_t nv = int64_t(B) * d.V;
-  tsp_status s = prepare_weights(n, st);
-  if (s != TSP_OK) return s;
+  if (!n->prepared) {  // the bf16 / rounded copies, refreshed only after the parameters change
+    tsp_status s = prepare_weights(n, st);
+    if (s != TSP_OK) return s;
+    n->prepared = true;
+  }
   to_bf16_kernel<<<blocks_for(nv, 256), 256, 0, st>>>(a, n->a16, nv);
   conv_in_fwd_kernel<<<blocks_for(nv, 128), 128, 0, st>>>(db, n->a16, n->w1r, n->params + n->off_b[0], n->h[0],
                                                           n->mask[0]);
@@ -1370,6 +1374,7 @@ extern "C" tsp_status tsp_net_set_params(tsp_net n, const float* host, size_t co
   TSP_CUDA(cudaMemset(n->m, 0, sizeof(float) * count));
   TSP_CUDA(cudaMemset(n->v, 0, sizeof(float) * count));
   n->adam_step = 0;
+  n->prepared = false;
   return TSP_OK;
 }
 
@@ -1468,6 +1473,7 @@ extern "C" tsp_status tsp_net_adam(tsp_net n, float lr, float beta1, float beta2
                                    void* stream) {
   if (!n) return fail(TSP_EINVAL, "tsp_net_adam: NULL net");
   n->adam_step += 1;
+  n->prepared = false;
   return tsp_adam(n->params, n->grads, n->m, n->v, int64_t(n->n_params), lr, beta1, beta2, eps, weight_decay,
                   n->adam_step, stream);
 }

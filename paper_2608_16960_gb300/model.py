@@ -212,6 +212,7 @@ class WarmStartNet:
         n = ctypes.c_size_t()
         check(L_.tsp_net_num_params(h, ctypes.byref(n)), "tsp_net_num_params")
         self.n_params = n.value
+        self.version = 0  # bumped whenever the parameters change (set_params, adam)
 
     @staticmethod
     def layout():
@@ -241,6 +242,7 @@ class WarmStartNet:
         flat = np.ascontiguousarray(flat, dtype=np.float32)
         check(_lib.load().tsp_net_set_params(self.handle, ctypes.c_void_p(flat.ctypes.data), flat.size),
               "tsp_net_set_params")
+        self.version += 1
 
     def get_params(self) -> np.ndarray:
         out = np.zeros(self.n_params, np.float32)
@@ -274,6 +276,7 @@ class WarmStartNet:
     def adam(self, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, weight_decay=0.0):
         check(_lib.load().tsp_net_adam(self.handle, lr, betas[0], betas[1], eps, weight_decay,
                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)), "tsp_net_adam")
+        self.version += 1
 
     def activation(self, layer: int, batch: int) -> np.ndarray:
         nv = batch * int(np.prod(self.shape))

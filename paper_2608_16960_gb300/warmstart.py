@@ -44,6 +44,7 @@ class WarmStart:
         self.max_batch = max_batch
         self.net = WarmStartNet(self.shape, max_batch)
         self.net.init_params(seed=7)
+        self._graphs = {}  # (measurement shape, weights version) -> captured warm start
         L = _lib.load()
         self.R = torch.empty(self.geom.n_rays, device="cuda")
         self.C = torch.empty(self.shape, device="cuda")
@@ -117,12 +118,35 @@ class WarmStart:
         m = self.mask
         return float(torch.linalg.norm((x - truth)[m]) / torch.linalg.norm(truth[m]))
 
-    def warm_start(self, y):
-        """rho0 = net(a) * scale (clamped at 0)."""
+    def _warm_start_launches(self, y):
         a, scale = self.net_input(y[None])
         out = self.net.forward(a)
         check(_lib.load().tsp_scale_batch(_p(out), _p(scale), self.V, 1, 0, _st()), "tsp_scale_batch")
         return torch.clamp(out[0], min=0.0)
+
+    def warm_start(self, y):
+        """rho0 = net(a) * scale (clamped at 0). The input back-projection, the
+        network and the rescaling (about twenty short launches) are captured
+        once per measurement shape as a CUDA graph on a static input buffer and
+        replayed; the graphs are dropped whenever the weights change."""
+        key = (tuple(y.shape), self.net.version)
+        g = self._graphs.get(key)
+        if g is None:
+            self._graphs.clear()
+            static_y = y.detach().clone()
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):  # first run outside the capture: lazy set-up, weight copies
+                self._warm_start_launches(static_y)
+            torch.cuda.current_stream().wait_stream(side)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                out = self._warm_start_launches(static_y)
+            g = self._graphs[key] = (graph, static_y, out)
+        graph, static_y, out = g
+        static_y.copy_(y)
+        graph.replay()
+        return out.clone()
 
     def sirt(self, y, x, n_iter, reuse_weights):
         """n_iter non-negative SIRT updates of x in place (weights kept in self.ws)."""
