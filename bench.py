@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--lam", type=float, default=100.0, help="retrieval: radial Tikhonov weight of Eq. 10")
     ap.add_argument("--solver", choices=["cgls", "adam"], default="cgls", help="retrieval: solver of Eq. 10")
     ap.add_argument("--train-samples", type=int, default=20000, help="warm start: training phantoms")
-    ap.add_argument("--eval", type=int, default=8, help="warm start: held-out phantoms")
+    ap.add_argument("--eval", type=int, default=16, help="warm start: held-out phantoms")
     ap.add_argument("--cap", type=int, default=500, help="warm start: cold SIRT iteration cap")
     ap.add_argument("--target", type=float, default=0.01, help="warm start: relative error target")
     ap.add_argument("--ws-lr", type=float, default=2e-3, help="warm start: peak Adam step size (cosine decay)")
