@@ -86,15 +86,15 @@ def test_training_improves_on_the_input(ws):
 def test_captured_warm_start_equals_the_launches(ws):
     """The warm start replayed as a captured CUDA graph gives the eager
     launches' result (to float32 summation order: this pipeline
-    back-projects with atomic adds), repeats itself bit for bit on the same
-    input, and is captured again after the weights change (one training
-    step)."""
+    back-projects with atomic adds, so even two replays may differ in the
+    last bits), and is captured again after the weights change (one
+    training step)."""
     close = lambda u, v: float((u - v).abs().max()) <= 1e-4 * float(v.abs().max())
     rho = ws.phantoms([4242])
     y = ws.measure(rho, [4242])[0]
     a = ws.warm_start(y)
     assert close(a, ws._warm_start_launches(y))
-    assert torch.equal(ws.warm_start(y), a)  # replay with the same input
+    assert close(ws.warm_start(y), a)  # replay with the same input
     y2 = ws.measure(ws.phantoms([4243]), [4243])[0]
     assert close(ws.warm_start(y2), ws._warm_start_launches(y2))  # new input, same graph
     ws.train(4, batch=4, lr=1e-3, seed0=77)
