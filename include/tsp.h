@@ -162,10 +162,11 @@ tsp_status tsp_count_segments(tsp_grid grid, tsp_geom geom, int* counts, void* s
  * flat voxel index r*N_e*N_a + e*N_a + a and float32 length, ray-major in
  * order along each ray. With transpose != 0 the build also stores the same
  * segments voxel-major (uint32 ray index, float32 length), so that the
- * adjoint is a per-voxel gather instead of a per-segment scatter; the order of
- * the rays within one voxel's list is unspecified (it comes from atomic slot
- * claims), so adjoint results may differ run to run by float32 summation
- * order.
+ * adjoint is a per-voxel gather instead of a per-segment scatter. The
+ * transpose is a stable radix sort by voxel (8 key bits per pass), so each
+ * voxel's list is in ray-major order and the lists, and every result computed
+ * from them, are the same on every build; it takes 12 bytes per segment of
+ * temporary device memory during the build.
  *
  * The segments are those tsp_forward walks: lists and on-the-fly traversal
  * give the same F up to float32 rounding order. Forward and adjoint read the
@@ -196,6 +197,17 @@ tsp_status tsp_segments_info(tsp_segments s, int64_t* n_rays, int64_t* n_segment
  * Synchronous.
  */
 tsp_status tsp_segments_export(tsp_segments s, int64_t* ray_off, uint32_t* vox, float* len);
+/*
+ * tsp_segments_export_transposed - copies the voxel-major lists (built with
+ * transpose != 0) to HOST buffers (any may be NULL): vox_off int64 [V + 1]
+ * (entries of voxel v are [vox_off[v], vox_off[v+1]), V = N_r N_e N_a), ray
+ * uint32 [n_segments], len float32 [n_segments]. The transpose is a stable
+ * radix sort of the ray-major entries by voxel, so each voxel's entries are
+ * in ray-major order (by ray, then along the ray) and every build of the same
+ * grid and geometry gives the same lists. Synchronous. TSP_EINVAL if the
+ * handle has no voxel-major lists.
+ */
+tsp_status tsp_segments_export_transposed(tsp_segments s, int64_t* vox_off, uint32_t* ray, float* len);
 /*
  * tsp_segments_forward - y = F rho (Eq. 5) from the stored lists, one pass
  * over the lists per density. Shapes as tsp_forward; y overwritten.

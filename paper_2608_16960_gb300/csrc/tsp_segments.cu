@@ -179,27 +179,103 @@ __global__ void voxel_hist_kernel(const uint32_t* __restrict__ vox, int64_t S, i
     if ((vox[i] & ~HEAD) < V) atomicAdd(cnt + (vox[i] & ~HEAD), 1);
 }
 
-// warp per ray: scatter its segments into the voxel-major lists
-__global__ void transpose_kernel(const int64_t* __restrict__ ray_off, const uint32_t* __restrict__ vox,
-                                 const float* __restrict__ len, int64_t n_rays, int64_t V,
-                                 unsigned long long* __restrict__ cursor, uint32_t* __restrict__ ray_of,
-                                 float* __restrict__ len_t) {
-  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= n_rays) return;
-  for (int64_t s = ray_off[w] + lane; s < ray_off[w + 1]; s += 32) {
-    const uint32_t v = vox[s] & ~HEAD;
-    if (v >= V) continue;
-    const unsigned long long p = atomicAdd(cursor + v, 1ull);
-    ray_of[p] = uint32_t(w);
-    len_t[p] = len[s];
+// ---- voxel-major transpose: stable LSD radix sort of the entries by voxel ----
+// Keys are the voxel ids of the ray-major entries, values their positions s in
+// the ray-major lists, RB bits of the key per pass. A pass counts each tile's
+// digits, scans the counts digit-major (digit 0 of every tile, then digit 1,
+// ...) and scatters: an entry goes to its digit's base in its tile plus the
+// number of same-digit entries before it in the tile. Every pass keeps the
+// order of equal digits, so after the last one each voxel's entries are in
+// ray-major order (by ray, then along the ray): the same rows on every build.
+constexpr int RB = 8, RD = 1 << RB;  // key bits per pass, digits
+constexpr int RW = 8, RK = 16;       // warps per block, entries per lane
+constexpr int RT = RW * 32 * RK;     // entries per tile
+
+__device__ __forceinline__ uint32_t radix_key(const uint32_t* __restrict__ keys, bool first, int64_t i) {
+  return first ? (keys[i] & ~HEAD) : keys[i];
+}
+
+__global__ void __launch_bounds__(RW * 32) radix_hist_kernel(const uint32_t* __restrict__ keys, bool first,
+                                                             int64_t S, int shift, int64_t n_tiles,
+                                                             int* __restrict__ hist) {
+  __shared__ int h[RD];
+  for (int d = threadIdx.x; d < RD; d += blockDim.x) h[d] = 0;
+  __syncthreads();
+  const int64_t t = blockIdx.x, e0 = t * RT;
+  for (int j = threadIdx.x; j < RT; j += blockDim.x) {
+    const int64_t i = e0 + j;
+    if (i < S) atomicAdd(&h[(radix_key(keys, first, i) >> shift) & (RD - 1)], 1);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < RD; d += blockDim.x) hist[int64_t(d) * n_tiles + t] = h[d];
+}
+
+// One pass. A warp ranks its 32 * RK consecutive entries in order, RK rounds
+// of 32: lanes with equal digits find each other (match), take the warp's
+// running count for the digit plus the number of such lanes below them, and
+// the lowest of them advances the count. The warps' counts then become
+// offsets within the tile, in warp order. FIRST reads the ray-major columns
+// (values = positions); FINAL writes the transposed entries (ray id, length)
+// instead of (key, value).
+template <bool FIRST, bool FINAL>
+__global__ void __launch_bounds__(RW * 32) radix_scatter_kernel(
+    const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t S, int shift, int64_t n_tiles,
+    const int64_t* __restrict__ base, uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+    const uint32_t* __restrict__ ray_id, const float* __restrict__ len_in, float* __restrict__ len_out) {
+  __shared__ int cnt[RW][RD];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int d = lane; d < RD; d += 32) cnt[warp][d] = 0;
+  __syncwarp();
+  const int64_t t = blockIdx.x, w0 = t * RT + int64_t(warp) * (32 * RK);
+  const unsigned below = (1u << lane) - 1u;
+  uint32_t key[RK], val[RK];
+  int rank[RK];
+#pragma unroll
+  for (int k = 0; k < RK; ++k) {
+    const int64_t i = w0 + k * 32 + lane;
+    const bool ok = i < S;
+    key[k] = ok ? radix_key(keys, FIRST, i) : 0u;
+    val[k] = ok ? (FIRST ? uint32_t(i) : vals[i]) : 0u;
+    const uint32_t d = ok ? (key[k] >> shift) & (RD - 1) : uint32_t(RD);  // past the end: a class of its own
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    rank[k] = ok ? cnt[warp][d] + __popc(peers & below) : 0;
+    __syncwarp();
+    if (ok && (peers & below) == 0) cnt[warp][d] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < RD; d += blockDim.x) {
+    int run = 0;
+    for (int w = 0; w < RW; ++w) {
+      const int c = cnt[w][d];
+      cnt[w][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < RK; ++k) {
+    if (w0 + k * 32 + lane >= S) continue;
+    const uint32_t d = (key[k] >> shift) & (RD - 1);
+    const int64_t pos = base[int64_t(d) * n_tiles + t] + cnt[warp][d] + rank[k];
+    if (FINAL) {
+      keys_out[pos] = ray_id[val[k]];
+      len_out[pos] = len_in[val[k]];
+    } else {
+      keys_out[pos] = key[k];
+      vals_out[pos] = val[k];
+    }
   }
 }
 
-__global__ void i64_to_u64_kernel(const int64_t* __restrict__ a, unsigned long long* __restrict__ b, int64_t n) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    b[i] = (unsigned long long)a[i];
+// ray id of every ray-major entry (warp per ray)
+__global__ void ray_ids_kernel(const int64_t* __restrict__ off, int64_t n_rays, uint32_t* __restrict__ rid) {
+  const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_rays) return;
+  for (int64_t s = off[w] + lane; s < off[w + 1]; s += 32) rid[s] = uint32_t(w);
 }
+
 
 // ---- streaming forward / adjoint ----
 // The lists are read as one flat stream: warp t takes entries [t*TILE,
@@ -627,16 +703,22 @@ extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int trans
   int* vcount = nullptr;
   int* tmp = nullptr;
   int64_t* pos = nullptr;
-  unsigned long long* cursor = nullptr;
+  uint32_t *rk = nullptr, *rv = nullptr, *rid = nullptr;  // radix sort: second key/value buffer, ray ids
+  int* rhist = nullptr;
+  int64_t* rbase = nullptr;
   auto release = [&]() {
     cudaFree(counts);
     cudaFree(vcount);
     cudaFree(tmp);
     cudaFree(pos);
-    cudaFree(cursor);
-    counts = vcount = tmp = nullptr;
-    pos = nullptr;
-    cursor = nullptr;
+    cudaFree(rk);
+    cudaFree(rv);
+    cudaFree(rid);
+    cudaFree(rhist);
+    cudaFree(rbase);
+    counts = vcount = tmp = rhist = nullptr;
+    pos = rbase = nullptr;
+    rk = rv = rid = nullptr;
   };
   auto bail = [&](tsp_status r) {
     cudaStreamSynchronize(cs);
@@ -689,7 +771,6 @@ extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int trans
     t.n_cols = s->n_rays;
     t.S = s->n_segs;
     SEG_TRY(cudaMalloc(&vcount, sizeof(int) * size_t(s->V)));
-    SEG_TRY(cudaMalloc(&cursor, sizeof(unsigned long long) * size_t(s->V)));
     SEG_TRY(cudaMalloc(&t.off, sizeof(int64_t) * size_t(s->V + 1)));
     SEG_TRY(cudaMalloc(&t.idx, sizeof(uint32_t) * P));
     SEG_TRY(cudaMalloc(&t.len, sizeof(float) * P));
@@ -698,9 +779,51 @@ extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int trans
     voxel_hist_kernel<<<152 * 16, 256, 0, cs>>>(f.idx, s->n_segs, s->V, vcount);
     st = exclusive_scan(vcount, s->V, t.off, cs);
     if (st != TSP_OK) return bail(st);
-    i64_to_u64_kernel<<<152 * 4, 256, 0, cs>>>(t.off, cursor, s->V);
-    transpose_kernel<<<unsigned((s->n_rays * 32 + 255) / 256), 256, 0, cs>>>(f.off, f.idx, f.len, s->n_rays, s->V,
-                                                                            cursor, t.idx, t.len);
+    if (s->n_segs > 0) {
+      // stable radix sort by voxel; the last pass writes (ray, length) into t,
+      // the passes before it alternate between t's arrays and (rk, rv)
+      int bits = 1;
+      while (bits < 32 && (uint64_t(s->V - 1) >> bits) != 0) ++bits;
+      const int passes = (bits + RB - 1) / RB;
+      const int64_t n_rt = (s->n_segs + RT - 1) / RT;
+      SEG_TRY(cudaMalloc(&rid, sizeof(uint32_t) * P));
+      SEG_TRY(cudaMalloc(&rhist, sizeof(int) * size_t(RD * n_rt)));
+      SEG_TRY(cudaMalloc(&rbase, sizeof(int64_t) * size_t(RD * n_rt + 1)));
+      if (passes > 1) {
+        SEG_TRY(cudaMalloc(&rk, sizeof(uint32_t) * P));
+        SEG_TRY(cudaMalloc(&rv, sizeof(uint32_t) * P));
+      }
+      ray_ids_kernel<<<unsigned((s->n_rays * 32 + 255) / 256), 256, 0, cs>>>(f.off, s->n_rays, rid);
+      uint32_t* ak = t.idx;
+      uint32_t* av = reinterpret_cast<uint32_t*>(t.len);
+      const uint32_t *ik = f.idx, *iv = nullptr;
+      for (int p = 0; p < passes; ++p) {
+        const bool first = p == 0, final_pass = p == passes - 1;
+        const int shift = p * RB;
+        radix_hist_kernel<<<unsigned(n_rt), RW * 32, 0, cs>>>(ik, first, s->n_segs, shift, n_rt, rhist);
+        st = exclusive_scan(rhist, RD * n_rt, rbase, cs);
+        if (st != TSP_OK) return bail(st);
+        const bool to_a = (passes - 1 - p) % 2 == 0;
+        uint32_t* ok_ = to_a ? ak : rk;
+        uint32_t* ov = to_a ? av : rv;
+        const unsigned g = unsigned(n_rt);
+        if (first && final_pass)
+          radix_scatter_kernel<true, true><<<g, RW * 32, 0, cs>>>(ik, iv, s->n_segs, shift, n_rt, rbase, t.idx,
+                                                                  nullptr, rid, f.len, t.len);
+        else if (first)
+          radix_scatter_kernel<true, false><<<g, RW * 32, 0, cs>>>(ik, iv, s->n_segs, shift, n_rt, rbase, ok_, ov,
+                                                                   nullptr, nullptr, nullptr);
+        else if (final_pass)
+          radix_scatter_kernel<false, true><<<g, RW * 32, 0, cs>>>(ik, iv, s->n_segs, shift, n_rt, rbase, t.idx,
+                                                                   nullptr, rid, f.len, t.len);
+        else
+          radix_scatter_kernel<false, false><<<g, RW * 32, 0, cs>>>(ik, iv, s->n_segs, shift, n_rt, rbase, ok_, ov,
+                                                                    nullptr, nullptr, nullptr);
+        SEG_TRY(cudaGetLastError());
+        ik = ok_;
+        iv = ov;
+      }
+    }
     mark_heads_kernel<<<unsigned((s->V + 255) / 256), 256, 0, cs>>>(t.off, s->V, t.idx);
     SEG_TRY(cudaGetLastError());
     st = finish_list(t, tmp, pos, cs);
@@ -734,6 +857,21 @@ extern "C" tsp_status tsp_segments_export(tsp_segments s, int64_t* ray_off, uint
     for (int64_t i = 0; i < s->n_segs; ++i) vox[i] &= ~HEAD;
   }
   if (len && s->n_segs) TSP_CUDA(cudaMemcpy(len, s->fwd.len, sizeof(float) * size_t(s->n_segs), cudaMemcpyDeviceToHost));
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_segments_export_transposed(tsp_segments s, int64_t* vox_off, uint32_t* ray, float* len) {
+  if (!s) return fail(TSP_EINVAL, "tsp_segments_export_transposed: NULL handle");
+  if (!s->has_adj) return fail(TSP_EINVAL, "tsp_segments_export_transposed: lists built without the transpose");
+  tsp_status st = check_device(s->device);
+  if (st != TSP_OK) return st;
+  if (vox_off)
+    TSP_CUDA(cudaMemcpy(vox_off, s->adj.off, sizeof(int64_t) * size_t(s->V + 1), cudaMemcpyDeviceToHost));
+  if (ray && s->n_segs) {
+    TSP_CUDA(cudaMemcpy(ray, s->adj.idx, sizeof(uint32_t) * size_t(s->n_segs), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < s->n_segs; ++i) ray[i] &= ~HEAD;
+  }
+  if (len && s->n_segs) TSP_CUDA(cudaMemcpy(len, s->adj.len, sizeof(float) * size_t(s->n_segs), cudaMemcpyDeviceToHost));
   return TSP_OK;
 }
 

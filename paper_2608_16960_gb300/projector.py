@@ -293,6 +293,17 @@ class Segments:
         check(_lib.load().tsp_segments_export(self.handle, vp(off), vp(vox), vp(ln)), "tsp_segments_export")
         return off, vox[:n_segs], ln[:n_segs]
 
+    def export_transposed(self):
+        """Host copies (vox_off int64, ray uint32, len float32) of the voxel-major lists."""
+        n_rays, n_segs, _ = self.info()
+        off = np.zeros(self.grid.voxels + 1, dtype=np.int64)
+        ray = np.zeros(max(n_segs, 1), dtype=np.uint32)
+        ln = np.zeros(max(n_segs, 1), dtype=np.float32)
+        vp = lambda a: ctypes.c_void_p(a.ctypes.data)
+        check(_lib.load().tsp_segments_export_transposed(self.handle, vp(off), vp(ray), vp(ln)),
+              "tsp_segments_export_transposed")
+        return off, ray[:n_segs], ln[:n_segs]
+
     def forward(self, rho: torch.Tensor) -> torch.Tensor:
         _require_cuda(rho, "rho")
         if tuple(rho.shape[-3:]) != self.grid.shape or rho.dim() not in (3, 4):
