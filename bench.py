@@ -46,6 +46,12 @@ STREAM_DRAM_BYTES_PER_ENTRY = 8.38
 # traversal's: the running optical depth (multiply, fma) and the contribution
 # (add, exponential counted as one, multiply, fma).
 ATTEN_EXTRA_OPS = 6.0
+# DRAM bytes (read + write) per launch of the on-the-fly traversal on the
+# default paper-scale workload, averaged over its cone and parallel launches,
+# from one ncu capture of the last timed step (dram__bytes_read.sum +
+# dram__bytes_write.sum): the forward reads the volume once (2.86 MB of
+# 2.88 MB; y stays in L2), the adjoint the detector values and the volume.
+TRACE_DRAM_BYTES = {"forward": 2857472.0, "adjoint": 11263616.0}
 SUN_DIRECTION = (0.61, -0.42, 0.67)
 
 
@@ -357,7 +363,9 @@ def run_ours(args):
     peak_ops = SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12  # Tops/s
     achieved = OPS_PER_SEGMENT * seg_per_launch / t_dom_launch / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s", "frac": achieved / peak_ops,
-                "traffic": None, "kernel": f"{dom}_kernel", "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz",
+                "traffic": TRACE_DRAM_BYTES[dom] if not args.views else None,
+                "kernel": "trace_kernel<GatherOp> (F)" if dom == "forward" else "trace_kernel<ScatterOp> (F^T)",
+                "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz",
                 "ops_per_segment": OPS_PER_SEGMENT,
                 "l2_gbs": (4.0 if dom == "forward" else 8.0) * seg_per_launch / t_dom_launch / 1e9}
 
