@@ -165,7 +165,7 @@ tsp_status tsp_count_segments(tsp_grid grid, tsp_geom geom, int* counts, void* s
  * adjoint is a per-voxel gather instead of a per-segment scatter. The
  * transpose is a stable radix sort by voxel (8 key bits per pass), so each
  * voxel's list is in ray-major order and the lists, and every result computed
- * from them, are the same on every build; it takes 12 bytes per segment of
+ * from them, are the same on every build; it takes about 18 bytes per segment of
  * temporary device memory during the build.
  *
  * The segments are those tsp_forward walks: lists and on-the-fly traversal

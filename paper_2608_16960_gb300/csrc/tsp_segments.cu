@@ -180,15 +180,15 @@ __global__ void voxel_hist_kernel(const uint32_t* __restrict__ vox, int64_t S, i
 }
 
 // ---- voxel-major transpose: stable LSD radix sort of the entries by voxel ----
-// Keys are the voxel ids of the ray-major entries, values their positions s in
-// the ray-major lists, RB bits of the key per pass. A pass counts each tile's
-// digits, scans the counts digit-major (digit 0 of every tile, then digit 1,
-// ...) and scatters: an entry goes to its digit's base in its tile plus the
-// number of same-digit entries before it in the tile. Every pass keeps the
-// order of equal digits, so after the last one each voxel's entries are in
-// ray-major order (by ray, then along the ray): the same rows on every build.
+// Keys are the voxel ids of the ray-major entries, carried with their ray id
+// and length, RB bits of the key per pass. A pass counts each tile's digits,
+// scans the counts digit-major (digit 0 of every tile, then digit 1, ...) and
+// scatters: an entry goes to its digit's base in its tile plus the number of
+// same-digit entries before it in the tile. Every pass keeps the order of
+// equal digits, so after the last one each voxel's entries are in ray-major
+// order (by ray, then along the ray): the same rows on every build.
 constexpr int RB = 8, RD = 1 << RB;  // key bits per pass, digits
-constexpr int RW = 8, RK = 16;       // warps per block, entries per lane
+constexpr int RW = 8, RK = 8;        // warps per block, entries per lane
 constexpr int RT = RW * 32 * RK;     // entries per tile
 
 __device__ __forceinline__ uint32_t radix_key(const uint32_t* __restrict__ keys, bool first, int64_t i) {
@@ -210,32 +210,40 @@ __global__ void __launch_bounds__(RW * 32) radix_hist_kernel(const uint32_t* __r
   for (int d = threadIdx.x; d < RD; d += blockDim.x) hist[int64_t(d) * n_tiles + t] = h[d];
 }
 
-// One pass. A warp ranks its 32 * RK consecutive entries in order, RK rounds
-// of 32: lanes with equal digits find each other (match), take the warp's
-// running count for the digit plus the number of such lanes below them, and
-// the lowest of them advances the count. The warps' counts then become
-// offsets within the tile, in warp order. FIRST reads the ray-major columns
-// (values = positions); FINAL writes the transposed entries (ray id, length)
-// instead of (key, value).
+// One pass over a tile of RT entries (RD == threads per block). Ranking: a
+// warp takes its 32 * RK consecutive entries in RK rounds of 32; lanes with
+// equal digits find each other (match), take the warp's running count for the
+// digit plus the number of such lanes below them, and the lowest of them
+// advances the count. The warps' counts become offsets in warp order and the
+// digits' totals offsets in digit order, which sorts the tile by digit in
+// shared memory; the tile then leaves as one contiguous run per digit.
+// FIRST reads the ray-major columns (keys with the head flag) and the ray ids
+// and lengths beside them; FINAL writes only (ray, length).
 template <bool FIRST, bool FINAL>
 __global__ void __launch_bounds__(RW * 32) radix_scatter_kernel(
-    const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t S, int shift, int64_t n_tiles,
-    const int64_t* __restrict__ base, uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-    const uint32_t* __restrict__ ray_id, const float* __restrict__ len_in, float* __restrict__ len_out) {
+    const uint32_t* __restrict__ keys, const uint32_t* __restrict__ rays, const float* __restrict__ lens, int64_t S,
+    int shift, int64_t n_tiles, const int64_t* __restrict__ base, uint32_t* __restrict__ keys_out,
+    uint32_t* __restrict__ rays_out, float* __restrict__ lens_out) {
   __shared__ int cnt[RW][RD];
+  __shared__ int start[RD];
+  __shared__ int64_t scan_sh[32];
+  __shared__ uint32_t sk[RT], sr[RT];
+  __shared__ float sl[RT];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int d = lane; d < RD; d += 32) cnt[warp][d] = 0;
   __syncwarp();
   const int64_t t = blockIdx.x, w0 = t * RT + int64_t(warp) * (32 * RK);
   const unsigned below = (1u << lane) - 1u;
-  uint32_t key[RK], val[RK];
+  uint32_t key[RK], ray[RK];
+  float len[RK];
   int rank[RK];
 #pragma unroll
   for (int k = 0; k < RK; ++k) {
     const int64_t i = w0 + k * 32 + lane;
     const bool ok = i < S;
     key[k] = ok ? radix_key(keys, FIRST, i) : 0u;
-    val[k] = ok ? (FIRST ? uint32_t(i) : vals[i]) : 0u;
+    ray[k] = ok ? rays[i] : 0u;
+    len[k] = ok ? lens[i] : 0.0f;
     const uint32_t d = ok ? (key[k] >> shift) & (RD - 1) : uint32_t(RD);  // past the end: a class of its own
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     rank[k] = ok ? cnt[warp][d] + __popc(peers & below) : 0;
@@ -244,27 +252,36 @@ __global__ void __launch_bounds__(RW * 32) radix_scatter_kernel(
     __syncwarp();
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < RD; d += blockDim.x) {
+  {
+    const int d = threadIdx.x;
     int run = 0;
     for (int w = 0; w < RW; ++w) {
       const int c = cnt[w][d];
       cnt[w][d] = run;
       run += c;
     }
+    const int64_t incl = block_incl_scan(run, scan_sh);
+    start[d] = int(incl - run);
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < RK; ++k) {
     if (w0 + k * 32 + lane >= S) continue;
     const uint32_t d = (key[k] >> shift) & (RD - 1);
-    const int64_t pos = base[int64_t(d) * n_tiles + t] + cnt[warp][d] + rank[k];
-    if (FINAL) {
-      keys_out[pos] = ray_id[val[k]];
-      len_out[pos] = len_in[val[k]];
-    } else {
-      keys_out[pos] = key[k];
-      vals_out[pos] = val[k];
-    }
+    const int lp = start[d] + cnt[warp][d] + rank[k];
+    sk[lp] = key[k];
+    sr[lp] = ray[k];
+    sl[lp] = len[k];
+  }
+  __syncthreads();
+  const int n = int(S - t * RT < RT ? S - t * RT : RT);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const uint32_t kk = sk[j];
+    const uint32_t d = (kk >> shift) & (RD - 1);
+    const int64_t g = base[int64_t(d) * n_tiles + t] + (j - start[d]);
+    if (!FINAL) keys_out[g] = kk;
+    rays_out[g] = sr[j];
+    lens_out[g] = sl[j];
   }
 }
 
@@ -703,7 +720,8 @@ extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int trans
   int* vcount = nullptr;
   int* tmp = nullptr;
   int64_t* pos = nullptr;
-  uint32_t *rk = nullptr, *rv = nullptr, *rid = nullptr;  // radix sort: second key/value buffer, ray ids
+  uint32_t *ka = nullptr, *kb = nullptr, *rb = nullptr;  // radix sort: keys of both buffers, B's ray ids
+  float* lb = nullptr;                                    // and B's lengths
   int* rhist = nullptr;
   int64_t* rbase = nullptr;
   auto release = [&]() {
@@ -711,14 +729,16 @@ extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int trans
     cudaFree(vcount);
     cudaFree(tmp);
     cudaFree(pos);
-    cudaFree(rk);
-    cudaFree(rv);
-    cudaFree(rid);
+    cudaFree(ka);
+    cudaFree(kb);
+    cudaFree(rb);
+    cudaFree(lb);
     cudaFree(rhist);
     cudaFree(rbase);
     counts = vcount = tmp = rhist = nullptr;
     pos = rbase = nullptr;
-    rk = rv = rid = nullptr;
+    ka = kb = rb = nullptr;
+    lb = nullptr;
   };
   auto bail = [&](tsp_status r) {
     cudaStreamSynchronize(cs);
@@ -780,48 +800,52 @@ extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int trans
     st = exclusive_scan(vcount, s->V, t.off, cs);
     if (st != TSP_OK) return bail(st);
     if (s->n_segs > 0) {
-      // stable radix sort by voxel; the last pass writes (ray, length) into t,
-      // the passes before it alternate between t's arrays and (rk, rv)
+      // Stable radix sort by voxel. The last pass writes (ray, length) into t;
+      // the passes before it alternate between the buffers A = (ka, t.idx,
+      // t.len) and B = (kb, rb, lb) so that the last one reads B. The ray ids
+      // of the ray-major entries start in the ray array that the first pass
+      // does not write.
       int bits = 1;
       while (bits < 32 && (uint64_t(s->V - 1) >> bits) != 0) ++bits;
       const int passes = (bits + RB - 1) / RB;
       const int64_t n_rt = (s->n_segs + RT - 1) / RT;
-      SEG_TRY(cudaMalloc(&rid, sizeof(uint32_t) * P));
       SEG_TRY(cudaMalloc(&rhist, sizeof(int) * size_t(RD * n_rt)));
       SEG_TRY(cudaMalloc(&rbase, sizeof(int64_t) * size_t(RD * n_rt + 1)));
+      SEG_TRY(cudaMalloc(&rb, sizeof(uint32_t) * P));
       if (passes > 1) {
-        SEG_TRY(cudaMalloc(&rk, sizeof(uint32_t) * P));
-        SEG_TRY(cudaMalloc(&rv, sizeof(uint32_t) * P));
+        SEG_TRY(cudaMalloc(&kb, sizeof(uint32_t) * P));
+        SEG_TRY(cudaMalloc(&lb, sizeof(float) * P));
       }
+      if (passes > 2) SEG_TRY(cudaMalloc(&ka, sizeof(uint32_t) * P));
+      const bool first_to_a = (passes - 1) % 2 == 0;
+      uint32_t* rid = first_to_a ? rb : t.idx;
       ray_ids_kernel<<<unsigned((s->n_rays * 32 + 255) / 256), 256, 0, cs>>>(f.off, s->n_rays, rid);
-      uint32_t* ak = t.idx;
-      uint32_t* av = reinterpret_cast<uint32_t*>(t.len);
-      const uint32_t *ik = f.idx, *iv = nullptr;
+      const uint32_t *ik = f.idx, *ir = rid;
+      const float* il = f.len;
       for (int p = 0; p < passes; ++p) {
         const bool first = p == 0, final_pass = p == passes - 1;
         const int shift = p * RB;
         radix_hist_kernel<<<unsigned(n_rt), RW * 32, 0, cs>>>(ik, first, s->n_segs, shift, n_rt, rhist);
         st = exclusive_scan(rhist, RD * n_rt, rbase, cs);
         if (st != TSP_OK) return bail(st);
-        const bool to_a = (passes - 1 - p) % 2 == 0;
-        uint32_t* ok_ = to_a ? ak : rk;
-        uint32_t* ov = to_a ? av : rv;
+        const bool to_a = final_pass || (passes - 1 - p) % 2 == 0;
+        uint32_t* ok_ = to_a ? ka : kb;
+        uint32_t* orr = to_a ? t.idx : rb;
+        float* ol = to_a ? t.len : lb;
         const unsigned g = unsigned(n_rt);
+        const int64_t S_ = s->n_segs;
         if (first && final_pass)
-          radix_scatter_kernel<true, true><<<g, RW * 32, 0, cs>>>(ik, iv, s->n_segs, shift, n_rt, rbase, t.idx,
-                                                                  nullptr, rid, f.len, t.len);
+          radix_scatter_kernel<true, true><<<g, RW * 32, 0, cs>>>(ik, ir, il, S_, shift, n_rt, rbase, ok_, orr, ol);
         else if (first)
-          radix_scatter_kernel<true, false><<<g, RW * 32, 0, cs>>>(ik, iv, s->n_segs, shift, n_rt, rbase, ok_, ov,
-                                                                   nullptr, nullptr, nullptr);
+          radix_scatter_kernel<true, false><<<g, RW * 32, 0, cs>>>(ik, ir, il, S_, shift, n_rt, rbase, ok_, orr, ol);
         else if (final_pass)
-          radix_scatter_kernel<false, true><<<g, RW * 32, 0, cs>>>(ik, iv, s->n_segs, shift, n_rt, rbase, t.idx,
-                                                                   nullptr, rid, f.len, t.len);
+          radix_scatter_kernel<false, true><<<g, RW * 32, 0, cs>>>(ik, ir, il, S_, shift, n_rt, rbase, ok_, orr, ol);
         else
-          radix_scatter_kernel<false, false><<<g, RW * 32, 0, cs>>>(ik, iv, s->n_segs, shift, n_rt, rbase, ok_, ov,
-                                                                    nullptr, nullptr, nullptr);
+          radix_scatter_kernel<false, false><<<g, RW * 32, 0, cs>>>(ik, ir, il, S_, shift, n_rt, rbase, ok_, orr, ol);
         SEG_TRY(cudaGetLastError());
         ik = ok_;
-        iv = ov;
+        ir = orr;
+        il = ol;
       }
     }
     mark_heads_kernel<<<unsigned((s->V + 255) / 256), 256, 0, cs>>>(t.off, s->V, t.idx);
