@@ -230,6 +230,16 @@ tsp_status tsp_segments_adjoint(tsp_segments s, const float* y, float* rho, int 
  * lists' fixup and memset launches). No host synchronisation.
  */
 tsp_status tsp_segments_sirt_workspace_bytes(tsp_segments s, size_t* bytes);
+/*
+ * tsp_segments_sirt_weights - the SIRT weights of tsp_sirt_weights from the
+ * stored lists: R = 1/(F 1) per ray (device float32 [n_rays]) and
+ * C = 1/(F^T 1) per voxel (device float32 [voxels]), 0 where the sum is 0,
+ * as tsp_segments_sirt computes them. With the voxel-major lists every sum
+ * runs in the lists' fixed order, so the weights are identical on every call
+ * and every build (tsp_sirt_weights sums with atomics). Allocates and frees
+ * 8 * max(n_rays, voxels) bytes of scratch in stream order.
+ */
+tsp_status tsp_segments_sirt_weights(tsp_segments s, float* R, float* C, void* stream);
 tsp_status tsp_segments_sirt(tsp_segments s, const float* y, float* x, int n_iter, int flags,
                              void* workspace, size_t workspace_bytes, void* stream);
 void tsp_segments_destroy(tsp_segments s);

@@ -62,6 +62,7 @@ SIGNATURES = {
     "tsp_segments_info": (_I, [_P, _I64P, _I64P, ctypes.POINTER(ctypes.c_size_t)]),
     "tsp_segments_export": (_I, [_P, _P, _P, _P]),
     "tsp_segments_export_transposed": (_I, [_P, _P, _P, _P]),
+    "tsp_segments_sirt_weights": (_I, [_P, _P, _P, _P]),
     "tsp_segments_forward": (_I, [_P, _P, _P, _I, _P]),
     "tsp_segments_adjoint": (_I, [_P, _P, _P, _I, _I, _P]),
     "tsp_segments_sirt_workspace_bytes": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),

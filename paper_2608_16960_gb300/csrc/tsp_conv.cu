@@ -873,9 +873,11 @@ __global__ void conv_in_fwd_kernel(Dims d, const bf16* __restrict__ a, const flo
   mask[gi] = bits;
 }
 
-// g_out = 2 (out - target) / n; loss += sum (out - target)^2 / n (double).
+// g_out = 2 (out - target) / n; shares[block] = the block's share of
+// sum (out - target)^2 / n (double), summed by ordered_sum_kernel.
+constexpr int MSE_BLOCKS = 152 * 8;
 __global__ void mse_kernel(const float* __restrict__ out, const float* __restrict__ tgt, int64_t n,
-                           float* __restrict__ g, double* __restrict__ loss) {
+                           float* __restrict__ g, double* __restrict__ shares) {
   double acc = 0.0;
   const double inv = 1.0 / double(n);
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
@@ -890,8 +892,17 @@ __global__ void mse_kernel(const float* __restrict__ out, const float* __restric
   if (threadIdx.x < 32) {
     double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) atomicAdd(loss, v);
+    if (threadIdx.x == 0) shares[blockIdx.x] = v;
   }
+}
+
+// *out = sum of part[0 .. n) in a fixed order (one warp: strided lane sums,
+// then a shuffle tree), so the loss repeats bit for bit.
+__global__ void ordered_sum_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += 32) v += part[i];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (threadIdx.x == 0) *out = v;
 }
 
 // Output layer backward, input side: g_h[v][ci] = sum_tap w6[tap][ci] g_out[v - d_tap].
@@ -1160,6 +1171,7 @@ struct tsp_net_s {
   float *out = nullptr, *gout = nullptr, *gh = nullptr;
   bf16* gz = nullptr;
   double* loss = nullptr;
+  double* loss_part = nullptr;  // per-block shares of the loss
   float* part = nullptr;  // per-CTA partial sums of the weight / bias gradient reductions
   int part_rows = 0;
   float* wpart = nullptr;  // per-CTA partial 32 -> 32 weight gradients [SMs][27][32][32]
@@ -1334,6 +1346,7 @@ extern "C" tsp_status tsp_net_create(int n_r, int n_e, int n_a, int max_batch, t
   if (st == TSP_OK) st = net_alloc(n, &n->gh, nv * CH);
   if (st == TSP_OK) st = net_alloc(n, &n->gz, nv * CH);
   if (st == TSP_OK) st = net_alloc(n, &n->loss, 1);
+  if (st == TSP_OK) st = net_alloc(n, &n->loss_part, MSE_BLOCKS);
   if (st == TSP_OK) st = set_attrs(n_a);
   if (st == TSP_OK) {  // one row per CTA of the reductions (2 per multiprocessor, THIN_OUT floats)
     n->part_rows = 2 * g_sm_count;
@@ -1444,9 +1457,10 @@ extern "C" tsp_status tsp_net_loss_grad(tsp_net n, const float* a, const float* 
   Dims db = d;
   db.B = batch;
   const int64_t nv = int64_t(batch) * d.V;
-  TSP_CUDA(cudaMemsetAsync(n->loss, 0, sizeof(double), cs));
   TSP_CUDA(cudaMemsetAsync(n->grads, 0, sizeof(float) * n->n_params, cs));
-  mse_kernel<<<std::min(blocks_for(nv, 256), 152 * 8), 256, 0, cs>>>(n->out, target, nv, n->gout, n->loss);
+  const int mse_blocks = int(std::min<int64_t>(blocks_for(nv, 256), MSE_BLOCKS));
+  mse_kernel<<<mse_blocks, 256, 0, cs>>>(n->out, target, nv, n->gout, n->loss_part);
+  ordered_sum_kernel<<<1, 32, 0, cs>>>(n->loss_part, mse_blocks, n->loss);
   // output layer
   thin_wgrad(n, 0, db, n->grads + n->off_w[5], n->grads + n->off_b[5], 1, cs);
   conv_out_dgrad_kernel<<<blocks_for(nv, 128), 128, 0, cs>>>(db, n->gout, n->w6r, n->gh);

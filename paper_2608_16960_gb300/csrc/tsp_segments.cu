@@ -928,6 +928,35 @@ extern "C" tsp_status tsp_segments_sirt_workspace_bytes(tsp_segments s, size_t* 
   return TSP_OK;
 }
 
+// R = 1 / (F 1), C = 1 / (F^T 1) from the lists (0 where a sum is 0); ones_v
+// [V] and ones_r [n_rays] are scratch.
+static tsp_status list_weights(tsp_segments s, float* R, float* C, float* ones_v, float* ones_r, cudaStream_t cs) {
+  const int64_t nr = s->n_rays, V = s->V;
+  fill_kernel<<<ew_blocks(V), 256, 0, cs>>>(ones_v, V, 1.0f);
+  tsp_status st = rows_apply(s->fwd, ones_v, V, R, nr, 1, 0, cs);
+  if (st != TSP_OK) return st;
+  recip_kernel<<<ew_blocks(nr), 256, 0, cs>>>(R, nr);
+  fill_kernel<<<ew_blocks(nr), 256, 0, cs>>>(ones_r, nr, 1.0f);
+  st = s->has_adj ? rows_apply(s->adj, ones_r, nr, C, V, 1, 0, cs) : tsp_segments_adjoint(s, ones_r, C, 1, 0, cs);
+  if (st != TSP_OK) return st;
+  recip_kernel<<<ew_blocks(V), 256, 0, cs>>>(C, V);
+  TSP_CUDA(cudaGetLastError());
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_segments_sirt_weights(tsp_segments s, float* R, float* C, void* stream) {
+  if (!s || !R || !C) return fail(TSP_EINVAL, "tsp_segments_sirt_weights: NULL argument");
+  tsp_status st = check_device(s->device);
+  if (st != TSP_OK) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  float* ones = nullptr;
+  const int64_t n = std::max<int64_t>(std::max(s->n_rays, s->V), 1);
+  TSP_CUDA(cudaMallocAsync(&ones, sizeof(float) * size_t(n) * 2, cs));
+  st = list_weights(s, R, C, ones, ones + n, cs);
+  cudaFreeAsync(ones, cs);
+  return st;
+}
+
 extern "C" tsp_status tsp_segments_sirt(tsp_segments s, const float* y, float* x, int n_iter, int flags,
                                         void* workspace, size_t workspace_bytes, void* stream) {
   if (!s || !y || !x || !workspace) return fail(TSP_EINVAL, "tsp_segments_sirt: NULL argument");
@@ -949,15 +978,8 @@ extern "C" tsp_status tsp_segments_sirt(tsp_segments s, const float* y, float* x
   float* C = reinterpret_cast<float*>(p + 2 * align256(4 * size_t(nr)));
   float* g = reinterpret_cast<float*>(p + 2 * align256(4 * size_t(nr)) + align256(4 * size_t(V)));
   if (!(flags & TSP_SIRT_REUSE_WEIGHTS)) {
-    // R = 1 / (F 1), C = 1 / (F^T 1)
-    fill_kernel<<<ew_blocks(V), 256, 0, cs>>>(g, V, 1.0f);
-    st = rows_apply(s->fwd, g, V, R, nr, 1, 0, cs);
+    st = list_weights(s, R, C, g, r, cs);
     if (st != TSP_OK) return st;
-    recip_kernel<<<ew_blocks(nr), 256, 0, cs>>>(R, nr);
-    fill_kernel<<<ew_blocks(nr), 256, 0, cs>>>(r, nr, 1.0f);
-    st = s->has_adj ? rows_apply(s->adj, r, nr, C, V, 1, 0, cs) : tsp_segments_adjoint(s, r, C, 1, 0, stream);
-    if (st != TSP_OK) return st;
-    recip_kernel<<<ew_blocks(V), 256, 0, cs>>>(C, V);
   }
   for (int it = 0; it < n_iter; ++it) {
     st = rows_apply(s->fwd, x, V, r, nr, 1, 0, cs);  // r = F x

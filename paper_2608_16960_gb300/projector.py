@@ -341,6 +341,17 @@ class Segments:
               "tsp_segments_sirt_workspace_bytes")
         return torch.empty(n.value, dtype=torch.uint8, device=torch.device("cuda", self.geom.device))
 
+    def sirt_weights(self):
+        """(R [n_rays], C [grid shape]): the SIRT weights as tsp_segments_sirt forms them."""
+        dev = torch.device("cuda", self.geom.device)
+        R = torch.empty(self.geom.n_rays, device=dev)
+        C = torch.empty(self.grid.shape, device=dev)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        check(_lib.load().tsp_segments_sirt_weights(self.handle, ctypes.c_void_p(R.data_ptr()),
+                                                    ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(st)),
+              "tsp_segments_sirt_weights")
+        return R, C
+
     def sirt(self, y: torch.Tensor, x: torch.Tensor, n_iter: int, nonneg: bool = False,
              workspace: torch.Tensor | None = None, reuse_weights: bool = False) -> torch.Tensor:
         """n_iter SIRT updates of x in place (as tsp_sirt), projections from the lists."""

@@ -45,14 +45,19 @@ class WarmStart:
         self.net = WarmStartNet(self.shape, max_batch)
         self.net.init_params(seed=7)
         self._graphs = {}  # (measurement shape, weights version) -> captured warm start
-        L = _lib.load()
-        self.R = torch.empty(self.geom.n_rays, device="cuda")
-        self.C = torch.empty(self.shape, device="cuda")
-        check(L.tsp_sirt_weights(self.grid.handle, self.geom.handle, _p(self.R), _p(self.C), _st()), "tsp_sirt_weights")
-        self.mask = self.C > 0  # voxels some ray crosses
         # SIRT projections: stored segment lists (steps 1-3 once) or on-the-fly traversal
         self.segs = Segments(self.grid, self.geom) if use_lists else None
         self.ws = self.segs.sirt_workspace() if use_lists else sirt_workspace(self.grid, self.geom)
+        # weights R = 1/(F 1), C = 1/(F^T 1); from the lists they sum in a fixed
+        # order, so the network's input, and training, repeat bit for bit
+        if use_lists:
+            self.R, self.C = self.segs.sirt_weights()
+        else:
+            self.R = torch.empty(self.geom.n_rays, device="cuda")
+            self.C = torch.empty(self.shape, device="cuda")
+            check(_lib.load().tsp_sirt_weights(self.grid.handle, self.geom.handle, _p(self.R), _p(self.C), _st()),
+                  "tsp_sirt_weights")
+        self.mask = self.C > 0  # voxels some ray crosses
 
     # ---- data -------------------------------------------------------------
     def phantoms(self, seeds):

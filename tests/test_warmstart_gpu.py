@@ -101,3 +101,36 @@ def test_captured_warm_start_equals_the_launches(ws):
     b = ws.warm_start(y)
     assert close(b, ws._warm_start_launches(y))  # new weights: captured again
     assert not close(b, a)
+
+
+def test_list_weights_match_traversal_weights_and_repeat():
+    """R = 1/(F 1) and C = 1/(F^T 1) from the stored lists: equal to the
+    traversal's weights up to float32 summation order, identical over two
+    builds of the lists (fixed-order sums, no atomics)."""
+    from paper_2608_16960_gb300.projector import Segments
+    e = synth.grid_edges(12, 10, 32)
+    w = WarmStart(e, synth.circular_orbit(12, 60.0, incline_deg=35.0), 32, 50.0, max_batch=4)
+    R0 = torch.empty(w.geom.n_rays, device="cuda")
+    C0 = torch.empty(w.shape, device="cuda")
+    _lib.check(_lib.load().tsp_sirt_weights(w.grid.handle, w.geom.handle, _p(R0), _p(C0), _st()), "tsp_sirt_weights")
+    R1, C1 = Segments(w.grid, w.geom).sirt_weights()
+    R2, C2 = Segments(w.grid, w.geom).sirt_weights()
+    assert torch.equal(R1, R2) and torch.equal(C1, C2)
+    assert torch.equal(R1 > 0, R0 > 0) and torch.equal(C1 > 0, C0 > 0)
+    assert torch.allclose(R1, R0, rtol=2e-6, atol=0.0) and torch.allclose(C1, C0, rtol=2e-6, atol=0.0)
+
+
+def test_training_from_lists_repeats_bit_for_bit():
+    """Two warm starts built from scratch on stored lists train to identical
+    losses and weights: phantoms, noise, the network input (list weights and
+    list back-projection) and every gradient are fixed-order computations."""
+    e = synth.grid_edges(12, 10, 32)
+    pos = synth.circular_orbit(12, 60.0, incline_deg=35.0)
+    runs = []
+    for _ in range(2):
+        w = WarmStart(e, pos, 32, 50.0, max_batch=4, use_lists=True)
+        losses = w.train(24, batch=4, lr=2e-3, seed0=500)
+        y = w.measure(w.phantoms([77]), [77])[0]
+        runs.append((losses, w.warm_start(y).cpu()))
+    assert runs[0][0] == runs[1][0]
+    assert torch.equal(runs[0][1], runs[1][1])
