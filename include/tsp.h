@@ -509,7 +509,9 @@ tsp_status tsp_net_activation(tsp_net net, int layer, int batch, void* host);
 /*
  * tsp_sirt_weights - the SIRT weights alone: R = 1/(F 1) per ray (device float32
  * [n_rays]) and C = 1/(F^T 1) per voxel (device float32 [voxels]), 0 where the
- * sum is 0. Used to form the warm start's input C * F^T(R * y).
+ * sum is 0. Used to form the warm start's input C * F^T(R * y) when it runs
+ * without stored lists (with them, tsp_segments_sirt_weights). F^T 1 sums
+ * with atomics, so C may differ in its last bits between calls.
  */
 tsp_status tsp_sirt_weights(tsp_grid grid, tsp_geom geom, float* R, float* C, void* stream);
 
