@@ -329,7 +329,7 @@ extern "C" tsp_status tsp_atten_backward(tsp_grid grid, tsp_geom geom, const flo
   if (st != TSP_OK) return st;
   if (!rho || !sigma || !tau1 || !y) return fail(TSP_EINVAL, "tsp_atten_backward: NULL array");
   const tsp_launch l = preferred_launch(grid, geom, true);
-  const int64_t V = grid->voxels(), n = geom->n_rays;
+  const int64_t V = grid->voxels();
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
   if (!accumulate) {
     const size_t bytes = sizeof(float) * size_t(V) * batch;

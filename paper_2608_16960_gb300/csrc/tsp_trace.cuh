@@ -350,7 +350,6 @@ struct op_has_gap<Op, decltype(void(static_cast<Op*>(nullptr)->gap()))> {
 template <class Op>
 TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d[3], Op& op) {
   const float xx = x[0].hi, xy = x[1].hi, xz = x[2].hi;
-  const float dx = d[0].hi, dy = d[1].hi, dz = d[2].hi;
   // The line arrives as float-float start and direction (exact for float32
   // inputs; carrying the rounding residue of detector-generated rays).
   // Its closest point to the origin, q = (d x (x x d)) / |d|^2, is formed in
