@@ -52,6 +52,12 @@ ATTEN_EXTRA_OPS = 6.0
 # dram__bytes_write.sum): the forward reads the volume once (2.86 MB of
 # 2.88 MB; y stays in L2), the adjoint the detector values and the volume.
 TRACE_DRAM_BYTES = {"forward": 2857472.0, "adjoint": 11263616.0}
+
+
+def ordinal(k: int) -> str:
+    """1st, 2nd, 3rd, 4th, ..., 11th, 12th, 13th, 21st, ..."""
+    suffix = "th" if 10 <= k % 100 <= 20 else {1: "st", 2: "nd", 3: "rd"}.get(k % 10, "th")
+    return f"{k}{suffix}"
 SUN_DIRECTION = (0.61, -0.42, 0.67)
 
 
@@ -183,7 +189,7 @@ def cpu_baseline(wl, target_s=15.0):
     stride = max(1, int(stride * dt / target_s))
     n, dt = time_oracle(wl, stride)
     return {"value": n / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"every {stride}th ray of each view set ({n} rays), forward + adjoint, FP64, {dt:.1f} s"}
+            "sample": f"every {ordinal(stride)} ray of each view set ({n} rays), forward + adjoint, FP64, {dt:.1f} s"}
 
 
 # ---------------------------------------------------------------------------
@@ -213,7 +219,7 @@ def run_reference(args):
         oracle.adjoint(wl.edges, st, di, yv)
     dt = time.perf_counter() - t
     value = len(st) * args.steps / dt
-    sample = f"every {stride}th ray of each view set ({len(st)} rays) per step, forward + adjoint, FP64"
+    sample = f"every {ordinal(stride)} ray of each view set ({len(st)} rays) per step, forward + adjoint, FP64"
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
