@@ -240,6 +240,18 @@ tsp_status tsp_segments_sirt_workspace_bytes(tsp_segments s, size_t* bytes);
  * 8 * max(n_rays, voxels) bytes of scratch in stream order.
  */
 tsp_status tsp_segments_sirt_weights(tsp_segments s, float* R, float* C, void* stream);
+/*
+ * tsp_debug_fail_allocation - test hook: the device allocation `after`
+ * allocations from now (0: the next one) made by the stored-list code
+ * (tsp_segments_build, tsp_sirt_chunked) fails once as if the device were out
+ * of memory; a negative value disarms it. Lets tests drive the out-of-memory
+ * paths (TSP_ENOMEM, the chunked driver's finish-and-retry) without
+ * exhausting a GPU. tsp_debug_allocation_count gives the number of such
+ * allocations made so far (to aim the hook). Process-wide, not thread-safe
+ * with respect to concurrent builds.
+ */
+tsp_status tsp_debug_fail_allocation(int64_t after);
+tsp_status tsp_debug_allocation_count(int64_t* count);
 tsp_status tsp_segments_sirt(tsp_segments s, const float* y, float* x, int n_iter, int flags,
                              void* workspace, size_t workspace_bytes, void* stream);
 void tsp_segments_destroy(tsp_segments s);
@@ -501,6 +513,18 @@ tsp_status tsp_net_num_params(tsp_net net, size_t* count);
 tsp_status tsp_net_set_params(tsp_net net, const float* host_params, size_t count);
 tsp_status tsp_net_get_params(tsp_net net, float* host_params, size_t count);
 tsp_status tsp_net_get_grads(tsp_net net, float* host_grads, size_t count);
+/*
+ * tsp_net_get_state / tsp_net_set_state - the whole training state, for
+ * checkpoint and resume: parameters, Adam's first and second moments (HOST
+ * float32 [count] each, count = tsp_net_num_params) and the Adam step
+ * counter. Both synchronise the device. set_state replaces all of it, so the
+ * next tsp_net_adam continues the optimiser exactly where get_state found it:
+ * a resumed training run repeats an uninterrupted one bit for bit (given the
+ * same data). TSP_EINVAL on a count mismatch or a negative step.
+ */
+tsp_status tsp_net_get_state(tsp_net net, float* params, float* m, float* v, size_t count, int* adam_step);
+tsp_status tsp_net_set_state(tsp_net net, const float* params, const float* m, const float* v, size_t count,
+                             int adam_step);
 tsp_status tsp_net_forward(tsp_net net, const float* a, int batch, float* out, void* stream);
 tsp_status tsp_net_loss_grad(tsp_net net, const float* a, const float* target, int batch, double* loss, void* stream);
 tsp_status tsp_net_adam(tsp_net net, float lr, float beta1, float beta2, float eps, float weight_decay, void* stream);

@@ -63,6 +63,8 @@ SIGNATURES = {
     "tsp_segments_export": (_I, [_P, _P, _P, _P]),
     "tsp_segments_export_transposed": (_I, [_P, _P, _P, _P]),
     "tsp_segments_sirt_weights": (_I, [_P, _P, _P, _P]),
+    "tsp_debug_fail_allocation": (_I, [_I64]),
+    "tsp_debug_allocation_count": (_I, [_I64P]),
     "tsp_segments_forward": (_I, [_P, _P, _P, _I, _P]),
     "tsp_segments_adjoint": (_I, [_P, _P, _P, _I, _I, _P]),
     "tsp_segments_sirt_workspace_bytes": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
@@ -112,6 +114,8 @@ SIGNATURES = {
     "tsp_net_set_params": (_I, [_P, _P, ctypes.c_size_t]),
     "tsp_net_get_params": (_I, [_P, _P, ctypes.c_size_t]),
     "tsp_net_get_grads": (_I, [_P, _P, ctypes.c_size_t]),
+    "tsp_net_get_state": (_I, [_P, _P, _P, _P, ctypes.c_size_t, _IP]),
+    "tsp_net_set_state": (_I, [_P, _P, _P, _P, ctypes.c_size_t, _I]),
     "tsp_net_forward": (_I, [_P, _P, _I, _P, _P]),
     "tsp_net_loss_grad": (_I, [_P, _P, _P, _I, ctypes.POINTER(ctypes.c_double), _P]),
     "tsp_net_adam": (_I, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),

@@ -305,6 +305,7 @@ extern "C" tsp_status tsp_atten_optical_depth_adjoint(tsp_grid grid, tsp_geom su
 
 extern "C" tsp_status tsp_atten_forward(tsp_grid grid, tsp_geom geom, const float* rho, const float* sigma,
                                         const float* tau1, float* y, int batch, void* stream) {
+  TSP_RANGE("tsp_atten_forward");
   tsp_status st = check_trace_args(grid, geom, rho, y, batch, nullptr, "tsp_atten_forward");
   if (st != TSP_OK) return st;
   if (!sigma || !tau1) return fail(TSP_EINVAL, "tsp_atten_forward: NULL array");
@@ -325,6 +326,7 @@ extern "C" tsp_status tsp_atten_forward(tsp_grid grid, tsp_geom geom, const floa
 extern "C" tsp_status tsp_atten_backward(tsp_grid grid, tsp_geom geom, const float* rho, const float* sigma,
                                          const float* tau1, const float* y, const float* gy, float* g_rho,
                                          float* g_sigma, float* g_tau1, int batch, int accumulate, void* stream) {
+  TSP_RANGE("tsp_atten_backward");
   tsp_status st = check_trace_args(grid, geom, gy, g_rho, batch, nullptr, "tsp_atten_backward");
   if (st != TSP_OK) return st;
   if (!rho || !sigma || !tau1 || !y) return fail(TSP_EINVAL, "tsp_atten_backward: NULL array");

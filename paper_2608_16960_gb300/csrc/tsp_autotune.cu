@@ -53,6 +53,7 @@ using namespace tsp;
 
 extern "C" tsp_status tsp_autotune(tsp_grid grid, tsp_geom geom, tsp_launch* fwd_out, tsp_launch* adj_out,
                                    void* stream) {
+  TSP_RANGE("tsp_autotune");
   tsp_status st = check_trace_args(grid, geom, grid, geom, 1, nullptr, "tsp_autotune");
   if (st != TSP_OK) return st;
   cudaStream_t cs = static_cast<cudaStream_t>(stream);

@@ -371,6 +371,7 @@ static tsp_status check_ws(tsp_batch b, int n_iter, int flags, void* ws, size_t 
 }
 
 extern "C" tsp_status tsp_batch_sirt(tsp_batch b, int n_iter, int flags, void* ws, size_t bytes, void* stream) {
+  TSP_RANGE("tsp_batch_sirt");
   tsp_status st = check_ws(b, n_iter, flags, ws, bytes, "tsp_batch_sirt");
   if (st != TSP_OK) return st;
   return enqueue_batch(b, n_iter, flags, ws, static_cast<cudaStream_t>(stream));

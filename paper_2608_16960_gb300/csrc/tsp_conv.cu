@@ -1397,6 +1397,35 @@ extern "C" tsp_status tsp_net_get_params(tsp_net n, float* host, size_t count) {
   return TSP_OK;
 }
 
+extern "C" tsp_status tsp_net_get_state(tsp_net n, float* params, float* m, float* v, size_t count,
+                                        int* adam_step) {
+  if (!n || !params || !m || !v || !adam_step || count != n->n_params)
+    return fail(TSP_EINVAL, "tsp_net_get_state: bad argument");
+  tsp_status st = check_device(n->device);
+  if (st != TSP_OK) return st;
+  TSP_CUDA(cudaDeviceSynchronize());  // Adam steps enqueued on any stream have landed
+  TSP_CUDA(cudaMemcpy(params, n->params, sizeof(float) * count, cudaMemcpyDeviceToHost));
+  TSP_CUDA(cudaMemcpy(m, n->m, sizeof(float) * count, cudaMemcpyDeviceToHost));
+  TSP_CUDA(cudaMemcpy(v, n->v, sizeof(float) * count, cudaMemcpyDeviceToHost));
+  *adam_step = n->adam_step;
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_net_set_state(tsp_net n, const float* params, const float* m, const float* v,
+                                        size_t count, int adam_step) {
+  if (!n || !params || !m || !v || count != n->n_params || adam_step < 0)
+    return fail(TSP_EINVAL, "tsp_net_set_state: bad argument");
+  tsp_status st = check_device(n->device);
+  if (st != TSP_OK) return st;
+  TSP_CUDA(cudaDeviceSynchronize());  // no kernel of an earlier call still reads the old state
+  TSP_CUDA(cudaMemcpy(n->params, params, sizeof(float) * count, cudaMemcpyHostToDevice));
+  TSP_CUDA(cudaMemcpy(n->m, m, sizeof(float) * count, cudaMemcpyHostToDevice));
+  TSP_CUDA(cudaMemcpy(n->v, v, sizeof(float) * count, cudaMemcpyHostToDevice));
+  n->adam_step = adam_step;
+  n->prepared = false;
+  return TSP_OK;
+}
+
 extern "C" tsp_status tsp_net_get_grads(tsp_net n, float* host, size_t count) {
   if (!n || !host || count != n->n_params) return fail(TSP_EINVAL, "tsp_net_get_grads: bad argument");
   TSP_CUDA(cudaMemcpy(host, n->grads, sizeof(float) * count, cudaMemcpyDeviceToHost));
@@ -1404,6 +1433,7 @@ extern "C" tsp_status tsp_net_get_grads(tsp_net n, float* host, size_t count) {
 }
 
 extern "C" tsp_status tsp_net_forward(tsp_net n, const float* a, int batch, float* out, void* stream) {
+  TSP_RANGE("tsp_net_forward");
   if (!n || !a || !out || batch <= 0 || batch > n->max_batch) return fail(TSP_EINVAL, "tsp_net_forward: bad argument");
   tsp_status st = check_device(n->device);
   if (st != TSP_OK) return st;
@@ -1446,6 +1476,7 @@ void thin_wgrad(tsp_net n, int mode, const Dims& db, float* dw, float* dbias, in
 
 extern "C" tsp_status tsp_net_loss_grad(tsp_net n, const float* a, const float* target, int batch, double* loss_host,
                                         void* stream) {
+  TSP_RANGE("tsp_net_loss_grad");
   if (!n || !a || !target || batch <= 0 || batch > n->max_batch)
     return fail(TSP_EINVAL, "tsp_net_loss_grad: bad argument");
   tsp_status st = check_device(n->device);
@@ -1485,6 +1516,7 @@ extern "C" tsp_status tsp_net_loss_grad(tsp_net n, const float* a, const float* 
 
 extern "C" tsp_status tsp_net_adam(tsp_net n, float lr, float beta1, float beta2, float eps, float weight_decay,
                                    void* stream) {
+  TSP_RANGE("tsp_net_adam");
   if (!n) return fail(TSP_EINVAL, "tsp_net_adam: NULL net");
   n->adam_step += 1;
   n->prepared = false;

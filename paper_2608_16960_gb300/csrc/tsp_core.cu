@@ -1,4 +1,5 @@
 // Handles, validation and error reporting of the C ABI (include/tsp.h).
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -21,7 +22,28 @@ tsp_status fail(tsp_status st, const std::string& msg) {
 
 tsp_status cuda_fail(cudaError_t e, const char* what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // not sticky: clear it so the context stays usable
+    return TSP_ENOMEM;
+  }
   return TSP_ECUDA;
+}
+
+namespace {
+std::atomic<long long> g_fail_alloc{-1};  // allocations left before the injected failure (-1: none)
+std::atomic<long long> g_alloc_count{0};  // allocations made through dev_malloc_raw
+}  // namespace
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+  g_alloc_count.fetch_add(1);
+  long long c = g_fail_alloc.load();
+  while (c >= 0 && !g_fail_alloc.compare_exchange_weak(c, c - 1)) {
+  }
+  if (c == 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
 }
 
 tsp_status check_device(int device) {
@@ -502,4 +524,15 @@ extern "C" void tsp_geom_destroy(tsp_geom g) {
   if (g->d_views) cudaFree(g->d_views);
   if (g->owned) cudaFree(g->owned);
   delete g;
+}
+
+extern "C" tsp_status tsp_debug_fail_allocation(int64_t after) {
+  tsp::g_fail_alloc.store(after < 0 ? -1 : (long long)after);
+  return TSP_OK;
+}
+
+extern "C" tsp_status tsp_debug_allocation_count(int64_t* count) {
+  if (!count) return fail(TSP_EINVAL, "tsp_debug_allocation_count: count is NULL");
+  *count = (int64_t)tsp::g_alloc_count.load();
+  return TSP_OK;
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstdint>
@@ -92,6 +93,24 @@ inline tsp_launch default_launch() {
   l.warp_tile_w = 8;
   l.scatter = 0;
   return l;
+}
+
+// NVTX range over one library call: it names the call's kernels in a
+// profiler's timeline and costs nothing measurable when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define TSP_RANGE(name) const tsp::NvtxRange tsp_nvtx_range_(name)
+
+// cudaMalloc with the test hook of tsp_debug_fail_allocation (one injected
+// out-of-memory failure after a countdown); used by the stored-list code.
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+template <class T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc_raw(reinterpret_cast<void**>(p), bytes);
 }
 
 }  // namespace tsp

@@ -98,6 +98,7 @@ using namespace tsp;
 
 extern "C" tsp_status tsp_forward_ex(tsp_grid grid, tsp_geom geom, const float* rho, float* y, int batch,
                                      const tsp_launch* launch, void* stream) {
+  TSP_RANGE("tsp_forward_ex");
   tsp_status st = check_trace_args(grid, geom, rho, y, batch, launch, "tsp_forward");
   if (st != TSP_OK) return st;
   const tsp_launch l = launch ? *launch : preferred_launch(grid, geom, false);
@@ -123,6 +124,7 @@ extern "C" tsp_status tsp_forward(tsp_grid grid, tsp_geom geom, const float* rho
 
 extern "C" tsp_status tsp_adjoint_ex(tsp_grid grid, tsp_geom geom, const float* y, float* rho, int batch,
                                      int accumulate, const tsp_launch* launch, void* stream) {
+  TSP_RANGE("tsp_adjoint_ex");
   tsp_status st = check_trace_args(grid, geom, y, rho, batch, launch, "tsp_adjoint");
   if (st != TSP_OK) return st;
   const tsp_launch l = launch ? *launch : preferred_launch(grid, geom, true);
@@ -165,6 +167,7 @@ extern "C" tsp_status tsp_count_segments(tsp_grid grid, tsp_geom geom, int* coun
 }
 
 extern "C" tsp_status tsp_forward_dynamic(tsp_grid grid, tsp_geom geom, const float* rho, float* y, void* stream) {
+  TSP_RANGE("tsp_forward_dynamic");
   tsp_status st = check_trace_args(grid, geom, rho, y, 1, nullptr, "tsp_forward_dynamic");
   if (st != TSP_OK) return st;
   const tsp_launch l = preferred_launch(grid, geom, false);
@@ -180,6 +183,7 @@ extern "C" tsp_status tsp_forward_dynamic(tsp_grid grid, tsp_geom geom, const fl
 
 extern "C" tsp_status tsp_adjoint_dynamic(tsp_grid grid, tsp_geom geom, const float* y, float* rho, int accumulate,
                                           void* stream) {
+  TSP_RANGE("tsp_adjoint_dynamic");
   tsp_status st = check_trace_args(grid, geom, y, rho, 1, nullptr, "tsp_adjoint_dynamic");
   if (st != TSP_OK) return st;
   const tsp_launch l = preferred_launch(grid, geom, true);

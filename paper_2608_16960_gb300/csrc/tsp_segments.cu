@@ -618,14 +618,14 @@ tsp_status finish_list(SegList& l, int* tmp, int64_t* pos, cudaStream_t st) {
   if (r != TSP_OK) return r;
   TSP_CUDA(cudaMemcpyAsync(&l.n_nz, pos + l.n_rows, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   TSP_CUDA(cudaStreamSynchronize(st));
-  TSP_CUDA(cudaMalloc(&l.nz, sizeof(uint32_t) * size_t(l.n_nz > 0 ? l.n_nz : 1)));
+  TSP_CUDA(dev_malloc(&l.nz, sizeof(uint32_t) * size_t(l.n_nz > 0 ? l.n_nz : 1)));
   nonempty_ids_kernel<<<rb, 256, 0, st>>>(l.off, pos, l.n_rows, l.nz);
   l.n_tiles = (l.S + TILE - 1) / TILE;
   const size_t nt = size_t(l.n_tiles > 0 ? l.n_tiles : 1);
-  TSP_CUDA(cudaMalloc(&l.tile_base, sizeof(int64_t) * (nt + 1)));
-  TSP_CUDA(cudaMalloc(&l.carry, sizeof(float) * nt));
-  TSP_CUDA(cudaMalloc(&l.headless, nt));
-  TSP_CUDA(cudaMalloc(&l.open_row, sizeof(uint32_t) * nt));
+  TSP_CUDA(dev_malloc(&l.tile_base, sizeof(int64_t) * (nt + 1)));
+  TSP_CUDA(dev_malloc(&l.carry, sizeof(float) * nt));
+  TSP_CUDA(dev_malloc(&l.headless, nt));
+  TSP_CUDA(dev_malloc(&l.open_row, sizeof(uint32_t) * nt));
   if (l.n_tiles > 0) {
     tile_heads_kernel<<<unsigned((l.n_tiles * 32 + 255) / 256), 256, 0, st>>>(l.idx, l.S, l.n_tiles, tmp);
     r = exclusive_scan(tmp, l.n_tiles, l.tile_base, st);
@@ -704,6 +704,7 @@ extern "C" void tsp_segments_destroy(tsp_segments s) {
 
 extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int transpose, tsp_segments* out,
                                          void* stream) {
+  TSP_RANGE("tsp_segments_build");
   if (!out) return fail(TSP_EINVAL, "tsp_segments_build: out is NULL");
   *out = nullptr;
   tsp_status st = check_trace_args(grid, geom, grid, geom, 1, nullptr, "tsp_segments_build");
@@ -758,8 +759,8 @@ extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int trans
   SegList& f = s->fwd;
   f.n_rows = s->n_rays;
   f.n_cols = s->V;
-  SEG_TRY(cudaMalloc(&counts, sizeof(int) * size_t(s->n_rays)));
-  SEG_TRY(cudaMalloc(&f.off, sizeof(int64_t) * size_t(s->n_rays + 1)));
+  SEG_TRY(dev_malloc(&counts, sizeof(int) * size_t(s->n_rays)));
+  SEG_TRY(dev_malloc(&f.off, sizeof(int64_t) * size_t(s->n_rays + 1)));
   const tsp_launch l = preferred_launch(grid, geom, false);
   CountOnlyOp cop;
   cop.counts = counts;
@@ -771,8 +772,8 @@ extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int trans
   if (s->n_segs >= (int64_t(1) << 32)) return bail(fail(TSP_ENOTSUP, "tsp_segments_build: 2^32 or more segments"));
   f.S = s->n_segs;
   const size_t P = entries_alloc(s->n_segs);
-  SEG_TRY(cudaMalloc(&f.idx, sizeof(uint32_t) * P));
-  SEG_TRY(cudaMalloc(&f.len, sizeof(float) * P));
+  SEG_TRY(dev_malloc(&f.idx, sizeof(uint32_t) * P));
+  SEG_TRY(dev_malloc(&f.len, sizeof(float) * P));
   SEG_TRY(cudaMemsetAsync(f.idx, 0, sizeof(uint32_t) * P, cs));  // no stray head flags in unfilled slots
   FillOp fop;
   fop.off = f.off;
@@ -781,8 +782,8 @@ extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int trans
   launch_trace(grid, geom, l, fop, cs);
   SEG_TRY(cudaGetLastError());
   const int64_t rows_max = std::max<int64_t>(s->n_rays, s->V);
-  SEG_TRY(cudaMalloc(&tmp, sizeof(int) * size_t(std::max<int64_t>(rows_max, (s->n_segs + TILE - 1) / TILE + 1))));
-  SEG_TRY(cudaMalloc(&pos, sizeof(int64_t) * size_t(rows_max + 1)));
+  SEG_TRY(dev_malloc(&tmp, sizeof(int) * size_t(std::max<int64_t>(rows_max, (s->n_segs + TILE - 1) / TILE + 1))));
+  SEG_TRY(dev_malloc(&pos, sizeof(int64_t) * size_t(rows_max + 1)));
   st = finish_list(f, tmp, pos, cs);
   if (st != TSP_OK) return bail(st);
   if (transpose) {
@@ -790,10 +791,10 @@ extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int trans
     t.n_rows = s->V;
     t.n_cols = s->n_rays;
     t.S = s->n_segs;
-    SEG_TRY(cudaMalloc(&vcount, sizeof(int) * size_t(s->V)));
-    SEG_TRY(cudaMalloc(&t.off, sizeof(int64_t) * size_t(s->V + 1)));
-    SEG_TRY(cudaMalloc(&t.idx, sizeof(uint32_t) * P));
-    SEG_TRY(cudaMalloc(&t.len, sizeof(float) * P));
+    SEG_TRY(dev_malloc(&vcount, sizeof(int) * size_t(s->V)));
+    SEG_TRY(dev_malloc(&t.off, sizeof(int64_t) * size_t(s->V + 1)));
+    SEG_TRY(dev_malloc(&t.idx, sizeof(uint32_t) * P));
+    SEG_TRY(dev_malloc(&t.len, sizeof(float) * P));
     SEG_TRY(cudaMemsetAsync(vcount, 0, sizeof(int) * size_t(s->V), cs));
     SEG_TRY(cudaMemsetAsync(t.idx, 0, sizeof(uint32_t) * P, cs));
     voxel_hist_kernel<<<152 * 16, 256, 0, cs>>>(f.idx, s->n_segs, s->V, vcount);
@@ -809,14 +810,14 @@ extern "C" tsp_status tsp_segments_build(tsp_grid grid, tsp_geom geom, int trans
       while (bits < 32 && (uint64_t(s->V - 1) >> bits) != 0) ++bits;
       const int passes = (bits + RB - 1) / RB;
       const int64_t n_rt = (s->n_segs + RT - 1) / RT;
-      SEG_TRY(cudaMalloc(&rhist, sizeof(int) * size_t(RD * n_rt)));
-      SEG_TRY(cudaMalloc(&rbase, sizeof(int64_t) * size_t(RD * n_rt + 1)));
-      SEG_TRY(cudaMalloc(&rb, sizeof(uint32_t) * P));
+      SEG_TRY(dev_malloc(&rhist, sizeof(int) * size_t(RD * n_rt)));
+      SEG_TRY(dev_malloc(&rbase, sizeof(int64_t) * size_t(RD * n_rt + 1)));
+      SEG_TRY(dev_malloc(&rb, sizeof(uint32_t) * P));
       if (passes > 1) {
-        SEG_TRY(cudaMalloc(&kb, sizeof(uint32_t) * P));
-        SEG_TRY(cudaMalloc(&lb, sizeof(float) * P));
+        SEG_TRY(dev_malloc(&kb, sizeof(uint32_t) * P));
+        SEG_TRY(dev_malloc(&lb, sizeof(float) * P));
       }
-      if (passes > 2) SEG_TRY(cudaMalloc(&ka, sizeof(uint32_t) * P));
+      if (passes > 2) SEG_TRY(dev_malloc(&ka, sizeof(uint32_t) * P));
       const bool first_to_a = (passes - 1) % 2 == 0;
       uint32_t* rid = first_to_a ? rb : t.idx;
       ray_ids_kernel<<<unsigned((s->n_rays * 32 + 255) / 256), 256, 0, cs>>>(f.off, s->n_rays, rid);
@@ -900,6 +901,7 @@ extern "C" tsp_status tsp_segments_export_transposed(tsp_segments s, int64_t* vo
 }
 
 extern "C" tsp_status tsp_segments_forward(tsp_segments s, const float* rho, float* y, int batch, void* stream) {
+  TSP_RANGE("tsp_segments_forward");
   if (!s || !rho || !y || batch <= 0) return fail(TSP_EINVAL, "tsp_segments_forward: bad argument");
   tsp_status st = check_device(s->device);
   if (st != TSP_OK) return st;
@@ -908,6 +910,7 @@ extern "C" tsp_status tsp_segments_forward(tsp_segments s, const float* rho, flo
 
 extern "C" tsp_status tsp_segments_adjoint(tsp_segments s, const float* y, float* rho, int batch, int accumulate,
                                            void* stream) {
+  TSP_RANGE("tsp_segments_adjoint");
   if (!s || !y || !rho || batch <= 0) return fail(TSP_EINVAL, "tsp_segments_adjoint: bad argument");
   tsp_status st = check_device(s->device);
   if (st != TSP_OK) return st;
@@ -959,6 +962,7 @@ extern "C" tsp_status tsp_segments_sirt_weights(tsp_segments s, float* R, float*
 
 extern "C" tsp_status tsp_segments_sirt(tsp_segments s, const float* y, float* x, int n_iter, int flags,
                                         void* workspace, size_t workspace_bytes, void* stream) {
+  TSP_RANGE("tsp_segments_sirt");
   if (!s || !y || !x || !workspace) return fail(TSP_EINVAL, "tsp_segments_sirt: NULL argument");
   if (n_iter < 0) return fail(TSP_EINVAL, "tsp_segments_sirt: n_iter < 0");
   if (flags & ~(TSP_SIRT_NONNEG | TSP_SIRT_REUSE_WEIGHTS)) return fail(TSP_EINVAL, "tsp_segments_sirt: unknown flags");
@@ -1003,6 +1007,7 @@ extern "C" tsp_status tsp_segments_sirt(tsp_segments s, const float* y, float* x
 // ---------------------------------------------------------------------------
 extern "C" tsp_status tsp_sirt_chunked(const tsp_batch_item* items, int n_items, int n_iter, int flags,
                                        size_t budget_bytes, int* n_chunks, size_t* peak_bytes, void* stream) {
+  TSP_RANGE("tsp_sirt_chunked");
   if (!items || n_items <= 0) return fail(TSP_EINVAL, "tsp_sirt_chunked: no items");
   if (n_iter < 0) return fail(TSP_EINVAL, "tsp_sirt_chunked: n_iter < 0");
   if (flags & ~TSP_SIRT_NONNEG) return fail(TSP_EINVAL, "tsp_sirt_chunked: unknown flags");
@@ -1032,7 +1037,7 @@ extern "C" tsp_status tsp_sirt_chunked(const tsp_batch_item* items, int n_items,
         if (ws) cudaFree(ws);
         ws = nullptr;
         ws_bytes = 0;
-        cudaError_t e = cudaMalloc(&ws, need);
+        cudaError_t e = dev_malloc(&ws, need);
         if (e != cudaSuccess) return cuda_fail(e, "tsp_sirt_chunked: workspace");
         ws_bytes = need;
       }

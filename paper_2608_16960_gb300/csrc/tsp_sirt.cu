@@ -176,6 +176,7 @@ extern "C" tsp_status tsp_sirt_workspace_bytes(tsp_grid grid, tsp_geom geom, siz
 extern "C" tsp_status tsp_sirt(tsp_grid grid, tsp_geom geom, const float* y, float* x, int n_iter, int flags,
                                void* workspace, size_t workspace_bytes_given, const tsp_launch* launch,
                                void* stream) {
+  TSP_RANGE("tsp_sirt");
   tsp_status st = check_trace_args(grid, geom, y, x, 1, launch, "tsp_sirt");
   if (st != TSP_OK) return st;
   if (n_iter < 0) return fail(TSP_EINVAL, "tsp_sirt: n_iter must be >= 0");

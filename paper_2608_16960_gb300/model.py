@@ -250,6 +250,23 @@ class WarmStartNet:
               "tsp_net_get_params")
         return out
 
+    def get_state(self) -> dict:
+        """Training state for a checkpoint: params, Adam moments m and v, step."""
+        f = [np.zeros(self.n_params, np.float32) for _ in range(3)]
+        step = ctypes.c_int()
+        vp = lambda a: ctypes.c_void_p(a.ctypes.data)
+        check(_lib.load().tsp_net_get_state(self.handle, vp(f[0]), vp(f[1]), vp(f[2]), self.n_params,
+                                            ctypes.byref(step)), "tsp_net_get_state")
+        return {"params": f[0], "m": f[1], "v": f[2], "adam_step": step.value}
+
+    def set_state(self, state: dict):
+        """Restore a state from get_state: training continues bit for bit."""
+        f = [np.ascontiguousarray(state[k], dtype=np.float32) for k in ("params", "m", "v")]
+        vp = lambda a: ctypes.c_void_p(a.ctypes.data)
+        check(_lib.load().tsp_net_set_state(self.handle, vp(f[0]), vp(f[1]), vp(f[2]), f[0].size,
+                                            int(state["adam_step"])), "tsp_net_set_state")
+        self.version += 1
+
     def get_grads(self) -> np.ndarray:
         out = np.zeros(self.n_params, np.float32)
         check(_lib.load().tsp_net_get_grads(self.handle, ctypes.c_void_p(out.ctypes.data), out.size),

@@ -103,12 +103,16 @@ class WarmStart:
         return a, t, y, rho, scale
 
     # ---- training -----------------------------------------------------------
-    def train(self, n_samples, batch=8, lr=1e-3, seed0=1000, log_every=0, cosine=True):
+    def train(self, n_samples, batch=8, lr=1e-3, seed0=1000, log_every=0, cosine=True, start_step=0,
+              stop_step=None):
         """Adam on fresh phantoms, `batch` per step; with cosine=True the step
-        size decays from lr to lr / 20 along a half cosine."""
+        size decays from lr to lr / 20 along a half cosine over the whole run.
+        Steps start_step .. stop_step - 1 of the run are taken (a run split at
+        a checkpoint takes the same steps, on the same phantoms, with the same
+        step sizes as an uninterrupted one)."""
         losses = []
         steps = (n_samples + batch - 1) // batch
-        for s in range(steps):
+        for s in range(start_step, steps if stop_step is None else min(stop_step, steps)):
             seeds = [seed0 + s * batch + i for i in range(batch)]
             a, t, _, _, _ = self.batch(seeds)
             losses.append(self.net.loss_grad(a, t))
@@ -117,6 +121,21 @@ class WarmStart:
             if log_every and s % log_every == 0:
                 print(f"step {s}/{steps} loss {losses[-1]:.4e}", flush=True)
         return losses
+
+    # ---- checkpoint / resume ----------------------------------------------------
+    def save_checkpoint(self, path, next_step):
+        """Network parameters, Adam state and the next training step to `path` (.npz)."""
+        st = self.net.get_state()
+        np.savez(path, params=st["params"], m=st["m"], v=st["v"], adam_step=np.int64(st["adam_step"]),
+                 next_step=np.int64(next_step), shape=np.array(self.shape, np.int64))
+
+    def load_checkpoint(self, path):
+        """Restore a checkpoint of save_checkpoint; returns the step to resume at."""
+        with np.load(path) as z:
+            if tuple(int(x) for x in z["shape"]) != self.shape:
+                raise ValueError(f"checkpoint for grid {tuple(z['shape'])}, this warm start has {self.shape}")
+            self.net.set_state({"params": z["params"], "m": z["m"], "v": z["v"], "adam_step": int(z["adam_step"])})
+            return int(z["next_step"])
 
     # ---- reconstruction -------------------------------------------------------
     def rel_error(self, x, truth):

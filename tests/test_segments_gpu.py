@@ -293,3 +293,78 @@ def test_transposed_export_needs_the_transpose():
     geom = Geometry.cone(synth.circular_orbit(1, 60.0), (16, 16), 45.0)
     with pytest.raises(TspError, match="without the transpose"):
         Segments(grid, geom, transpose=False).export_transposed()
+
+
+def _alloc_count():
+    import ctypes
+    from paper_2608_16960_gb300._lib import check, load
+    n = ctypes.c_int64()
+    check(load().tsp_debug_allocation_count(ctypes.byref(n)), "tsp_debug_allocation_count")
+    return n.value
+
+
+def test_build_out_of_memory_at_every_allocation_is_reported_and_recovered():
+    """The failure is made on the host (the allocation hook returns
+    out-of-memory without touching the device): whichever allocation of the
+    build fails, the build returns TSP_ENOMEM, frees what it holds, and the
+    next build succeeds with the same results."""
+    from paper_2608_16960_gb300._lib import load
+    e = synth.grid_edges(10, 8, 12)
+    grid = Grid.from_edges(e)
+    geom = Geometry.cone(synth.circular_orbit(2, 60.0), (24, 24), 40.0)
+    rho = torch.tensor(synth.blob_phantom(e, 5), device=DEV)
+    n0 = _alloc_count()
+    ref = Segments(grid, geom, transpose=True)
+    n_build = _alloc_count() - n0
+    assert n_build >= 10
+    y_ref = ref.forward(rho)
+    free0 = torch.cuda.mem_get_info()[0]
+    L = load()
+    try:
+        for k in range(n_build):
+            assert L.tsp_debug_fail_allocation(k) == 0
+            with pytest.raises(TspError) as ei:
+                Segments(grid, geom, transpose=True)
+            assert ei.value.status == 3, (k, str(ei.value))  # TSP_ENOMEM
+            assert torch.equal(Segments(grid, geom, transpose=True).forward(rho), y_ref)
+    finally:
+        L.tsp_debug_fail_allocation(-1)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)  # nothing of the failed builds is held
+    assert tsp_device_status() == 0
+
+
+def test_chunked_sirt_finishes_the_chunk_and_retries_after_out_of_memory():
+    """An out-of-memory failure while building the third item's lists: the
+    chunked driver runs the two items it holds, frees their lists and builds
+    the third again; every item ends bit-identical to the run without the
+    failure, in one more chunk."""
+    from paper_2608_16960_gb300._lib import load
+    from paper_2608_16960_gb300.projector import sirt_chunked
+    items = []
+    for k in range(4):
+        e = synth.grid_edges(8 + 2 * k, 6 + k, 12 + 4 * k)
+        grid = Grid.from_edges(e)
+        geom = Geometry.cone(synth.circular_orbit(3 + k, 60.0, incline_deg=10.0 * k), (24, 24), 40.0)
+        y = tsp_forward(grid, geom, torch.tensor(synth.blob_phantom(e, seed=700 + k), device=DEV))
+        items.append((grid, geom, y))
+    per_item = []
+    for grid, geom, _ in items:
+        n0 = _alloc_count()
+        Segments(grid, geom, transpose=True)
+        per_item.append(_alloc_count() - n0)
+    runs = []
+    L = load()
+    for fail_at in (None, per_item[0] + per_item[1] + 2):
+        xs = [(g, m, y, torch.zeros(g.shape, device=DEV)) for g, m, y in items]
+        try:
+            if fail_at is not None:
+                assert L.tsp_debug_fail_allocation(fail_at) == 0
+            chunks, _ = sirt_chunked(xs, 5, nonneg=True, budget_bytes=1 << 40)
+        finally:
+            L.tsp_debug_fail_allocation(-1)
+        runs.append((chunks, [x for _, _, _, x in xs]))
+    assert runs[0][0] == 1 and runs[1][0] == 2
+    for a, b in zip(runs[0][1], runs[1][1]):
+        assert torch.equal(a, b)
+    assert tsp_device_status() == 0

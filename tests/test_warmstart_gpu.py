@@ -134,3 +134,29 @@ def test_training_from_lists_repeats_bit_for_bit():
         runs.append((losses, w.warm_start(y).cpu()))
     assert runs[0][0] == runs[1][0]
     assert torch.equal(runs[0][1], runs[1][1])
+
+
+def test_checkpoint_resume_continues_bit_for_bit(tmp_path):
+    """A training run split at a checkpoint (network, Adam moments and step
+    count saved to disk, restored into a fresh warm start) takes the same
+    steps as an uninterrupted run: identical losses and final weights."""
+    e = synth.grid_edges(12, 10, 32)
+    pos = synth.circular_orbit(12, 60.0, incline_deg=35.0)
+    kw = dict(batch=4, lr=2e-3, seed0=600)
+    whole = WarmStart(e, pos, 32, 50.0, max_batch=4, use_lists=True)
+    l_whole = whole.train(40, **kw)
+    first = WarmStart(e, pos, 32, 50.0, max_batch=4, use_lists=True)
+    l_a = first.train(40, stop_step=4, **kw)
+    path = tmp_path / "ws.npz"
+    first.save_checkpoint(path, next_step=4)
+    second = WarmStart(e, pos, 32, 50.0, max_batch=4, use_lists=True)
+    start = second.load_checkpoint(path)
+    assert start == 4
+    l_b = second.train(40, start_step=start, **kw)
+    assert l_a + l_b == l_whole
+    sw, s2 = whole.net.get_state(), second.net.get_state()
+    assert sw["adam_step"] == s2["adam_step"] == 10
+    for k in ("params", "m", "v"):
+        assert np.array_equal(sw[k], s2[k]), k
+    with pytest.raises(ValueError, match="checkpoint for grid"):
+        WarmStart(synth.grid_edges(8, 10, 32), pos, 32, 50.0, max_batch=4).load_checkpoint(path)
