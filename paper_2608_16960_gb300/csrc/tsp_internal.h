@@ -62,10 +62,6 @@ tsp_status fail(tsp_status st, const std::string& msg);
 tsp_status cuda_fail(cudaError_t e, const char* what);
 tsp_status check_device(int device);
 
-// Host construction of a grid's shared-memory table (no CUDA calls).
-void build_grid_table(const double* r_edges, int n_r_edges, const double* theta_edges, int n_theta_edges,
-                      const double* phi_edges, int n_phi_edges, std::vector<float>* table, tsp_grid_s* g);
-
 // Autotuner cache lookup (tsp_autotune.cu).
 bool tuned_launch(const tsp_grid_s* grid, const tsp_geom_s* geom, tsp_launch* fwd, tsp_launch* adj);
 

@@ -120,11 +120,13 @@ TSP_HD TGrid tgrid_from_smem(const GridDesc& d, const float* s) {
   return g;
 }
 
+#if defined(__CUDACC__)
 // Cooperative copy of the grid table into shared memory (whole block).
 __device__ __forceinline__ void load_table(const GridDesc& d, float* s) {
   for (int i = threadIdx.x; i < d.words; i += blockDim.x) s[i] = __ldg(d.table + i);
   __syncthreads();
 }
+#endif
 
 // ---- classification of one point (only at the ray's first in-grid point) ----
 
@@ -433,10 +435,18 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d[3], Op& op) {
   s.sec = classify_sector(G, px, py);
   float t_ax = INFINITY;
   int sec_ax = 0;
-  if (s.mz != 0.0f) {
+  // A line whose distance from the z axis, |m_z| / |n_xy|, is below 2^-20 of
+  // the start's size meets the axis as far as float32 rays can tell: rounding
+  // the inputs moves a line through the axis by about that much. Walking its
+  // azimuth plane by plane would hinge on half-plane tests that see only
+  // rounding noise for the plane the line lies in (and could stop the sweep
+  // past the axis); taking the jump instead moves at most that distance of
+  // path between neighbouring sectors.
+  const float nxy = fmaf(s.nx, s.nx, T_MUL(s.ny, s.ny));
+  const float xsz = T_ADD(T_ADD(fabsf(xx), fabsf(xy)), fabsf(xz));
+  if (fabsf(s.mz) > T_MUL(T_MUL(0x1p-20f, T_SQRT(nxy)), xsz)) {
     s.ph_mode = 0;
   } else {
-    const float nxy = fmaf(s.nx, s.nx, T_MUL(s.ny, s.ny));
     if (nxy > 0.0f) {  // the line meets the z axis: azimuth jumps by pi there
       t_ax = -T_DIV(fmaf(s.qx, s.nx, T_MUL(s.qy, s.ny)), nxy);
       s.ph_mode = t_ax > tcur ? 2 : 1;

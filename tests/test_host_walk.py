@@ -1,0 +1,195 @@
+"""The library's per-ray walk (tsp_trace.cuh over the library's boundary table,
+tsp_table.h), built for the host, against the FP64 oracle on the CPU.
+
+- Line integrals (Eq. 5) of random rays on full, wedge and hollow grids, with
+  starts outside and inside, meet the parity rule of tests/_util.py.
+- The degenerate families of Sec. 5.1 meet it too: rays through the origin,
+  along and parallel to the axis, and grazing a sphere. Rays in the
+  equatorial plane or in a half-plane match the oracle for the ray or for
+  the ray moved just off that surface.
+- Voxel sequences equal the oracle's (Eq. 4) wherever no two crossings lie
+  within float32 reach of each other.
+
+No GPU: this checks the walk's index logic wherever the driver runs the CPU
+tests. Its host build rounds divisions and square roots correctly, so lengths
+differ from the GPU's in the last bits; the GPU itself is checked by the
+`gpu` tests."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2608_16960_gb300 import synth
+
+from _util import parity
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_2608_16960_gb300", "csrc")
+BUILD = os.path.join(HERE, "_build")
+SO = os.path.join(BUILD, "libhostwalk.so")
+SRCS = [os.path.join(HERE, "host_walk.cpp"), os.path.join(CSRC, "tsp_trace.cuh"), os.path.join(CSRC, "tsp_table.h"),
+        os.path.join(CSRC, "tsp_internal.h"), os.path.join(ROOT, "include", "tsp.h")]
+CUDA_INC = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+
+
+def _lib():
+    if shutil.which("g++") is None or not os.path.isdir(CUDA_INC):
+        pytest.skip("g++ or the CUDA headers are not available")
+    os.makedirs(BUILD, exist_ok=True)
+    if not os.path.exists(SO) or os.path.getmtime(SO) < max(os.path.getmtime(s) for s in SRCS):
+        tmp = SO + f".{os.getpid()}.tmp"
+        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-I" + CUDA_INC,
+                        "-I" + CSRC, SRCS[0], "-o", tmp], check=True)
+        os.replace(tmp, SO)
+    L = ctypes.CDLL(SO)
+    P = ctypes.c_void_p
+    L.host_walk.restype = ctypes.c_int
+    L.host_walk.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, ctypes.c_long, P, P, ctypes.c_int, P, P,
+                            P]
+    return L
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _lib()
+
+
+def walk(lib, edges, starts, dirs, cap=1024):
+    """Segments of rays given as float32 (n, 3) starts and directions."""
+    r, t, p = [np.ascontiguousarray(a, np.float64) for a in (edges.r, edges.theta, edges.phi)]
+    x = np.ascontiguousarray(starts, np.float32)
+    d = np.ascontiguousarray(dirs, np.float32)
+    n = len(x)
+    vox = np.zeros((n, cap), np.int32)
+    ln = np.zeros((n, cap), np.float32)
+    cnt = np.zeros(n, np.int32)
+    bad = lib.host_walk(r.ctypes.data, len(r), t.ctypes.data, len(t), p.ctypes.data, len(p), n, x.ctypes.data,
+                        d.ctypes.data, cap, vox.ctypes.data, ln.ctypes.data, cnt.ctypes.data)
+    assert bad == 0
+    assert cnt.max(initial=0) <= cap
+    return vox, ln, cnt
+
+
+def forward(lib, edges, starts, dirs, rho):
+    vox, ln, cnt = walk(lib, edges, starts, dirs)
+    flat = rho.reshape(-1).astype(np.float64)
+    mask = np.arange(vox.shape[1])[None, :] < cnt[:, None]
+    return np.where(mask, flat[np.where(mask, vox, 0)] * ln.astype(np.float64), 0.0).sum(axis=1)
+
+
+GRIDS = {
+    "paper": lambda: synth.grid_edges(100, 60, 120),
+    "wedge": lambda: synth.GridEdges(np.linspace(1.0, 2.0, 11), np.linspace(0.3, 2.0, 18),
+                                     np.linspace(0.2, 2.5, 21)),
+    "hollow-free": lambda: synth.GridEdges(np.array([0.0, 1.0, 2.0, 5.0, 25.0]),
+                                           np.array([0.0, 0.5, np.pi / 2, 2.5, np.pi]),
+                                           np.linspace(-np.pi, np.pi, 4)),
+    "polar-cap": lambda: synth.GridEdges(np.linspace(0.5, 3.0, 6), np.linspace(0.1, 1.2, 7),
+                                         np.linspace(0.0, 2 * np.pi, 9)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GRIDS))
+def test_forward_parity_random_rays(lib, name):
+    e = GRIDS[name]()
+    R = float(e.r[-1])
+    rho = synth.uniform_volume(e.shape, 5, 0.1, 1.0)
+    s1, d1 = synth.random_rays(1500, 11, start_radius=2.4 * R, aim_radius=R)
+    s2, d2 = synth.interior_rays(500, 12, radius=0.9 * R)
+    st = np.concatenate([s1.T, s2.T])
+    di = np.concatenate([d1.T, d2.T])
+    y = forward(lib, e, st, di, rho)
+    ref = oracle.forward(e, st.astype(np.float64), di.astype(np.float64), rho)
+    parity(y, ref, what=f"host walk {name}")
+    assert np.linalg.norm(y - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
+def _close(y, candidates, big):
+    return min(abs(y - c) for c in candidates) <= 1e-4 * max(max(abs(c) for c in candidates), 1e-2 * big)
+
+
+def test_degenerate_rays(lib):
+    """Rays through the origin, parallel to and along the axis, grazing a
+    sphere: the parity rule. Rays lying in a boundary surface (the equatorial
+    cone theta = pi/2, an azimuth half-plane) may be attributed to either
+    neighbouring voxel: they must match the oracle for the ray itself or for
+    the ray moved just off the surface (shifted to either side, or turned
+    either way about the axis, which moves both halves of a ray through the
+    axis to the same rotational side)."""
+    e = synth.grid_edges(20, 15, 30)
+    rho = synth.uniform_volume(e.shape, 6, 0.1, 1.0)
+    R = float(e.r[-1])
+    rng = np.random.default_rng(3)
+    plain, on_surface = [], []
+    for _ in range(40):
+        v = rng.normal(size=3)
+        v /= np.linalg.norm(v)
+        plain.append((2.0 * R * v, -v))                                                  # through the origin
+        off = rng.uniform(-R, R, size=2)
+        plain.append((np.array([off[0], off[1], 2.0 * R]), np.array([0.0, 0.0, -1.0])))  # parallel to the axis
+        k = rng.integers(1, len(e.r))
+        plain.append((np.array([-2.0 * R, float(e.r[k]) * (1 - 1e-7), 0.3]), np.array([1.0, 0.0, 0.0])))  # grazing
+        a = rng.uniform(0, 2 * np.pi)
+        on_surface.append((np.array([2.0 * R * np.cos(a), 2.0 * R * np.sin(a), 0.0]),
+                           np.array([-np.cos(a + 0.3), -np.sin(a + 0.3), 0.0]), np.array([0.0, 0.0, 1.0])))
+        p = e.phi[rng.integers(0, len(e.phi) - 1)]
+        u = np.array([np.cos(p), np.sin(p), 0.0])
+        on_surface.append((2 * R * u + rng.uniform(-R, R) * np.array([0.0, 0.0, 1.0]), -u + np.array([0, 0, 0.1]),
+                           np.array([-np.sin(p), np.cos(p), 0.0])))
+    plain.append((np.array([0.0, 0.0, 2.0 * R]), np.array([0.0, 0.0, -1.0])))          # along the axis
+    st = np.array([a for a, _ in plain], np.float32)
+    di = np.array([b for _, b in plain], np.float32)
+    y = forward(lib, e, st, di, rho)
+    ref = oracle.forward(e, st.astype(np.float64), di.astype(np.float64), rho)
+    parity(y, ref, what="host walk degenerate rays")
+    st = np.array([a for a, _, _ in on_surface], np.float32)
+    di = np.array([b for _, b, _ in on_surface], np.float32)
+    y = forward(lib, e, st, di, rho)
+    # The rays as given, and the exact surface rays they round (built in
+    # float64 in the surface) moved off it by 1e-9: shifted across it, or
+    # turned about z. A half-plane ray crosses the axis into the opposite
+    # half-plane, and its two halves may each fall on either side: a shift
+    # puts them on opposite sides, a turn on the same side.
+    s64 = np.array([a for a, _, _ in on_surface])
+    d64 = np.array([b for _, b, _ in on_surface])
+    nrm = np.array([n for _, _, n in on_surface])
+    cands = [oracle.forward(e, st.astype(np.float64), di.astype(np.float64), rho)]
+    cands += [oracle.forward(e, s64 + h * nrm, d64, rho) for h in (1e-9, -1e-9)]
+    for ang in (1e-9, -1e-9):
+        c, sn = np.cos(ang), np.sin(ang)
+        rot = np.array([[c, -sn, 0.0], [sn, c, 0.0], [0.0, 0.0, 1.0]])
+        cands.append(oracle.forward(e, s64 @ rot.T, d64 @ rot.T, rho))
+    big = max(np.max(np.abs(c)) for c in cands)
+    bad = [i for i in range(len(y)) if not _close(y[i], [c[i] for c in cands], big)]
+    assert not bad, (bad[:5], y[bad[:5]], [c[bad[:5]] for c in cands])
+
+
+def _merge(v, l):
+    mv, ml = [], []
+    for a, b in zip(v.tolist(), l.tolist()):
+        if mv and mv[-1] == a:
+            ml[-1] += b
+        else:
+            mv.append(a)
+            ml.append(b)
+    return mv, np.array(ml)
+
+
+def test_voxel_sequences_match_the_definition(lib):
+    e = synth.grid_edges(20, 15, 30)
+    s, d = synth.random_rays(1500, 21)
+    st, di = s.T, d.T
+    vox, ln, cnt = walk(lib, e, st, di)
+    same = 0
+    for i in range(len(st)):
+        ov, ol = oracle.ray_segments(e, st[i].astype(np.float64), di[i].astype(np.float64))
+        mo, _ = _merge(ov, ol)
+        mg, _ = _merge(vox[i, :cnt[i]].astype(np.int64), ln[i, :cnt[i]].astype(np.float64))
+        same += mo == mg
+        assert abs(ln[i, :cnt[i]].astype(np.float64).sum() - ol.sum()) <= 1e-4 * max(ol.sum(), 1e-30) + 1e-6, i
+    assert same >= 0.995 * len(st), same

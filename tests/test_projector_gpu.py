@@ -332,3 +332,40 @@ def test_autograd_backward_is_adjoint_and_matches_fd(tiny):
         rm = rho0.astype(np.float64).copy(); rm[idx] -= h
         fd = (L(rp) - L(rm)) / (2 * h)
         assert abs(fd - g[idx]) <= 2e-3 * abs(fd) + 1e-6 * np.abs(g_ref).max(), (idx, fd, g[idx])
+
+
+def test_rays_through_the_axis_in_a_half_plane():
+    """Rays lying in a boundary half-plane that cross the z axis away from the
+    origin; float32 rounding leaves them a few 1e-6 off the axis. Each half
+    must land in a sector beside its half-plane: y matches the oracle for the
+    float32 ray, or for the exact ray moved off the surface by 1e-9 (shifted
+    across it, which sends the halves to opposite sides, or turned about z,
+    which sends both to the same side). A walk that let rounding noise decide
+    whether the half-planes are crossed left the second half in the first
+    half's sector, an O(1) error."""
+    e = synth.grid_edges(20, 15, 30)
+    grid = Grid.from_edges(e)
+    rho = synth.uniform_volume(e.shape, 6, 0.1, 1.0)
+    R = float(e.r[-1])
+    rng = np.random.default_rng(31)
+    s64, d64, nrm = [], [], []
+    for _ in range(200):
+        p = e.phi[rng.integers(0, len(e.phi) - 1)]
+        u = np.array([math.cos(p), math.sin(p), 0.0])
+        s64.append(2 * R * u + rng.uniform(-R, R) * np.array([0.0, 0.0, 1.0]))
+        d64.append(-u + np.array([0.0, 0.0, rng.uniform(-0.3, 0.3)]))
+        nrm.append(np.array([-math.sin(p), math.cos(p), 0.0]))
+    s64, d64, nrm = np.array(s64), np.array(d64), np.array(nrm)
+    geom, st, di = rays_geom(s64.T, d64.T)
+    y = tsp_forward(grid, geom, torch.tensor(rho, device=DEV)).cpu().numpy().reshape(-1)
+    cands = [oracle.forward(e, st.T, di.T, rho)]
+    cands += [oracle.forward(e, s64 + h * nrm, d64, rho) for h in (1e-9, -1e-9)]
+    for ang in (1e-9, -1e-9):
+        c, sn = math.cos(ang), math.sin(ang)
+        rot = np.array([[c, -sn, 0.0], [sn, c, 0.0], [0.0, 0.0, 1.0]])
+        cands.append(oracle.forward(e, s64 @ rot.T, d64 @ rot.T, rho))
+    big = max(np.max(np.abs(c)) for c in cands)
+    bad = [i for i in range(len(y))
+           if min(abs(y[i] - c[i]) for c in cands) > 1e-4 * max(max(abs(c[i]) for c in cands), 1e-2 * big)]
+    assert not bad, (bad[:5], y[bad[:5]])
+    assert tsp_device_status() == 0
