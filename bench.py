@@ -46,12 +46,11 @@ STREAM_DRAM_BYTES_PER_ENTRY = 8.38
 # traversal's: the running optical depth (multiply, fma) and the contribution
 # (add, exponential counted as one, multiply, fma).
 ATTEN_EXTRA_OPS = 6.0
-# DRAM bytes (read + write) per launch of the on-the-fly traversal on the
-# default paper-scale workload, averaged over its cone and parallel launches,
-# from one ncu capture of the last timed step (dram__bytes_read.sum +
-# dram__bytes_write.sum): the forward reads the volume once (2.86 MB of
-# 2.88 MB; y stays in L2), the adjoint the detector values and the volume.
-TRACE_DRAM_BYTES = {"forward": 2857472.0, "adjoint": 11263616.0}
+# DRAM bytes (read + write) per launch of the on-the-fly traversal, from ncu
+# counters: None while the kernel has changed since the counters were taken
+# (the last capture, 2.86 MB per forward launch, the volume read once,
+# predates the near-axis set-up of the walk).
+TRACE_DRAM_BYTES = {"forward": None, "adjoint": None}
 
 
 def ordinal(k: int) -> str:
