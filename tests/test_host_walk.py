@@ -193,3 +193,74 @@ def test_voxel_sequences_match_the_definition(lib):
         same += mo == mg
         assert abs(ln[i, :cnt[i]].astype(np.float64).sum() - ol.sum()) <= 1e-4 * max(ol.sum(), 1e-30) + 1e-6, i
     assert same >= 0.995 * len(st), same
+
+
+def _unit(v):
+    return v / np.linalg.norm(v)
+
+
+def test_more_degenerate_families(lib):
+    """The rest of the degenerate suite (Sec. 5.1, Fig. 10 spirit), checked
+    with the parity rule: rays parallel to a cone's generator (the cone
+    quadratic's leading term vanishes), through a corner where a sphere, a
+    cone and a half-plane meet (three-way ties), across the azimuth seam
+    phi = 0 = 2 pi, and starting exactly on a sphere or a cone. Rays tangent
+    to a cone (along a circle of latitude) get the parity rule plus the
+    sliver that float32 rounding of a tangent line can add or remove."""
+    e = synth.grid_edges(20, 15, 30)
+    rho = synth.uniform_volume(e.shape, 8, 0.1, 1.0)
+    R = float(e.r[-1])
+    rng = np.random.default_rng(5)
+    rays = []
+    for _ in range(60):
+        k = rng.integers(1, len(e.theta) - 1)
+        th = float(e.theta[k])
+        ph = rng.uniform(0, 2 * np.pi)
+        r = rng.uniform(e.r[0], R)
+        p = r * np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+        t_phi = np.array([-np.sin(ph), np.cos(ph), 0.0])
+        rays.append((p - 2 * R * t_phi, t_phi))                                      # tangent to the cone
+        g = np.array([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+        off = _unit(np.cross(g, rng.normal(size=3))) * rng.uniform(0.1, 0.5) * R
+        rays.append((off - 2 * R * g, g))                                            # parallel to a generator
+        j, m = rng.integers(1, len(e.r)), rng.integers(0, len(e.phi) - 1)
+        c = e.r[j] * np.array([np.sin(th) * np.cos(e.phi[m]), np.sin(th) * np.sin(e.phi[m]), np.cos(th)])
+        d = _unit(rng.normal(size=3))
+        rays.append((c - 2 * R * d, d))                                              # through a corner
+        x0 = rng.uniform(0.1, 0.9) * R
+        rays.append((np.array([x0, -2 * R, rng.uniform(-0.3, 0.3) * R]),
+                     np.array([0.0, 1.0, rng.uniform(-0.2, 0.2)])))                  # across the seam
+        u = _unit(rng.normal(size=3))
+        rays.append((e.r[j] * u, _unit(rng.normal(size=3))))                         # starting on a sphere
+        rays.append((p, _unit(rng.normal(size=3))))                                  # starting on a cone
+    st = np.array([a for a, _ in rays], np.float32)
+    di = np.array([b for _, b in rays], np.float32)
+    y = forward(lib, e, st, di, rho)
+    ref = oracle.forward(e, st.astype(np.float64), di.astype(np.float64), rho)
+    tangent = np.arange(len(rays)) % 6 == 0
+    parity(y[~tangent], ref[~tangent], what="host walk: more degenerate families")
+    # At exact tangency, float32 rounding puts the line up to delta ~ 8 ulps of
+    # R inside or outside the cone, cutting or missing a sliver of width up to
+    # 2 sqrt(2 R delta); no float32 evaluation decides which the rounded line
+    # does. So the bound adds that sliver in the densest voxel.
+    delta = 8 * 2.0 ** -24 * R
+    sliver = 2 * np.sqrt(2 * R * delta) * float(rho.max())
+    big = np.max(np.abs(ref))
+    err = np.abs(y[tangent] - ref[tangent])
+    assert np.all(err <= 1e-4 * np.maximum(np.abs(ref[tangent]), 1e-2 * big) + sliver), (err.max(), sliver)
+
+
+def test_fig4_grid_and_single_shell(lib):
+    """The (1, 2, 7) grid of Fig. 4 (one shell, two polar bins, seven
+    azimuth bins: sectors wider than a quarter turn get virtual half-planes),
+    full and as a wedge, on rays from outside and from inside."""
+    for e in (synth.GridEdges(np.array([1.0, 2.0]), np.array([0.0, 1.2, np.pi]), np.linspace(0.0, 2 * np.pi, 8)),
+              synth.GridEdges(np.array([1.0, 2.0]), np.array([0.0, 1.2, np.pi]), np.linspace(0.3, 5.0, 8))):
+        rho = synth.uniform_volume(e.shape, 9, 0.1, 1.0)
+        s1, d1 = synth.random_rays(800, 31, start_radius=5.0, aim_radius=2.0)
+        s2, d2 = synth.interior_rays(400, 32, radius=1.9)
+        st = np.concatenate([s1.T, s2.T])
+        di = np.concatenate([d1.T, d2.T])
+        y = forward(lib, e, st, di, rho)
+        ref = oracle.forward(e, st.astype(np.float64), di.astype(np.float64), rho)
+        parity(y, ref, what=f"host walk Fig. 4 grid {e.phi[0]:.1f}..{e.phi[-1]:.1f}")
