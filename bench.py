@@ -53,6 +53,18 @@ ATTEN_EXTRA_OPS = 6.0
 TRACE_DRAM_BYTES = {"forward": None, "adjoint": None}
 
 
+_LOG = ""
+
+
+def emit(out: dict):
+    """Print the result line; with --log, append it to that JSONL file too."""
+    line = json.dumps(out)
+    print(line, flush=True)
+    if _LOG:
+        with open(_LOG, "a") as f:
+            f.write(line + "\n")
+
+
 def ordinal(k: int) -> str:
     """1st, 2nd, 3rd, 4th, ..., 11th, 12th, 13th, 21st, ..."""
     suffix = "th" if 10 <= k % 100 <= 20 else {1: "st", 2: "nd", 3: "rd"}.get(k % 10, "th")
@@ -88,6 +100,7 @@ def parse():
     ap.add_argument("--eval", type=int, default=16, help="warm start: held-out phantoms")
     ap.add_argument("--cap", type=int, default=500, help="warm start: cold SIRT iteration cap")
     ap.add_argument("--target", type=float, default=0.01, help="warm start: relative error target")
+    ap.add_argument("--log", default="", help="also append the JSON line to this file (JSONL)")
     ap.add_argument("--ws-lr", type=float, default=2e-3, help="warm start: peak Adam step size (cosine decay)")
     return ap.parse_args()
 
@@ -237,7 +250,7 @@ def run_reference(args):
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "gpu_launches": 0}
-    print(json.dumps(out), flush=True)
+    emit(out)
 
 
 # ---------------------------------------------------------------------------
@@ -400,7 +413,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
-        print(json.dumps(out), flush=True)
+        emit(out)
     if dist:
         dist.destroy_process_group()
 
@@ -639,7 +652,7 @@ def run_batched(args):
                                   f"{args.iters} SIRT iterations per step in one captured graph",
                       "block_threads": block, "autotuned_classes": tuned},
            "clocks": clocks}
-    print(json.dumps(out), flush=True)
+    emit(out)
 
 
 def run_batched_lists(args, items):
@@ -683,7 +696,7 @@ def run_batched_lists(args, items):
                                   f"memory-bounded chunks (builds inside the timed region)",
                       "chunks": info[0], "peak_list_bytes": info[1]},
            "clocks": clocks}
-    print(json.dumps(out), flush=True)
+    emit(out)
 
 
 def run_differentiation(args):
@@ -744,7 +757,7 @@ def run_differentiation(args):
                       "lr": args.lr, "launch_fwd_adj": tuned},
            "loss_first": float(first), "loss_last": float(loss.detach()), "noise_energy": noise_floor,
            "coeff_rel_error": rel}
-    print(json.dumps(out), flush=True)
+    emit(out)
 
 
 def run_retrieval(args):
@@ -802,7 +815,7 @@ def run_retrieval(args):
            "noise_energy": float((noise.double() ** 2).sum()),
            "error_pct_where_above_25_per_cm3": {"median": float(q[0]), "p95": float(q[1]), "max": float(pct.max()),
                                                 "voxels": int(mask.sum())}}
-    print(json.dumps(out), flush=True)
+    emit(out)
 
 
 def run_warmstart(args):
@@ -878,11 +891,13 @@ def run_warmstart(args):
                       "cold_cap": args.cap, "launch_fwd_adj": tuned,
                       "sirt_projections": "on-the-fly traversal" if args.no_segments else "stored segment lists"},
            "per_phantom": results}
-    print(json.dumps(out), flush=True)
+    emit(out)
 
 
 def main():
+    global _LOG
     args = parse()
+    _LOG = args.log
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":

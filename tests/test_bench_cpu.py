@@ -37,3 +37,21 @@ def test_cpu_baseline_reaches_its_target(monkeypatch):
         assert out["value"] == n / dt and out["cores"] == 16 and out["kind"] == "oracle"
         assert ("every ray" in out["sample"]) == (calls[-1] == 1)
         assert len(calls) <= 4
+
+
+def test_emit_appends_jsonl(monkeypatch, capsys):
+    import json
+    import os
+    scratch = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build")
+    os.makedirs(scratch, exist_ok=True)
+    log = os.path.join(scratch, f"bench_{os.getpid()}.jsonl")
+    if os.path.exists(log):
+        os.remove(log)
+    monkeypatch.setattr(bench, "_LOG", log)
+    bench.emit({"metric": "m", "value": 1.0})
+    bench.emit({"metric": "m", "value": 2.0})
+    with open(log) as f:
+        lines = f.read().splitlines()
+    os.remove(log)
+    assert [json.loads(x)["value"] for x in lines] == [1.0, 2.0]
+    assert capsys.readouterr().out.splitlines() == lines

@@ -136,7 +136,7 @@ def test_training_from_lists_repeats_bit_for_bit():
     assert torch.equal(runs[0][1], runs[1][1])
 
 
-def test_checkpoint_resume_continues_bit_for_bit(tmp_path):
+def test_checkpoint_resume_continues_bit_for_bit():
     """A training run split at a checkpoint (network, Adam moments and step
     count saved to disk, restored into a fresh warm start) takes the same
     steps as an uninterrupted run: identical losses and final weights."""
@@ -147,7 +147,10 @@ def test_checkpoint_resume_continues_bit_for_bit(tmp_path):
     l_whole = whole.train(40, **kw)
     first = WarmStart(e, pos, 32, 50.0, max_batch=4, use_lists=True)
     l_a = first.train(40, stop_step=4, **kw)
-    path = tmp_path / "ws.npz"
+    import os
+    scratch = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build")
+    os.makedirs(scratch, exist_ok=True)
+    path = os.path.join(scratch, f"ws_checkpoint_{os.getpid()}.npz")
     first.save_checkpoint(path, next_step=4)
     second = WarmStart(e, pos, 32, 50.0, max_batch=4, use_lists=True)
     start = second.load_checkpoint(path)
@@ -160,3 +163,4 @@ def test_checkpoint_resume_continues_bit_for_bit(tmp_path):
         assert np.array_equal(sw[k], s2[k]), k
     with pytest.raises(ValueError, match="checkpoint for grid"):
         WarmStart(synth.grid_edges(8, 10, 32), pos, 32, 50.0, max_batch=4).load_checkpoint(path)
+    os.remove(path)
