@@ -350,8 +350,25 @@ struct op_has_gap<Op, decltype(void(static_cast<Op*>(nullptr)->gap()))> {
 // (and op.gap() for the pieces in between that hold no voxel, if Op has it).
 // Returns false if the step cap was hit (an internal inconsistency).
 template <class Op>
-TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d[3], Op& op) {
+TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op) {
   const float xx = x[0].hi, xy = x[1].hi, xz = x[2].hi;
+  // The direction is first scaled by a power of two that puts its largest
+  // component in [0.5, 1). The scaling is exact, so every quantity below is the
+  // same as without it (up to that power of two, which cancels in q and n),
+  // while |d|^2 can neither overflow (float32 directions up to 3.4e38) nor lose
+  // precision as a subnormal (directions down to the smallest floats).
+  const float dm = fmaxf(fabsf(d_in[0].hi), fmaxf(fabsf(d_in[1].hi), fabsf(d_in[2].hi)));
+  if (!(dm > 0.0f) || !(dm < INFINITY)) return true;  // zero or non-finite direction: y = 0
+  ff d[3] = {d_in[0], d_in[1], d_in[2]};
+  int ex = 0;
+  frexpf(dm, &ex);
+  for (int k = -ex; k != 0;) {  // multiply by 2^-ex in steps that stay representable
+    const int step = k > 100 ? 100 : (k < -100 ? -100 : k);
+    const float sc = ldexpf(1.0f, step);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) d[i] = ff{T_MUL(d[i].hi, sc), T_MUL(d[i].lo, sc)};
+    k -= step;
+  }
   // The line arrives as float-float start and direction (exact for float32
   // inputs; carrying the rounding residue of detector-generated rays).
   // Its closest point to the origin, q = (d x (x x d)) / |d|^2, is formed in
@@ -435,16 +452,16 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d[3], Op& op) {
   s.sec = classify_sector(G, px, py);
   float t_ax = INFINITY;
   int sec_ax = 0;
-  // A line whose distance from the z axis, |m_z| / |n_xy|, is below 2^-20 of
+  // A line whose distance from the z axis, |m_z| / |n_xy|, is below 2^-22 of
   // the start's size meets the axis as far as float32 rays can tell: rounding
   // the inputs moves a line through the axis by about that much. Walking its
   // azimuth plane by plane would hinge on half-plane tests that see only
   // rounding noise for the plane the line lies in (and could stop the sweep
-  // past the axis); taking the jump instead moves at most that distance of
-  // path between neighbouring sectors.
+  // past the axis); taking the jump instead moves the path near the axis
+  // between neighbouring sectors.
   const float nxy = fmaf(s.nx, s.nx, T_MUL(s.ny, s.ny));
   const float xsz = T_ADD(T_ADD(fabsf(xx), fabsf(xy)), fabsf(xz));
-  if (fabsf(s.mz) > T_MUL(T_MUL(0x1p-20f, T_SQRT(nxy)), xsz)) {
+  if (fabsf(s.mz) > T_MUL(T_MUL(0x1p-22f, T_SQRT(nxy)), xsz)) {
     s.ph_mode = 0;
   } else {
     if (nxy > 0.0f) {  // the line meets the z axis: azimuth jumps by pi there

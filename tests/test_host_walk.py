@@ -264,3 +264,25 @@ def test_fig4_grid_and_single_shell(lib):
         y = forward(lib, e, st, di, rho)
         ref = oracle.forward(e, st.astype(np.float64), di.astype(np.float64), rho)
         parity(y, ref, what=f"host walk Fig. 4 grid {e.phi[0]:.1f}..{e.phi[-1]:.1f}")
+
+
+def test_extreme_direction_scales(lib):
+    """Free-form directions are normalised (reading 7) whatever their scale:
+    directions of length 1e-20 and 1e20 (whose squared length is subnormal or
+    overflows float32) and starts 1e4 grid radii away give the same line
+    integrals as the oracle."""
+    e = synth.grid_edges(12, 9, 16)
+    R = float(e.r[-1])
+    rho = synth.uniform_volume(e.shape, 3, 0.1, 1.0)
+    rng = np.random.default_rng(19)
+    for scale, dist in ((1e-20, 2.0), (1e20, 2.0), (1.0, 1e4)):
+        rays = []
+        for _ in range(200):
+            v = _unit(rng.normal(size=3))
+            rays.append((dist * R * v, scale * (-v + 0.3 * _unit(rng.normal(size=3)) / dist)))
+        st = np.array([a for a, _ in rays], np.float32)
+        di = np.array([b for _, b in rays], np.float32)
+        y = forward(lib, e, st, di, rho)
+        ref = oracle.forward(e, st.astype(np.float64), di.astype(np.float64), rho)
+        assert np.count_nonzero(ref) > 50
+        parity(y, ref, what=f"host walk, directions x {scale:g}, starts at {dist:g} R")
