@@ -65,3 +65,11 @@ def test_null_arguments_rejected():
     n = ctypes.c_int64()
     assert L.tsp_geom_num_rays(None, ctypes.byref(n)) == 1
     assert L.tsp_geom_cone(0, None, None, None, 4, 4, 30.0, 30.0, None) == 1
+
+
+def test_stall_hook_rejects_bad_budgets():
+    """tsp_debug_tc_stall takes 1 .. 2e9 cycles (host-side check, no device)."""
+    L = _lib.load()
+    assert L.tsp_debug_tc_stall(0) == 1  # TSP_EINVAL
+    assert L.tsp_debug_tc_stall(3_000_000_000) == 1
+    assert b"wait_cycles" in L.tsp_last_error()

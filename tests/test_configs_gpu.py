@@ -1,8 +1,10 @@
 """Parity at the sizes of every workload configuration, in the launch
 configuration the library picks by default: the forward sampled against the
 FP64 oracle (per ray, with the tolerance rule of tests/_util.py, and
-normwise), the adjoint of sparse rays against the oracle's exact volume, and
-the adjoint identity <F x, y> = <x, F^T y>.
+normwise), the adjoint of sparse rays against the oracle's exact volume (per
+voxel 1e-4 relative plus the crossing-position term of grazing_allowance in
+tests/_util.py, and normwise 1e-4), and the adjoint identity
+<F x, y> = <x, F^T y>.
 
 Configurations: the differentiation grid 128 x 64 x 128 with 512^2 cone views
 (50 deg); the largest instances of the uneven batched set, by voxels
@@ -18,7 +20,7 @@ import oracle
 from paper_2608_16960_gb300 import synth, workloads
 from paper_2608_16960_gb300.projector import Geometry, Grid, tsp_adjoint, tsp_device_status, tsp_forward
 
-from _util import parity
+from _util import grazing_allowance, sparse_adjoint_parity
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
@@ -54,8 +56,8 @@ def _check(edges, rho, pos, shape, fov, n_fwd=1500, n_adj=600, seed=0, what=""):
     yv[views] = sub.reshape(len(views), per)
     out = tsp_adjoint(grid, geom, torch.tensor(yv.reshape(geom.det_shape), device=DEV)).cpu().numpy()
     ref = oracle.adjoint(edges, st[idx], di[idx], sub[idx].astype(np.float64))
-    parity(out, ref, rel=1e-2, what=f"sparse adjoint {what}")
-    assert np.linalg.norm(out - ref) <= 1e-4 * np.linalg.norm(ref), what
+    allow, gmax = grazing_allowance(edges, st[idx], di[idx], sub[idx])
+    sparse_adjoint_parity(out, ref, allow, gmax, what=f"sparse adjoint {what}")
 
     # adjoint identity over every view
     x = torch.tensor(synth.uniform_volume(grid.shape, seed + 1), device=DEV)

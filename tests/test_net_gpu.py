@@ -8,12 +8,14 @@ bfloat16 ulp (2^-8 relative) away; activations must agree to one ulp and such
 flips must be rare (a flip feeds the next layer, hence two ulps); outputs and gradients (sums over many voxels) agree
 normwise to 1e-2.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
 
 from oracle import net as onet
-from paper_2608_16960_gb300 import synth
+from paper_2608_16960_gb300 import _lib, synth
 from paper_2608_16960_gb300.model import WarmStartNet
 
 pytestmark = pytest.mark.gpu
@@ -123,3 +125,32 @@ def test_training_steps_reduce_loss(case):
         net.adam(lr=1e-3)
     assert losses[-1] < 0.5 * losses[0], losses[::10]
     net.set_params(_flat(params))
+
+
+def test_bounded_wait_runs_out_and_the_next_call_matches_the_oracle(case):
+    """Failure detection without a fault: tsp_debug_tc_stall makes the next
+    tensor-core convolution's loader issue no shell copy and limits its waits
+    to 2e5 cycles (about 0.1 ms). The MMA warp's first wait for a shell then
+    runs out; the kernel sets the timeout bit, releases its tensor memory and
+    returns with nothing in flight, and tsp_device_status reports TSP_ETIMEOUT.
+    The next forward pass (which allocates the tensor memory again on every
+    multiprocessor) must run normally and match the oracle."""
+    shape, B, params, a, t, net = case
+    L = _lib.load()
+    net.set_params(_flat(params))
+    at = torch.tensor(a, device=DEV)
+    torch.cuda.synchronize()
+    assert L.tsp_debug_tc_stall(200000) == 0
+    net.forward(at)
+    code = ctypes.c_int(0)
+    st = L.tsp_device_status(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(code))
+    assert st == 5, (st, L.tsp_last_error())  # TSP_ETIMEOUT
+    assert code.value & 0x100, code.value      # TSP_DEVERR_WAIT_TIMEOUT
+    assert b"bounded wait" in L.tsp_last_error()
+    out = net.forward(at).cpu().numpy()
+    ref = onet.forward(params, a)
+    assert np.linalg.norm(out - ref) <= 1e-2 * np.linalg.norm(ref)
+    code = ctypes.c_int(0)
+    assert L.tsp_device_status(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(code)) == 0
+    assert code.value == 0
+

@@ -7,7 +7,10 @@ use this entry point: it keeps its scratch in a static device array instead of
 asking for a workspace. These tests call it through the C ABI twice in a row,
 on different problems (the shared array keeps the previous call's contents),
 and compare each result with the workspace-based tsp_sirt under the parity
-tolerance of the other tests.
+tolerance of the other tests. Once each problem has run once (the first call
+on a device looks up the scratch array's address, and the CUDA runtime may
+load kernels lazily on first use), repeated calls must leave the device's free
+memory and the library's own allocation counter unchanged.
 """
 import ctypes
 
@@ -57,6 +60,26 @@ def test_noalloc_matches_workspace_sirt_two_calls_in_a_row():
         assert _noalloc(grid, geom, y, x, n_iter, nonneg) == 0, _lib.load().tsp_last_error()
         torch.cuda.synchronize()
         parity(x.cpu().numpy(), x_ref.cpu().numpy(), what=f"noalloc sirt {kind}")
+    assert tsp_device_status() == 0
+
+
+def test_noalloc_allocates_nothing_after_the_first_calls():
+    probs = [_problem(k) for k in ("tiny", "multiview")]
+    xs = [torch.zeros(g.shape, device=DEV) for g, _, _ in probs]
+    for (grid, geom, y), x, nonneg in zip(probs, xs, (False, True)):
+        assert _noalloc(grid, geom, y, x, 3, nonneg) == 0, _lib.load().tsp_last_error()
+    torch.cuda.synchronize()
+    L = _lib.load()
+    count = ctypes.c_int64()
+    assert L.tsp_debug_allocation_count(ctypes.byref(count)) == 0
+    free0, count0 = torch.cuda.mem_get_info()[0], count.value
+    for _ in range(2):
+        for (grid, geom, y), x, nonneg in zip(probs, xs, (False, True)):
+            assert _noalloc(grid, geom, y, x, 3, nonneg) == 0, L.tsp_last_error()
+    torch.cuda.synchronize()
+    assert L.tsp_debug_allocation_count(ctypes.byref(count)) == 0
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert count.value == count0
     assert tsp_device_status() == 0
 
 
