@@ -48,6 +48,7 @@ tsp_status scratch_for_current_device(void** out) {
 
 extern "C" tsp_status tsp_sirt_noalloc(tsp_grid grid, tsp_geom geom, const float* y, float* x, int n_iter,
                                        int flags, void* stream) {
+  TSP_RANGE("tsp_sirt_noalloc");
   tsp_status st = tsp::check_trace_args(grid, geom, y, x, 1, nullptr, "tsp_sirt_noalloc");
   if (st != TSP_OK) return st;
   if (n_iter < 0) return tsp::fail(TSP_EINVAL, "tsp_sirt_noalloc: n_iter must be >= 0");
