@@ -562,11 +562,33 @@ tsp_status tsp_add_noise(float* y, int64_t n, int batch, const uint64_t* seeds, 
 tsp_status tsp_mul_bcast(float* x, const float* s, int64_t n, int batch, void* stream);
 tsp_status tsp_scale_batch(float* x, const float* scale, int64_t n, int batch, int divide, void* stream);
 
+/* Bits of the device error word (tsp_device_status). */
+#define TSP_DEVERR_STEP_CAP 0x1        /* a traversal hit its step cap */
+#define TSP_DEVERR_LIST_BOUND 0x2      /* a list fill wrote other than its counted entries */
+#define TSP_DEVERR_LIST_ROWS 0x8       /* a list stream found a row rank outside the lists */
+#define TSP_DEVERR_WAIT_TIMEOUT 0x100  /* a tensor-core kernel's bounded mbarrier wait gave up */
+#define TSP_DEVERR_SMEM_ALIGN 0x200    /* a tensor-core kernel got misaligned shared memory */
+
 /*
  * tsp_device_status - synchronises `stream`, then reads and clears the device
- * error word (0 = no kernel reported an inconsistency).
+ * error word (0 = no kernel reported an inconsistency). Returns TSP_ETIMEOUT
+ * if TSP_DEVERR_WAIT_TIMEOUT is set: the kernel gave up its waits, released
+ * its tensor memory and returned, so the context stays usable but that
+ * kernel's output is incomplete. Any other bit gives TSP_EDEVICE.
  */
 tsp_status tsp_device_status(void* stream, int* code);
+
+/*
+ * tsp_debug_tc_stall - test hook (no counterpart in the paper): the next
+ * launch of the tensor-core convolution (a tsp_net_* call) runs with its
+ * shell loader stalled, issuing no copy at all, and with every bounded wait
+ * limited to wait_cycles SM cycles (1 .. 2e9; the default bound is 2e9). Its
+ * first wait for a shell therefore runs out: the kernel sets
+ * TSP_DEVERR_WAIT_TIMEOUT, frees its tensor memory and returns with nothing
+ * in flight, and tsp_device_status reports TSP_ETIMEOUT. One-shot and
+ * process-wide; later launches run normally.
+ */
+tsp_status tsp_debug_tc_stall(int64_t wait_cycles);
 
 /* Thread-local message describing the last non-OK status of this thread. */
 const char* tsp_last_error(void);

@@ -65,6 +65,7 @@ SIGNATURES = {
     "tsp_segments_sirt_weights": (_I, [_P, _P, _P, _P]),
     "tsp_debug_fail_allocation": (_I, [_I64]),
     "tsp_debug_allocation_count": (_I, [_I64P]),
+    "tsp_debug_tc_stall": (_I, [_I64]),
     "tsp_segments_forward": (_I, [_P, _P, _P, _I, _P]),
     "tsp_segments_adjoint": (_I, [_P, _P, _P, _I, _I, _P]),
     "tsp_segments_sirt_workspace_bytes": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),

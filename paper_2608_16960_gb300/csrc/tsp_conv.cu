@@ -20,6 +20,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <cmath>
 #include <vector>
 
@@ -110,6 +111,8 @@ __device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, u
 // (tcgen05.ld 32x32b) and runs its epilogue while the tensor cores work.
 // ---------------------------------------------------------------------------
 constexpr int WROWS = 27 * CH + 2;  // weight rows per chunk plane (+2: chunk planes 32 bytes off a bank period)
+// Default bound of every mbarrier wait of the tensor-core kernels, in SM clock
+// cycles (about one second): a kernel argument, so that a test can shorten it.
 constexpr long long TC_WAIT_BUDGET = 2000000000LL;
 
 // Tiles per chunk and shell-buffer geometry for an azimuth count (host and
@@ -388,13 +391,14 @@ __device__ __forceinline__ bool epilogue_and(bool p) {
   return r != 0;
 }
 
-// Bounded wait on an mbarrier phase that also gives up when another role of
-// the CTA has already given up (s_abort); sets s_abort on its own timeout.
-__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* s_abort) {
+// Bounded wait on an mbarrier phase (at most `budget` SM cycles) that also
+// gives up when another role of the CTA has already given up (s_abort); sets
+// s_abort on its own timeout.
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity, volatile int* s_abort, long long budget) {
   const long long t0 = clock64();
   while (!mbar_try(bar, parity)) {
     if (*s_abort) return false;
-    if (clock64() - t0 > TC_WAIT_BUDGET) {
+    if (clock64() - t0 > budget) {
       *s_abort = 1;
       return false;
     }
@@ -422,7 +426,8 @@ template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1) conv32_tc_kernel(const __grid_constant__ CUtensorMap xmap, Dims d, int rseg,
                                                            const bf16* __restrict__ X, const bf16* __restrict__ W,
                                                            const float* __restrict__ bias, bf16* __restrict__ Y,
-                                                           uint32_t* __restrict__ mask, float* __restrict__ G) {
+                                                           uint32_t* __restrict__ mask, float* __restrict__ G,
+                                                           long long budget, int stall_loader) {
   extern __shared__ __align__(128) unsigned char smem[];
   // full[s]: shell slot s loaded (32 loader arrivals + TMA bytes); empty[s]: its last MMA done (commit);
   // tfull[j]: TMEM buffer j holds a finished step (commit); tempty[j]: drained (one arrival per epilogue thread)
@@ -491,7 +496,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv32_tc_kernel(const __grid_c
       const int r0 = seg * rseg, n = min(rseg, d.Nr - r0);
       const int o0 = q * TC_TOUT * T, e_lo = (o0 - 1 + cols) / cols - 2;  // floor((o0 - 1) / cols) - 1
       for (int i = 0; i < n && go; ++i, ++K) {
-        if (K >= NB && !__all_sync(0xffffffffu, tc_wait(&tempty[kb], kph ^ 1u, &s_abort))) {
+        if (K >= NB && !__all_sync(0xffffffffu, tc_wait(&tempty[kb], kph ^ 1u, &s_abort, budget))) {
           go = false;
           break;
         }
@@ -499,7 +504,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv32_tc_kernel(const __grid_c
         const uint32_t acc0 = tmem + uint32_t(kb) * uint32_t(T) * 96;
         for (int dri = 0; dri < 3 && go; ++dri) {
           const int Gl = G0 + i + dri, slot = Gl % 3;
-          if (!__all_sync(0xffffffffu, tc_wait(&full[slot], uint32_t(Gl / 3) & 1u, &s_abort))) {
+          if (!__all_sync(0xffffffffu, tc_wait(&full[slot], uint32_t(Gl / 3) & 1u, &s_abort, budget))) {
             go = false;
             break;
           }
@@ -531,11 +536,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv32_tc_kernel(const __grid_c
     }
     if (!go && lane == 0) {  // let issued MMAs land before TMEM is released
       const long long t0 = clock64();
-      while (clock64() - t0 < TC_WAIT_BUDGET / 8) {
+      while (clock64() - t0 < budget / 8) {
       }
     }
     __syncwarp();
-  } else if (warp == 1) {  // ---- shell loader ----
+  } else if (warp == 1 && !stall_loader) {  // ---- shell loader (a test may stall it: no load at all) ----
     int G0 = 0;
     bool go = true;
     for (int item = blockIdx.x; item < items && go; item += gridDim.x) {
@@ -544,7 +549,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv32_tc_kernel(const __grid_c
       const int e_lo = (q * TC_TOUT * T - 1 + cols) / cols - 2;
       for (int j = 0; j < n + 2; ++j) {
         const int Gl = G0 + j, slot = Gl % 3;
-        if (Gl >= 3 && !__all_sync(0xffffffffu, tc_wait(&empty[slot], uint32_t(Gl / 3 - 1) & 1u, &s_abort))) {
+        if (Gl >= 3 && !__all_sync(0xffffffffu, tc_wait(&empty[slot], uint32_t(Gl / 3 - 1) & 1u, &s_abort, budget))) {
           go = false;
           break;
         }
@@ -583,7 +588,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv32_tc_kernel(const __grid_c
         const bf16* xres = MODE == 2 ? Y : X;  // mode 2: Y carries the input a
         if (T == 2) tc_epilogue_fetch<MODE, 2>(roff, vb, vv, xres, G, hf, in);
         else tc_epilogue_fetch<MODE, 1>(roff, vb, vv, xres, G, hf, in);
-        const bool ok = epilogue_and(tc_wait(&tfull[kb], kph, &s_abort));
+        const bool ok = epilogue_and(tc_wait(&tfull[kb], kph, &s_abort, budget));
         if (!ok) {
           go = false;
           break;
@@ -599,7 +604,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv32_tc_kernel(const __grid_c
     }
   }
   __syncthreads();
-  if (tid == 0 && s_abort) atomicOr(&g_conv_error_word, 1);
+  if (tid == 0 && s_abort) atomicOr(&g_conv_error_word, 1);  // TSP_DEVERR_WAIT_TIMEOUT once shifted
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
@@ -691,7 +696,8 @@ __device__ __forceinline__ bool wg_epilogue_and(bool p) {
 // end. part: [gridDim.x][27][32][32].
 __global__ void __launch_bounds__(256, 1) wgrad32_tc_kernel(const __grid_constant__ CUtensorMap hmap,
                                                             const __grid_constant__ CUtensorMap gmap, Dims d,
-                                                            const bf16* __restrict__ H, float* __restrict__ part) {
+                                                            const bf16* __restrict__ H, float* __restrict__ part,
+                                                            long long budget) {
   extern __shared__ __align__(128) unsigned char smem[];
   // full[s]: stage s loaded (32 loader arrivals + TMA bytes); empty[s]: its MMAs done (commit);
   // done: every MMA of the CTA done (commit)
@@ -731,7 +737,7 @@ __global__ void __launch_bounds__(256, 1) wgrad32_tc_kernel(const __grid_constan
     int i = 0;
     for (int64_t row = blockIdx.x; row < rows && go; row += gridDim.x, ++i) {
       const int slot = i % NS;
-      if (!__all_sync(0xffffffffu, tc_wait(&full[slot], uint32_t(i / NS) & 1u, &s_abort))) {
+      if (!__all_sync(0xffffffffu, tc_wait(&full[slot], uint32_t(i / NS) & 1u, &s_abort, budget))) {
         go = false;
         break;
       }
@@ -758,7 +764,7 @@ __global__ void __launch_bounds__(256, 1) wgrad32_tc_kernel(const __grid_constan
       tc_commit_elect(&done);
     } else if (lane == 0) {  // let issued MMAs land before TMEM is released
       const long long t0 = clock64();
-      while (clock64() - t0 < TC_WAIT_BUDGET / 8) {
+      while (clock64() - t0 < budget / 8) {
       }
     }
     __syncwarp();
@@ -766,14 +772,14 @@ __global__ void __launch_bounds__(256, 1) wgrad32_tc_kernel(const __grid_constan
     const int slot = warp - 1;
     int i = slot;
     for (int64_t row = blockIdx.x + int64_t(slot) * gridDim.x; row < rows; row += int64_t(NS) * gridDim.x, i += NS) {
-      if (i >= NS && !__all_sync(0xffffffffu, tc_wait(&empty[slot], uint32_t(i / NS - 1) & 1u, &s_abort))) break;
+      if (i >= NS && !__all_sync(0xffffffffu, tc_wait(&empty[slot], uint32_t(i / NS - 1) & 1u, &s_abort, budget))) break;
       const int e = int(row % d.Ne), r = int((row / d.Ne) % d.Nr), b = int(row / (int64_t(d.Ne) * d.Nr));
       wg_load_stage(&hmap, &gmap, d, H, b, r, e, smem + size_t(slot) * ST, PS, &full[slot], lane);
     }
   } else if (warp >= 4) {  // ---- epilogue: the CTA's partial dW ----
     const int q = warp & 3;
     float* out = part + size_t(blockIdx.x) * 27 * CH * CH;
-    const bool ok = wg_epilogue_and(!any || tc_wait(&done, 0u, &s_abort));
+    const bool ok = wg_epilogue_and(!any || tc_wait(&done, 0u, &s_abort, budget));
     if (ok) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       for (int t = 0; t < 9; ++t) {
@@ -793,7 +799,7 @@ __global__ void __launch_bounds__(256, 1) wgrad32_tc_kernel(const __grid_constan
     }
   }
   __syncthreads();
-  if (tid == 0 && s_abort) atomicOr(&g_conv_error_word, 1);
+  if (tid == 0 && s_abort) atomicOr(&g_conv_error_word, 1);  // TSP_DEVERR_WAIT_TIMEOUT once shifted
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
@@ -1251,6 +1257,10 @@ tsp_status set_attrs(int Na) {
   return st;
 }
 
+// Armed by tsp_debug_tc_stall: the wait budget (cycles) of the next
+// tensor-core convolution launch, whose loader then stalls; 0 = not armed.
+std::atomic<long long> g_tc_stall{0};
+
 // Persistent launch: work items (sample, chunk, run of rseg shells), about
 // four per multiprocessor, one CTA per multiprocessor (its shared memory).
 void conv32(int mode, const Dims& d, int B, const CUtensorMap& xmap, const bf16* X, const bf16* W, const float* bias,
@@ -1264,9 +1274,16 @@ void conv32(int mode, const Dims& d, int B, const CUtensorMap& xmap, const bf16*
   const int rseg = int(std::max<int64_t>(2, std::min<int64_t>(d.Nr, steps / (4 * int64_t(g_sm_count)))));
   const int64_t items = int64_t(B) * nq * ((d.Nr + rseg - 1) / rseg);
   const unsigned grid = unsigned(std::min<int64_t>(items, g_sm_count));
-  if (mode == 0) conv32_tc_kernel<0><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
-  else if (mode == 1) conv32_tc_kernel<1><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
-  else conv32_tc_kernel<2><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G);
+  // the one-shot test hook of tsp_debug_tc_stall: this launch's loader issues
+  // nothing and its waits give up after the armed number of cycles
+  const long long armed = g_tc_stall.exchange(0);
+  const long long budget = armed > 0 ? armed : TC_WAIT_BUDGET;
+  const int stall = armed > 0 ? 1 : 0;
+  if (mode == 0)
+    conv32_tc_kernel<0><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G, budget, stall);
+  else if (mode == 1)
+    conv32_tc_kernel<1><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G, budget, stall);
+  else conv32_tc_kernel<2><<<grid, TC_THREADS, pl.smem, st>>>(xmap, db, rseg, X, W, bias, Y, mask, G, budget, stall);
 }
 
 tsp_status prepare_weights(tsp_net n, cudaStream_t st) {
@@ -1375,6 +1392,13 @@ extern "C" void tsp_net_destroy(tsp_net n) {
   delete n;
 }
 
+extern "C" tsp_status tsp_debug_tc_stall(int64_t wait_cycles) {
+  if (wait_cycles <= 0 || wait_cycles > TC_WAIT_BUDGET)
+    return fail(TSP_EINVAL, "tsp_debug_tc_stall: wait_cycles must be in 1 .. " + std::to_string(TC_WAIT_BUDGET));
+  g_tc_stall.store((long long)wait_cycles);
+  return TSP_OK;
+}
+
 extern "C" tsp_status tsp_net_num_params(tsp_net n, size_t* count) {
   if (!n || !count) return fail(TSP_EINVAL, "tsp_net_num_params: NULL argument");
   *count = n->n_params;
@@ -1453,7 +1477,8 @@ void wgrad32_tc(tsp_net n, int k, int batch, float* dW, cudaStream_t cs) {
   db.B = batch;
   const int64_t rows = int64_t(batch) * db.Nr * db.Ne;
   const int grid = int(std::min<int64_t>(rows, g_sm_count));
-  wgrad32_tc_kernel<<<grid, 256, wg_smem(db.Na), cs>>>(n->map_h[k], n->map_gz, db, n->h[k], n->wpart);
+  wgrad32_tc_kernel<<<grid, 256, wg_smem(db.Na), cs>>>(n->map_h[k], n->map_gz, db, n->h[k], n->wpart,
+                                                       TC_WAIT_BUDGET);
   part_reduce_kernel<<<27 * CH * CH / 32, 1024, 0, cs>>>(n->wpart, grid, 27 * CH * CH, 27 * CH * CH, dW);
 }
 

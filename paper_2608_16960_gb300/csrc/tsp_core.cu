@@ -79,6 +79,9 @@ extern "C" tsp_status tsp_device_status(void* stream, int* code) {
     if (e != cudaSuccess) return tsp::cuda_fail(e, "tsp_device_status");
   }
   *code = v;
+  if (v & TSP_DEVERR_WAIT_TIMEOUT)
+    return fail(TSP_ETIMEOUT, "a tensor-core kernel's bounded wait gave up (device error word " + std::to_string(v) +
+                                  ")");
   if (v != 0) return fail(TSP_EDEVICE, "a kernel set the device error word: " + std::to_string(v));
   return TSP_OK;
 }
