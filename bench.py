@@ -98,7 +98,10 @@ def parse():
     ap.add_argument("--solver", choices=["cgls", "adam"], default="cgls", help="retrieval: solver of Eq. 10")
     ap.add_argument("--train-samples", type=int, default=20000, help="warm start: training phantoms")
     ap.add_argument("--eval", type=int, default=16, help="warm start: held-out phantoms")
-    ap.add_argument("--cap", type=int, default=500, help="warm start: cold SIRT iteration cap")
+    ap.add_argument("--cap", type=int, default=500, help="warm start: SIRT iteration cap at 1%% noise")
+    ap.add_argument("--cap-low", type=int, default=1000, help="warm start: SIRT iteration cap at 0.1%% noise")
+    ap.add_argument("--eval-low", type=int, default=8, help="warm start: held-out phantoms at 0.1%% noise")
+    ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg")
     ap.add_argument("--target", type=float, default=0.01, help="warm start: relative error target")
     ap.add_argument("--log", default="", help="also append the JSON line to this file (JSONL)")
     ap.add_argument("--ws-lr", type=float, default=2e-3, help="warm start: peak Adam step size (cosine decay)")
@@ -115,7 +118,7 @@ class ClockSampler:
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
@@ -142,7 +145,7 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
+        sm, smax, busy, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for row in csv.reader(open(self.path)):
             if len(row) < 9:
@@ -152,12 +155,18 @@ class ClockSampler:
                 smax.append(float(row[2]))
             except ValueError:
                 continue
+            try:
+                busy.append(float(row[9]) > 0.0 if len(row) > 9 else True)
+            except ValueError:
+                busy.append(True)
             for nm, v in zip(names, row[5:9]):
                 if v.strip().lower() == "active":
                     reasons.add(nm)
         os.unlink(self.path)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        loaded = [f for f, b in zip(sm, busy) if b]
+        return {"sm_mhz": float(np.median(loaded)) if loaded else (float(np.median(sm)) if sm else None),
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons), "samples": len(sm),
+                "samples_under_load": len(loaded)}
 
 
 def measured_peaks():
@@ -321,6 +330,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    # clocks sampled from the main timed region through the last leg
     sampler = ClockSampler(local)
     sampler.start()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
@@ -328,7 +338,6 @@ def run_ours(args):
         flush.zero_()
         step(evs[k])
     torch.cuda.synchronize()
-    clocks = sampler.stop()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -383,6 +392,11 @@ def run_ours(args):
     dyn_leg = None
     if not args.no_dynamic:
         dyn_leg = time_dynamic(args, wl, grid, geoms, ws, flush, stream, n_rays, dist)
+    ws_leg = None
+    if not args.no_warmstart and not args.views and world == 1:
+        ws_leg = warmstart_leg(args, args.train_samples, args.eval, args.eval_low, flush)
+    clocks = sampler.stop()
+    clocks["span"] = "main timed region through the last leg"
     # dominant kernel: whichever of the forward / adjoint traversals takes longer
     dom = "forward" if t_fwd >= t_adj else "adjoint"
     t_dom_launch = (max(t_fwd, t_adj) / args.steps) / len(geoms) / 1e3  # s per launch
@@ -409,7 +423,7 @@ def run_ours(args):
            "segments_per_s": world * 2 * n_segs * args.steps / (t_tot / 1e3),
            "roofline": roofline, "clocks": clocks, "e2e": e2e,
            "gpu_launches": 2 * len(geoms) * args.steps, "peaks": peak_kind, "segment_lists": seg_leg,
-           "attenuated": att_leg, "dynamic": dyn_leg}
+           "attenuated": att_leg, "dynamic": dyn_leg, "warm_start": ws_leg}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -818,79 +832,156 @@ def run_retrieval(args):
     emit(out)
 
 
-def run_warmstart(args):
-    """Learned warm start vs plain SIRT: 64x48x96 grid, 48 cone views of 256^2 (50 deg,
-    orbit radius 60), 1% noise. Train the network on fresh phantoms, then on held-out
-    phantoms time (a) warm: input + network + SIRT iterations, (b) cold: SIRT from 0,
-    each to the error target (or, if cold SIRT never reaches it within the cap, to within
-    5% of the cold solver's best error), errors evaluated after every iteration."""
+def _error_curve(ws, y, truth, x0, cap):
+    """Untimed pass: relative error (masked to voxels some ray meets) after
+    0, 1, ..., cap SIRT iterations from x0. The errors stay on the device until
+    one read at the end, so the pass costs about cap iterations."""
+    import torch
+
+    mf = ws.mask.to(torch.float32)
+    tn = torch.linalg.norm(truth * mf)
+    x = x0.clone()
+    errs = [torch.linalg.norm((x - truth) * mf)]
+    for _ in range(cap):
+        ws.sirt(y, x, 1, reuse_weights=True)
+        errs.append(torch.linalg.norm((x - truth) * mf))
+    return (torch.stack(errs) / tn).cpu().numpy()
+
+
+def _timed_region(fn, flush, reps=3):
+    """Median over reps of fn's device time (CUDA events on the current stream),
+    L2 flushed before each."""
+    import torch
+
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return float(np.median(ts))
+
+
+def warmstart_eval(ws, flush, seeds, noise_frac, target, cap, fallback):
+    """Time to target, learned warm start vs plain SIRT, on held-out phantoms.
+
+    Per phantom an untimed pass records both error curves (SIRT from zero and
+    from the network's estimate), which gives the iteration counts k_cold and
+    k_warm at which each first reaches the target. Then each solver is run
+    again to its count as one timed region (CUDA events, median of three):
+    cold = k_cold SIRT iterations from zero; warm = the network's input
+    (back-projection, normalisation), the network, the rescaling and k_warm
+    SIRT iterations. With fallback=True a target the cold solver never
+    reaches within the cap becomes 1.05 x its best error on that phantom."""
+    import torch
+
+    ws.noise_frac = noise_frac
+    rows = []
+    for s in seeds:
+        rho = ws.phantoms([s])
+        y = ws.measure(rho, [s])[0].contiguous()
+        truth = rho[0]
+        cold = _error_curve(ws, y, truth, torch.zeros_like(truth), cap)
+        warm = _error_curve(ws, y, truth, ws.warm_start(y), cap)
+        tgt = target
+        if fallback and cold.min() > target:
+            tgt = 1.05 * float(cold.min())
+        hit_c = np.flatnonzero(cold <= tgt)
+        hit_w = np.flatnonzero(warm <= tgt)
+        row = {"seed": int(s), "target": float(tgt), "cold_best": float(cold.min()), "warm_best": float(warm.min()),
+               "warm_err_at_0": float(warm[0]), "cold_iters": int(hit_c[0]) if len(hit_c) else None,
+               "warm_iters": int(hit_w[0]) if len(hit_w) else None, "cold_time_s": None, "warm_time_s": None}
+        if row["cold_iters"] is not None:
+            x = torch.zeros_like(truth)
+
+            def cold_run():
+                x.zero_()
+                ws.sirt(y, x, row["cold_iters"], reuse_weights=True)
+
+            row["cold_time_s"] = _timed_region(cold_run, flush)
+        if row["warm_iters"] is not None:
+            def warm_run():
+                x0 = ws.warm_start(y)
+                ws.sirt(y, x0, row["warm_iters"], reuse_weights=True)
+
+            row["warm_time_s"] = _timed_region(warm_run, flush)
+        rows.append(row)
+    both = [r for r in rows if r["cold_time_s"] is not None and r["warm_time_s"] is not None]
+    out = {"noise_frac": noise_frac, "target": "within 5% of the cold solver's best error where it misses "
+           f"{target:g}" if fallback else f"{target:g} relative error", "phantoms": len(rows),
+           "cold_reached": sum(r["cold_time_s"] is not None for r in rows),
+           "warm_reached": sum(r["warm_time_s"] is not None for r in rows), "cap_iters": cap,
+           "literal_target_reached_by_cold": sum(r["cold_best"] <= target for r in rows),
+           "warm_time_s_median": float(np.median([r["warm_time_s"] for r in both])) if both else None,
+           "cold_time_s_median": float(np.median([r["cold_time_s"] for r in both])) if both else None,
+           "speedup_median": float(np.median([r["cold_time_s"] / r["warm_time_s"] for r in both])) if both else None,
+           "per_phantom": rows}
+    return out
+
+
+def warmstart_leg(args, n_train, n_eval, n_eval_low, flush):
+    """Learned warm start vs plain SIRT (64 x 48 x 96 grid, 48 cone views of
+    256^2, 50 deg, orbit radius 60): train the network on n_train fresh
+    phantoms (1% noise), then time both solvers to the error target on
+    held-out phantoms at 1% and at 0.1% noise: to the literal 1% target where
+    the cold solver reaches it within the cap, else to within 5% of its best
+    error (each leg counts the phantoms on which the literal target was
+    reached)."""
     import torch
 
     from paper_2608_16960_gb300 import synth
     from paper_2608_16960_gb300.projector import tsp_autotune
     from paper_2608_16960_gb300.warmstart import WarmStart
 
-    torch.cuda.set_device(0)
     e = synth.grid_edges(64, 48, 96)
     ws = WarmStart(e, synth.circular_orbit(48, 60.0, incline_deg=20.0), 256, 50.0, max_batch=8,
                    use_lists=not args.no_segments)
     tuned = tsp_autotune(ws.grid, ws.geom)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = ws.train(args.train_samples, batch=8, lr=args.ws_lr, seed0=1000)
+    losses = ws.train(n_train, batch=8, lr=args.ws_lr, seed0=1000)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-
-    # per-iteration SIRT time and warm-start overhead, timed without error evaluations
+    # the SIRT weights R = 1/(F 1), C = 1/(F^T 1) belong to the geometry, like the
+    # stored lists: computed once here, outside every timed region
     rho = ws.phantoms([900000])
-    y = ws.measure(rho, [900000])[0]
-    x = torch.zeros_like(rho[0])
-    ws.sirt(y, x, 1, reuse_weights=False)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    ws.sirt(y, x, 50, reuse_weights=True)
-    e1.record()
-    torch.cuda.synchronize()
-    t_iter = e0.elapsed_time(e1) / 50 / 1e3
-    ws.warm_start(y)
-    e0.record()
-    for _ in range(10):
-        ws.warm_start(y)
-    e1.record()
-    torch.cuda.synchronize()
-    t_warm0 = e0.elapsed_time(e1) / 10 / 1e3
+    y = ws.measure(rho, [900000])[0].contiguous()
+    ws.sirt(y, torch.zeros_like(rho[0]), 1, reuse_weights=False)
+    t_iter = _timed_region(lambda: ws.sirt(y, torch.zeros_like(rho[0]), 50, reuse_weights=True), flush) / 50
+    t_overhead = _timed_region(lambda: ws.warm_start(y), flush)
+    high = warmstart_eval(ws, flush, [900001 + i for i in range(n_eval)], 0.01, args.target, args.cap, True)
+    low = warmstart_eval(ws, flush, [950001 + i for i in range(n_eval_low)], 0.001, args.target, args.cap_low,
+                         True) if n_eval_low else None
+    return {"unit": "s", "higher_is_better": False, "noise_1pct": high, "noise_0p1pct": low,
+            "sirt_iter_ms": 1e3 * t_iter, "warm_start_overhead_ms": 1e3 * t_overhead,
+            "train": {"samples": n_train, "seconds": t_train, "loss_first": float(np.mean(losses[:20])),
+                      "loss_last": float(np.mean(losses[-20:])), "noise_frac": 0.01},
+            "config": {"workload": "grid 64x48x96, 48 cone views 256^2 (50 deg), network trained at 1% noise",
+                       "launch_fwd_adj": tuned, "timing": "CUDA events, median of 3, L2 flushed before each",
+                       "sirt_weights": "computed once per geometry, outside the timed regions",
+                       "sirt_projections": "on-the-fly traversal" if args.no_segments else "stored segment lists"}}
 
-    results = []
-    for i in range(args.eval):
-        s = 900001 + i
-        rho = ws.phantoms([s])
-        y = ws.measure(rho, [s])[0]
-        _, cold, _ = ws.sirt_curve(y, rho[0], torch.zeros_like(rho[0]), args.cap, every=1)
-        x0 = ws.warm_start(y)
-        _, warm, _ = ws.sirt_curve(y, rho[0], x0, args.cap, every=1)
-        # the error target, or (when 1% noise puts it out of reach) within 5% of the cold solver's best
-        target = args.target if min(cold) <= args.target else 1.05 * min(cold)
-        k_cold = next(j for j, v in enumerate(cold) if v <= target)
-        k_warm = next((j for j, v in enumerate(warm) if v <= target), None)
-        results.append({"seed": s, "target": target, "cold_iters": k_cold, "cold_time_s": k_cold * t_iter,
-                        "cold_err_at_20": cold[min(20, len(cold) - 1)], "cold_best": min(cold),
-                        "warm_iters": k_warm, "warm_time_s": None if k_warm is None else t_warm0 + k_warm * t_iter,
-                        "warm_err_at_0": warm[0], "warm_err_at_20": warm[min(20, len(warm) - 1)],
-                        "warm_best": min(warm)})
-    ok = [r for r in results if r["warm_time_s"] is not None]
+
+def run_warmstart(args):
+    """The warm-start workload alone, as its own result line (value = median
+    warm time to target at 1% noise)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+    sampler = ClockSampler(0)
+    sampler.start()
+    leg = warmstart_leg(args, args.train_samples, args.eval, args.eval_low, flush)
+    clocks = sampler.stop()
+    hi = leg["noise_1pct"]
     out = {"metric": "time to target relative error, learned warm start vs plain SIRT", "unit": "s",
            "higher_is_better": False, "dtype": "bf16 net / f32 projector", "data": "synthetic",
-           "value": float(np.median([r["warm_time_s"] for r in ok])) if ok else None,
-           "cold_value": float(np.median([r["cold_time_s"] for r in results])),
-           "warm_reached": f"{len(ok)}/{len(results)}",
-           "speedup_median": float(np.median([r["cold_time_s"] / r["warm_time_s"] for r in ok])) if ok else None,
-           "sirt_iter_ms": 1e3 * t_iter, "warm_start_overhead_ms": 1e3 * t_warm0,
-           "train": {"samples": args.train_samples, "seconds": t_train, "loss_first": float(np.mean(losses[:20])),
-                     "loss_last": float(np.mean(losses[-20:]))},
-           "config": {"workload": "grid 64x48x96, 48 cone views 256^2, 1% noise", "target": args.target,
-                      "cold_cap": args.cap, "launch_fwd_adj": tuned,
-                      "sirt_projections": "on-the-fly traversal" if args.no_segments else "stored segment lists"},
-           "per_phantom": results}
+           "value": hi["warm_time_s_median"], "cold_value": hi["cold_time_s_median"],
+           "speedup_median": hi["speedup_median"], "clocks": clocks}
+    out.update({k: v for k, v in leg.items() if k not in ("unit", "higher_is_better")})
     emit(out)
 
 
