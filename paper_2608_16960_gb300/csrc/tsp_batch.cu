@@ -82,7 +82,7 @@ struct BResid {
 };
 
 template <int GK, class Op>
-__device__ __forceinline__ void trace_tile(const TGrid& G, const InstDesc& d, int64_t t, Op& op) {
+__device__ __forceinline__ void trace_tile(const TGrid& G, const InstDesc& d, int64_t t, Op& op, const ConeList& L) {
   int64_t ray;
   ff x[3], dd[3];
   if (GK == GEOM_RAYS) {
@@ -103,22 +103,25 @@ __device__ __forceinline__ void trace_tile(const TGrid& G, const InstDesc& d, in
     ray_geometry<GK>(d.ga, view, row, col, ray, x, dd);
   }
   if (!op.begin(ray)) return;
-  if (!trace_ray(G, x, dd, op)) atomicOr(&g_tsp_error_word, 1);
+  if (!trace_ray(G, x, dd, op, L)) atomicOr(&g_tsp_error_word, 1);
   op.end(ray);
 }
 
 template <class Op>
-__device__ __forceinline__ void trace_any(const TGrid& G, const InstDesc& d, int64_t t, Op& op) {
-  if (d.kind == GEOM_CONE) trace_tile<GEOM_CONE>(G, d, t, op);
-  else if (d.kind == GEOM_PARALLEL) trace_tile<GEOM_PARALLEL>(G, d, t, op);
-  else trace_tile<GEOM_RAYS>(G, d, t, op);
+__device__ __forceinline__ void trace_any(const TGrid& G, const InstDesc& d, int64_t t, Op& op, const ConeList& L) {
+  if (d.kind == GEOM_CONE) trace_tile<GEOM_CONE>(G, d, t, op, L);
+  else if (d.kind == GEOM_PARALLEL) trace_tile<GEOM_PARALLEL>(G, d, t, op, L);
+  else trace_tile<GEOM_RAYS>(G, d, t, op, L);
 }
 
 // Persistent traversal stage over all instances.
 __global__ void __launch_bounds__(512) batch_trace_kernel(const InstDesc* __restrict__ insts, int n_inst,
                                                           int64_t total_items, unsigned long long* counter, int stage,
-                                                          BatchPtrs P) {
+                                                          BatchPtrs P, int list_off, int ccap) {
+  // shared memory: the current instance's grid table, then from word list_off
+  // (the largest table) each thread's cone-crossing list of ccap entries
   extern __shared__ float smem[];
+  const ConeList L{smem + list_off + threadIdx.x, int(blockDim.x), ccap};
   __shared__ long long s_item;
   __shared__ int s_inst;
   int loaded = -1;
@@ -142,18 +145,18 @@ __global__ void __launch_bounds__(512) batch_trace_kernel(const InstDesc* __rest
     if (stage == ST_PATHLEN) {
       BPathLen op;
       op.R = P.R + d.ray0;
-      trace_any(G, d, t, op);
+      trace_any(G, d, t, op, L);
     } else if (stage == ST_UNIT) {
       BUnit op;
       op.C = P.C + d.vox0;
-      trace_any(G, d, t, op);
+      trace_any(G, d, t, op, L);
     } else if (stage == ST_RESID) {
       BResid op;
       op.x = d.x;
       op.y = d.y;
       op.R = P.R + d.ray0;
       op.r = P.r + d.ray0;
-      trace_any(G, d, t, op);
+      trace_any(G, d, t, op, L);
     } else if (d.scatter) {
       AggScatterOp<1> op;
       op.y = P.r + d.ray0;
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(512) batch_trace_kernel(const InstDesc* __rest
       op.V = d.V;
       op.n_rays = d.ga.n_rays;
       op.nb = 1;
-      trace_any(G, d, t, op);
+      trace_any(G, d, t, op, L);
     } else {
       ScatterOp<1> op;
       op.y = P.r + d.ray0;
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(512) batch_trace_kernel(const InstDesc* __rest
       op.V = d.V;
       op.n_rays = d.ga.n_rays;
       op.nb = 1;
-      trace_any(G, d, t, op);
+      trace_any(G, d, t, op, L);
     }
     __syncthreads();  // the table may be replaced by the next item
   }
@@ -247,19 +250,20 @@ tsp_status enqueue_batch(tsp_batch b, int n_iter, int flags, void* ws, cudaStrea
   P.g = reinterpret_cast<float*>(p + 2 * nr + nv);
   unsigned long long* ctr = reinterpret_cast<unsigned long long*>(p + 2 * nr + 2 * nv);
   const int n_ctr = counters_for(n_iter);
-  const size_t smem = sizeof(float) * size_t(b->max_words);
+  const int ccap = cone_cap(b->block);
+  const size_t smem = sizeof(float) * (size_t(b->max_words) + size_t(ccap) * size_t(b->block));
   const int grid_trace = b->grid_trace, grid_vox = b->grid_vox;
   const int nonneg = flags & TSP_SIRT_NONNEG;
   int c = 0;
   TSP_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * size_t(n_ctr), st));
   TSP_CUDA(cudaMemsetAsync(P.C, 0, sizeof(float) * size_t(b->total_vox), st));
   TSP_CUDA(cudaMemsetAsync(P.g, 0, sizeof(float) * size_t(b->total_vox), st));
-  batch_trace_kernel<<<grid_trace, b->block, smem, st>>>(b->d, b->n, b->total_items, ctr + c++, ST_PATHLEN, P);
-  batch_trace_kernel<<<grid_trace, b->block, smem, st>>>(b->d, b->n, b->total_items, ctr + c++, ST_UNIT, P);
+  batch_trace_kernel<<<grid_trace, b->block, smem, st>>>(b->d, b->n, b->total_items, ctr + c++, ST_PATHLEN, P, b->max_words, ccap);
+  batch_trace_kernel<<<grid_trace, b->block, smem, st>>>(b->d, b->n, b->total_items, ctr + c++, ST_UNIT, P, b->max_words, ccap);
   batch_voxel_kernel<<<grid_vox, 256, 0, st>>>(b->d, b->n, b->total_vox, ctr + c++, 0, 0, P);
   for (int it = 0; it < n_iter; ++it) {
-    batch_trace_kernel<<<grid_trace, b->block, smem, st>>>(b->d, b->n, b->total_items, ctr + c++, ST_RESID, P);
-    batch_trace_kernel<<<grid_trace, b->block, smem, st>>>(b->d, b->n, b->total_items, ctr + c++, ST_SCATTER, P);
+    batch_trace_kernel<<<grid_trace, b->block, smem, st>>>(b->d, b->n, b->total_items, ctr + c++, ST_RESID, P, b->max_words, ccap);
+    batch_trace_kernel<<<grid_trace, b->block, smem, st>>>(b->d, b->n, b->total_items, ctr + c++, ST_SCATTER, P, b->max_words, ccap);
     batch_voxel_kernel<<<grid_vox, 256, 0, st>>>(b->d, b->n, b->total_vox, ctr + c++, 1, nonneg, P);
   }
   TSP_CUDA(cudaGetLastError());
@@ -339,15 +343,18 @@ extern "C" tsp_status tsp_batch_create(const tsp_batch_item* items, int n_items,
     delete b;
     return cuda_fail(e, "tsp_batch_create: upload");
   }
-  if (size_t(b->max_words) * sizeof(float) > 48 * 1024) {
+  const size_t smem = sizeof(float) * (size_t(b->max_words) + size_t(cone_cap(b->block)) * size_t(b->block));
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+  if (smem + 1024 > size_t(optin)) {
     cudaFree(b->d);
     delete b;
-    return fail(TSP_ENOTSUP, "tsp_batch_create: grid tables exceed 48 KB");
+    return fail(TSP_ENOTSUP, "tsp_batch_create: grid tables and cone lists exceed a block's shared memory");
   }
+  allow_smem(batch_trace_kernel, smem);
   int sms = 152, per_sm = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_trace_kernel, b->block,
-                                                sizeof(float) * size_t(b->max_words));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_trace_kernel, b->block, smem);
   b->grid_trace = std::max(1, per_sm) * sms;
   b->grid_vox = 4 * sms;
   *out = b;

@@ -120,8 +120,10 @@ __device__ __forceinline__ bool ray_of_thread(const GeomArgs& ga, int tw, int64_
   return true;
 }
 
+// Shared memory: the grid table, then each thread's cone-crossing list of
+// ccap entries (thread i's entry j at word words + j * blockDim + i).
 template <int GK, class Op>
-__global__ void __launch_bounds__(512) trace_kernel(GridDesc gd, GeomArgs ga, Op op, int tw) {
+__global__ void __launch_bounds__(512) trace_kernel(GridDesc gd, GeomArgs ga, Op op, int tw, int ccap) {
   extern __shared__ float smem[];
   load_table(gd, smem);
   const TGrid G = tgrid_from_smem(gd, smem);
@@ -129,19 +131,28 @@ __global__ void __launch_bounds__(512) trace_kernel(GridDesc gd, GeomArgs ga, Op
   ff x[3], d[3];
   if (!ray_of_thread<GK>(ga, tw, ray, x, d)) return;
   if (!op.begin(ray)) return;
-  if (!trace_ray(G, x, d, op)) atomicOr(&g_tsp_error_word, 1);
+  const ConeList L{smem + gd.words + threadIdx.x, int(blockDim.x), ccap};
+  if (!trace_ray(G, x, d, op, L)) atomicOr(&g_tsp_error_word, 1);
   op.end(ray);
 }
+
+// Cone-crossing list entries per thread: 48 up to 128 threads per block
+// (24 KB per block; one ray in two hundred at the paper-scale workload has
+// more and refills its list), proportionally fewer for larger blocks. At most
+// 64, the bits of the walk's direction mask.
+inline int cone_cap(int block_threads) { return block_threads <= 128 ? 48 : (48 * 128) / block_threads; }
 
 struct LaunchShape {
   dim3 grid, block;
   size_t smem;
+  int ccap;
 };
 
 inline LaunchShape shape_for(const tsp_grid_s* grid, const tsp_geom_s* geom, const tsp_launch& l) {
   LaunchShape s;
   s.block = dim3(l.block_threads);
-  s.smem = sizeof(float) * size_t(grid->words);
+  s.ccap = cone_cap(l.block_threads);
+  s.smem = sizeof(float) * (size_t(grid->words) + size_t(s.ccap) * size_t(l.block_threads));
   if (geom->kind == GEOM_RAYS) {
     s.grid = dim3(unsigned((geom->n_rays + l.block_threads - 1) / l.block_threads));
   } else {
@@ -151,6 +162,13 @@ inline LaunchShape shape_for(const tsp_grid_s* grid, const tsp_geom_s* geom, con
   return s;
 }
 
+// Dynamic shared memory above the default 48 KB (tables of the largest grids)
+// needs the kernel's opt-in, set on the current device before the launch.
+template <class K>
+inline void allow_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+}
+
 // Launch trace_kernel for the geometry kind of `geom`.
 template <class Op>
 void launch_trace(const tsp_grid_s* grid, const tsp_geom_s* geom, const tsp_launch& l, const Op& op,
@@ -158,10 +176,16 @@ void launch_trace(const tsp_grid_s* grid, const tsp_geom_s* geom, const tsp_laun
   const LaunchShape s = shape_for(grid, geom, l);
   const GridDesc gd = grid->desc();
   const GeomArgs ga = geom_args(geom);
-  if (geom->kind == GEOM_CONE) trace_kernel<GEOM_CONE, Op><<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w);
-  else if (geom->kind == GEOM_PARALLEL)
-    trace_kernel<GEOM_PARALLEL, Op><<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w);
-  else trace_kernel<GEOM_RAYS, Op><<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w);
+  if (geom->kind == GEOM_CONE) {
+    allow_smem(trace_kernel<GEOM_CONE, Op>, s.smem);
+    trace_kernel<GEOM_CONE, Op><<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w, s.ccap);
+  } else if (geom->kind == GEOM_PARALLEL) {
+    allow_smem(trace_kernel<GEOM_PARALLEL, Op>, s.smem);
+    trace_kernel<GEOM_PARALLEL, Op><<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w, s.ccap);
+  } else {
+    allow_smem(trace_kernel<GEOM_RAYS, Op>, s.smem);
+    trace_kernel<GEOM_RAYS, Op><<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w, s.ccap);
+  }
 }
 
 // Validation shared by the entry points that launch traversals.

@@ -21,9 +21,14 @@
 //     theta increasing through it:  t = (b2 n_z c + Q W) / (Q c - n_z W)
 //     (the roots of the cone quadratic of refs [28],[29], each tagged with its
 //      Eq. 12 direction; a non-positive denominator puts the root at infinity)
-//   half-plane j at azimuth psi_j: t = (q_y cos psi_j - q_x sin psi_j) / den_j,
-//     den_j = n_x sin psi_j - n_y cos psi_j, on the half-plane iff den_j m_z < 0
-//     where m_z = (q x n)_z (Eq. 13: the azimuth grows iff m_z > 0).
+//   half-plane j at azimuth psi_j, w_j = (cos psi_j, sin psi_j): measured from
+//     t_a, where the line's horizontal projection passes closest to the z axis,
+//     t = t_a - (m_z / |n_xy|^2) (n_xy . w_j) / den_j,  den_j = n_xy x w_j
+//     = n_x sin psi_j - n_y cos psi_j, on the half-plane iff den_j m_z < 0 where
+//     m_z = (q x n)_z (Eq. 13: the azimuth grows iff m_z > 0). A plane parallel
+//     to the line within rounding (den_j ~ 0) is stepped across at the start
+//     if the line comes from its direction (n_xy . w_j < 0), never crossed if
+//     it heads along it.
 // cos(theta) along the line peaks (Q > 0) or dips (Q < 0) once, at
 // t_e = b2 n_z / Q, with value sign(Q) sqrt(Q^2/b2 + n_z^2); before/after that
 // point theta moves monotonically, which fixes which cone comes next.
@@ -218,15 +223,22 @@ struct RayState {
   // line
   float qx, qy, qz, nx, ny, nz, b2;
   float b2lo;          // b2 + b2lo = squared impact parameter to ~2^-46
+  float b2nz;          // b2 n_z (the cone numerators)
   ff mxy2, mz2;        // |(q cross n)_xy|^2 and (q cross n)_z^2 in float-float
   // radial
   int ir, ir_next;
   bool r_out;
   float tr;
   // polar
-  int ie, ie_next;
-  bool th_br2;   // past the extremum of theta
+  int ie;
+  int gie;       // the cone generator's region (after the last crossing it produced)
+  bool th_br2;   // the generator is past the extremum of theta
   int th_mode;   // 0 walk, 1 no crossings, 2 one jump pending (line through the origin)
+  int ie_jump;   // th_mode 2: the polar region after the jump
+  int cn, ci;    // crossings in the cone list, index of the next one
+  unsigned long long cmask;  // bit i: crossing i of the list raises the polar index (else lowers it)
+  bool cmore;    // the list filled up: more crossings may follow
+  float tgen;    // the last crossing produced (each is clamped to it)
   float th_sg, th_fe, th_te;
   float tth;
   // azimuth
@@ -234,6 +246,9 @@ struct RayState {
   int ia;        // azimuth voxel index of sector sec (-1 outside a wedge)
   int ph_mode;   // 0 walk, 1 no crossings, 2 one jump pending (line meets the z axis)
   float mz;
+  float pk;      // m_z / |n_xy|^2
+  float ptax;    // t_a: closest approach of the horizontal projection to the z axis
+  int pstop;     // half-plane the line heads along (parallel within rounding): never crossed; -1 none
   float tph;
 };
 
@@ -278,42 +293,78 @@ TSP_HD float cone_w(const TGrid& G, const RayState& s, int k) {
   return T_SQRTA(fmaxf(w2, 0.0f));
 }
 
-TSP_HD void theta_next(const TGrid& G, RayState& s) {
-  if (s.th_mode != 0) {
-    s.tth = INFINITY;
-    return;
-  }
+// Next crossing of the cone family after the generator's region s.gie (in
+// its phase s.th_br2): t before clamping and the direction (+1: theta grows,
+// the polar index goes up; -1: it goes down). False when none is left.
+TSP_HD bool theta_gen(const TGrid& G, RayState& s, float& t, int& dir) {
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
     const bool dec = s.th_br2 ? (s.th_sg < 0.0f) : (s.th_sg > 0.0f);
     const float lim = s.th_br2 ? s.nz : s.th_fe;
     if (dec) {  // theta decreasing: next is the cone at the region's small-theta side
-      const int k = s.ie;
+      const int k = s.gie;
       if (k >= 0 && G.C[k] < lim) {
         const float c = G.C[k];
         const float W = cone_w(G, s, k);
-        const float num = T_SUB(T_MUL(T_MUL(s.b2, s.nz), c), T_MUL(s.qz, W));
-        const float den = T_ADD(T_MUL(s.qz, c), T_MUL(s.nz, W));
-        s.tth = den > 0.0f ? T_DIV(num, den) : (s.th_br2 ? INFINITY : -INFINITY);
-        s.ie_next = k - 1;
-        return;
+        const float num = fmaf(-s.qz, W, T_MUL(s.b2nz, c));
+        const float den = fmaf(s.nz, W, T_MUL(s.qz, c));
+        t = den > 0.0f ? T_DIV(num, den) : (s.th_br2 ? INFINITY : -INFINITY);
+        dir = -1;
+        s.gie = k - 1;
+        return t < INFINITY;
       }
     } else {  // theta increasing: next is the cone at the region's large-theta side
-      const int k = s.ie + 1;
+      const int k = s.gie + 1;
       if (k <= G.Ne && G.C[k] > lim) {
         const float c = G.C[k];
         const float W = cone_w(G, s, k);
-        const float num = T_ADD(T_MUL(T_MUL(s.b2, s.nz), c), T_MUL(s.qz, W));
-        const float den = T_SUB(T_MUL(s.qz, c), T_MUL(s.nz, W));
-        s.tth = den > 0.0f ? T_DIV(num, den) : (s.th_br2 ? INFINITY : -INFINITY);
-        s.ie_next = k;
-        return;
+        const float num = fmaf(s.qz, W, T_MUL(s.b2nz, c));
+        const float den = fmaf(-s.nz, W, T_MUL(s.qz, c));
+        t = den > 0.0f ? T_DIV(num, den) : (s.th_br2 ? INFINITY : -INFINITY);
+        dir = 1;
+        s.gie = k;
+        return t < INFINITY;
       }
     }
     if (s.th_br2) break;
     s.th_br2 = true;  // no more crossings before the extremum: continue past it
   }
-  s.tth = INFINITY;
+  return false;
+}
+
+// Cone crossings are produced ahead of the walk, up to L.cap at a time, into
+// a per-ray list (shared memory on the device: entry i at t[i * stride]).
+// Every lane of a warp fills its list in the same loop, so the crossing
+// arithmetic runs in lockstep instead of inside the walk's divergent
+// three-way step, where a lane needs a cone crossing in about one step in
+// eight. Each crossing is clamped to the one before, as the walk clamps a
+// next crossing to where it stands.
+struct ConeList {
+  float* t;
+  int stride, cap;
+};
+
+TSP_HD void cone_fill(const TGrid& G, RayState& s, const ConeList& L) {
+  int n = 0;
+  unsigned long long mask = 0ull;
+  float prev = s.tgen, first = INFINITY;
+#pragma unroll 1
+  for (; n < L.cap; ++n) {
+    float t;
+    int dir;
+    if (!theta_gen(G, s, t, dir)) break;
+    t = fmaxf(t, prev);
+    prev = t;
+    if (n == 0) first = t;
+    L.t[n * L.stride] = t;
+    mask |= (unsigned long long)(dir > 0) << n;
+  }
+  s.cmore = n == L.cap;
+  s.cn = n;
+  s.ci = 0;
+  s.cmask = mask;
+  s.tgen = prev;
+  s.tth = first;
 }
 
 TSP_HD void phi_next(const TGrid& G, RayState& s) {
@@ -324,10 +375,10 @@ TSP_HD void phi_next(const TGrid& G, RayState& s) {
   const bool ccw = s.mz > 0.0f;
   const int j = ccw ? (s.sec + 1 == G.M ? 0 : s.sec + 1) : s.sec;
   const float pc = G.PC[j], ps = G.PS[j];
-  const float den = T_SUB(T_MUL(s.nx, ps), T_MUL(s.ny, pc));
-  if (ccw ? den < 0.0f : den > 0.0f) {
-    const float num = T_SUB(T_MUL(s.qy, pc), T_MUL(s.qx, ps));
-    s.tph = T_DIV(num, den);
+  const float den = fmaf(s.nx, ps, -T_MUL(s.ny, pc));  // n_xy x w_j
+  if ((ccw ? den < 0.0f : den > 0.0f) && j != s.pstop) {
+    const float nw = fmaf(s.nx, pc, T_MUL(s.ny, ps));  // n_xy . w_j
+    s.tph = fmaf(-s.pk, T_DIV(nw, den), s.ptax);
     s.sec_next = ccw ? j : (s.sec == 0 ? G.M - 1 : s.sec - 1);
   } else {
     s.tph = INFINITY;
@@ -345,12 +396,13 @@ struct op_has_gap<Op, decltype(void(static_cast<Op*>(nullptr)->gap()))> {
   static constexpr bool value = true;
 };
 
-// Trace one ray from start x along direction d (need not be unit).
+// Trace one ray from start x along direction d (need not be unit); L is the
+// ray's cone-crossing list (at least one entry).
 // op(voxel, dl) is called for every valid segment in order along the ray
 // (and op.gap() for the pieces in between that hold no voxel, if Op has it).
 // Returns false if the step cap was hit (an internal inconsistency).
 template <class Op>
-TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op) {
+TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, const ConeList& L) {
   const float xx = x[0].hi, xy = x[1].hi, xz = x[2].hi;
   // The direction is first scaled by a power of two that puts its largest
   // component in [0.5, 1). The scaling is exact, so every quantity below is the
@@ -401,7 +453,10 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op) {
   const ff b2 = ff_add(s.mxy2, s.mz2);
   s.b2 = b2.hi;
   s.b2lo = b2.lo;
-  s.mz = mnz.hi;  // only its sign is used: the azimuth grows along the ray iff m_z > 0 (Eq. 13)
+  s.b2nz = T_MUL(s.b2, s.nz);
+  // m_z = (q x n)_z: its sign gives the azimuth's direction along the ray (it
+  // grows iff m_z > 0, Eq. 13); |m_z| / |n_xy| is the line's distance from the z axis
+  s.mz = mnz.hi;
   s.qx = qxf.hi;
   s.qy = qyf.hi;
   s.qz = qzf.hi;
@@ -452,20 +507,46 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op) {
   s.sec = classify_sector(G, px, py);
   float t_ax = INFINITY;
   int sec_ax = 0;
-  // A line whose distance from the z axis, |m_z| / |n_xy|, is below 2^-22 of
-  // the start's size meets the axis as far as float32 rays can tell: rounding
-  // the inputs moves a line through the axis by about that much. Walking its
-  // azimuth plane by plane would hinge on half-plane tests that see only
-  // rounding noise for the plane the line lies in (and could stop the sweep
-  // past the axis); taking the jump instead moves the path near the axis
-  // between neighbouring sectors.
+  // Half-plane crossings are measured from t_a, where the line's horizontal
+  // projection passes closest to the z axis (t_a in float-float from q and n):
+  // their offsets from it, (m_z / |n_xy|^2) (n_xy . w) / (n_xy x w), keep
+  // float32 relative precision however close the line passes to the axis,
+  // where a crossing formed from q alone loses it to cancellation (near the
+  // axis the whole azimuth sweep happens within |m_z| / |n_xy|^2 of t_a). A
+  // line whose sweep is shorter than an ulp of its half-chord meets the axis
+  // as far as float32 can tell: its azimuth jumps by pi there.
   const float nxy = fmaf(s.nx, s.nx, T_MUL(s.ny, s.ny));
-  const float xsz = T_ADD(T_ADD(fabsf(xx), fabsf(xy)), fabsf(xz));
-  if (fabsf(s.mz) > T_MUL(T_MUL(0x1p-22f, T_SQRT(nxy)), xsz)) {
+  if (nxy > 0.0f) {
+    const ff nn = ff_add(ff_mul(nxf, nxf), ff_mul(nyf, nyf));
+    s.ptax = -ff_div(ff_add(ff_mul(qxf, nxf), ff_mul(qyf, nyf)), nn).hi;
+    s.pk = T_DIV(s.mz, nn.hi);
+  }
+  s.pstop = -1;
+  if (nxy > 0.0f && fabsf(s.pk) > T_MUL(0x1p-24f, sout)) {
     s.ph_mode = 0;
+    // Half-planes parallel to the line within rounding of n and of the table
+    // (|n_xy x w| <= 2^-21 |n_xy|) can only sit at the two ends of the sweep,
+    // where their crossing test sees noise. The one the line comes from
+    // (n_xy . w < 0) can only be the first plane ahead, and the line lies on
+    // it there: the walk steps across it at once. The one the line heads
+    // along (n_xy . w > 0) is never crossed.
+    const float pde = T_MUL(0x1p-21f, T_SQRT(nxy));
+    const bool ccw = s.mz > 0.0f;
+    const int j0 = ccw ? (s.sec + 1 == G.M ? 0 : s.sec + 1) : s.sec;
+    if (fabsf(fmaf(s.nx, G.PS[j0], -T_MUL(s.ny, G.PC[j0]))) <= pde &&
+        fmaf(s.nx, G.PC[j0], T_MUL(s.ny, G.PS[j0])) < 0.0f)
+      s.sec = ccw ? j0 : (s.sec == 0 ? G.M - 1 : s.sec - 1);
+    const int se = classify_sector(G, s.nx, s.ny);  // the sector of the direction of travel
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int j = e == 0 ? se : (se + 1 == G.M ? 0 : se + 1);
+      if (fabsf(fmaf(s.nx, G.PS[j], -T_MUL(s.ny, G.PC[j]))) <= pde &&
+          fmaf(s.nx, G.PC[j], T_MUL(s.ny, G.PS[j])) > 0.0f)
+        s.pstop = j;
+    }
   } else {
     if (nxy > 0.0f) {  // the line meets the z axis: azimuth jumps by pi there
-      t_ax = -T_DIV(fmaf(s.qx, s.nx, T_MUL(s.qy, s.ny)), nxy);
+      t_ax = s.ptax;
       s.ph_mode = t_ax > tcur ? 2 : 1;
       sec_ax = classify_sector(G, s.nx, s.ny);
       if (t_ax <= tcur) s.sec = sec_ax;  // at or past the axis: the direction's azimuth
@@ -476,12 +557,18 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op) {
 
   radial_next(G, s);
   s.tr = fmaxf(s.tr, tcur);
+  s.gie = s.ie;
+  s.tgen = tcur;
+  s.cn = s.ci = 0;
+  s.cmask = 0ull;
+  s.cmore = false;
   if (s.th_mode == 2) {
     s.tth = 0.0f;
-    s.ie_next = classify_theta(G, s.nz, 1.0f);
+    s.ie_jump = classify_theta(G, s.nz, 1.0f);
+  } else if (s.th_mode == 0) {
+    cone_fill(G, s, L);
   } else {
-    theta_next(G, s);
-    s.tth = fmaxf(s.tth, tcur);
+    s.tth = INFINITY;
   }
   if (s.ph_mode == 2) {
     s.tph = t_ax;
@@ -508,10 +595,16 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op) {
       radial_next(G, s);
       s.tr = fmaxf(s.tr, tcur);
     } else if (s.tth <= s.tph) {
-      s.ie = s.ie_next;
-      if (s.th_mode == 2) s.th_mode = 1;
-      theta_next(G, s);
-      s.tth = fmaxf(s.tth, tcur);
+      if (s.th_mode == 2) {  // through the origin: the one jump
+        s.ie = s.ie_jump;
+        s.th_mode = 1;
+        s.tth = INFINITY;
+      } else {
+        s.ie += ((s.cmask >> s.ci) & 1ull) ? 1 : -1;
+        if (++s.ci < s.cn) s.tth = L.t[s.ci * L.stride];
+        else if (s.cmore) cone_fill(G, s, L);
+        else s.tth = INFINITY;
+      }
     } else {
       s.sec = s.sec_next;
       s.ia = G.SEC[s.sec];

@@ -23,11 +23,22 @@ struct Record {
 }  // namespace
 
 // Walks n rays (float32 starts / directions, [n][3]) through the grid given
-// by its edges. Ray i writes at most cap (voxel, length) pairs at i * cap and
+// by its edges, with a cone-crossing list of 32 entries. Ray i writes at most cap (voxel, length) pairs at i * cap and
 // its full segment count to cnt[i]. Returns the number of rays that hit the
 // walk's step cap (an internal inconsistency), or -1 for an empty grid.
+extern "C" int host_walk_list(const double* r, int nr, const double* th, int nt, const double* ph, int np, long n,
+                              const float* x, const float* d, int cap, int* vox, float* len, int* cnt, int ccap);
+
 extern "C" int host_walk(const double* r, int nr, const double* th, int nt, const double* ph, int np, long n,
                          const float* x, const float* d, int cap, int* vox, float* len, int* cnt) {
+  return host_walk_list(r, nr, th, nt, ph, np, n, x, d, cap, vox, len, cnt, 32);
+}
+
+// As host_walk, with a cone-crossing list of ccap entries (1..32): lists
+// shorter than a ray's cone crossings are refilled during the walk.
+extern "C" int host_walk_list(const double* r, int nr, const double* th, int nt, const double* ph, int np, long n,
+                              const float* x, const float* d, int cap, int* vox, float* len, int* cnt, int ccap) {
+  if (ccap < 1 || ccap > 32) return -1;
   if (nr < 2 || nt < 2 || np < 2) return -1;
   tsp_grid_s g;
   std::vector<float> table;
@@ -49,7 +60,8 @@ extern "C" int host_walk(const double* r, int nr, const double* th, int nt, cons
       dd[c] = tsp::ff{d[3 * i + c], 0.0f};
     }
     Record rec{vox + i * cap, len + i * cap, cap};
-    if (!tsp::trace_ray(G, xx, dd, rec)) ++bad;
+    float cone_buf[32];
+    if (!tsp::trace_ray(G, xx, dd, rec, tsp::ConeList{cone_buf, 1, ccap})) ++bad;
     cnt[i] = rec.n;
   }
   return bad;

@@ -9,6 +9,8 @@ tsp_table.h), built for the host, against the FP64 oracle on the CPU.
   the ray moved just off that surface.
 - Voxel sequences equal the oracle's (Eq. 4) wherever no two crossings lie
   within float32 reach of each other.
+- Lines passing just off the z axis, from horizontal to nearly vertical,
+  meet the parity rule too.
 
 No GPU: this checks the walk's index logic wherever the driver runs the CPU
 tests. Its host build rounds divisions and square roots correctly, so lengths
@@ -25,7 +27,7 @@ import pytest
 import oracle
 from paper_2608_16960_gb300 import synth
 
-from _util import parity
+from _util import K_POS, U32, _crossing_gain, parity
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -51,6 +53,8 @@ def _lib():
     L.host_walk.restype = ctypes.c_int
     L.host_walk.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, ctypes.c_long, P, P, ctypes.c_int, P, P,
                             P]
+    L.host_walk_list.restype = ctypes.c_int
+    L.host_walk_list.argtypes = L.host_walk.argtypes + [ctypes.c_int]
     return L
 
 
@@ -59,8 +63,9 @@ def lib():
     return _lib()
 
 
-def walk(lib, edges, starts, dirs, cap=1024):
-    """Segments of rays given as float32 (n, 3) starts and directions."""
+def walk(lib, edges, starts, dirs, cap=1024, ccap=32):
+    """Segments of rays given as float32 (n, 3) starts and directions; ccap is
+    the length of the walk's cone-crossing list."""
     r, t, p = [np.ascontiguousarray(a, np.float64) for a in (edges.r, edges.theta, edges.phi)]
     x = np.ascontiguousarray(starts, np.float32)
     d = np.ascontiguousarray(dirs, np.float32)
@@ -68,8 +73,8 @@ def walk(lib, edges, starts, dirs, cap=1024):
     vox = np.zeros((n, cap), np.int32)
     ln = np.zeros((n, cap), np.float32)
     cnt = np.zeros(n, np.int32)
-    bad = lib.host_walk(r.ctypes.data, len(r), t.ctypes.data, len(t), p.ctypes.data, len(p), n, x.ctypes.data,
-                        d.ctypes.data, cap, vox.ctypes.data, ln.ctypes.data, cnt.ctypes.data)
+    bad = lib.host_walk_list(r.ctypes.data, len(r), t.ctypes.data, len(t), p.ctypes.data, len(p), n, x.ctypes.data,
+                             d.ctypes.data, cap, vox.ctypes.data, ln.ctypes.data, cnt.ctypes.data, ccap)
     assert bad == 0
     assert cnt.max(initial=0) <= cap
     return vox, ln, cnt
@@ -286,3 +291,64 @@ def test_extreme_direction_scales(lib):
         ref = oracle.forward(e, st.astype(np.float64), di.astype(np.float64), rho)
         assert np.count_nonzero(ref) > 50
         parity(y, ref, what=f"host walk, directions x {scale:g}, starts at {dist:g} R")
+
+
+def test_lines_passing_just_off_the_axis(lib):
+    """Lines passing 1e-7 .. 1e-3 from the z axis, from horizontal to within
+    1e-3 of vertical, starting 2 to 100 grid radii away. Near the axis the
+    whole azimuth sweep happens within |m_z| / |n_xy|^2 of the point t_a
+    where the line's horizontal projection passes closest to the axis; the
+    walk measures half-plane crossings from t_a (float-float), so these rays
+    meet the parity rule. The bound adds, for each crossing, float32 position
+    error over the sine of its grazing angle (tests/_util.py): a line nearly
+    parallel to a half-plane far from the axis crosses it at a grazing angle,
+    like a line grazing a sphere."""
+    e = synth.grid_edges(20, 15, 30)
+    rho = synth.uniform_volume(e.shape, 6, 0.1, 1.0)
+    R = float(e.r[-1])
+    rng = np.random.default_rng(7)
+    rays = []
+    for S in (2.0, 10.0, 100.0):
+        for nxy in (1.0, 0.1, 0.01, 1e-3):
+            for dist in (1e-7, 1e-6, 1e-5, 1e-4, 1e-3):
+                for _ in range(25):
+                    a = rng.uniform(0, 2 * np.pi)
+                    u = np.array([np.cos(a), np.sin(a), 0.0])
+                    w = np.array([-np.sin(a), np.cos(a), 0.0])
+                    n = nxy * u + np.array([0.0, 0.0, np.sqrt(1.0 - nxy * nxy) * rng.choice([-1.0, 1.0])])
+                    p0 = dist * w + np.array([0.0, 0.0, rng.uniform(-0.5, 0.5) * R])
+                    rays.append((p0 - S * R * n, n))
+    st = np.array([a for a, _ in rays], np.float32)
+    di = np.array([b for _, b in rays], np.float32)
+    y = forward(lib, e, st, di, rho)
+    s64, d64 = st.astype(np.float64), di.astype(np.float64)
+    ref = oracle.forward(e, s64, d64, rho)
+    big = np.max(np.abs(ref))
+    err = np.abs(y - ref)
+    plain = 1e-4 * np.maximum(np.abs(ref), 1e-2 * big)
+    over = np.flatnonzero(err > plain)
+    for i in over:  # only these need the crossing term
+        n = d64[i] / np.linalg.norm(d64[i])
+        vox, l0, ln = oracle.ray_pieces(e, s64[i], d64[i])
+        g = _crossing_gain(e, s64[i][None, :] + np.concatenate([l0, l0 + ln])[:, None] * n[None, :], n, R)
+        allow = float(rho.max()) * K_POS * U32 * R * g.sum()
+        assert err[i] <= plain[i] + allow, (i, y[i], ref[i], allow, g.max())
+    assert len(over) <= 0.01 * len(rays), len(over)
+
+
+def test_cone_list_refills_give_the_same_segments(lib):
+    """The walk produces cone crossings ahead into a list and refills it when a
+    ray has more crossings than the list holds: lists of 1, 2, 3 and 7
+    entries give bit-identical segments to one of 32 (paper-scale grid, rays
+    with up to 50 cone crossings)."""
+    e = synth.grid_edges(100, 60, 120)
+    s, d = synth.random_rays(600, 41)
+    st, di = s.T, d.T
+    v0, l0, c0 = walk(lib, e, st, di)
+    assert c0.max() > 100
+    for ccap in (1, 2, 3, 7):
+        v1, l1, c1 = walk(lib, e, st, di, ccap=ccap)
+        assert np.array_equal(c0, c1), ccap
+        m = np.arange(v0.shape[1])[None, :] < c0[:, None]
+        assert np.array_equal(np.where(m, v0, 0), np.where(m, v1, 0)), ccap
+        assert np.array_equal(np.where(m, l0, 0).view(np.uint32), np.where(m, l1, 0).view(np.uint32)), ccap
