@@ -121,10 +121,12 @@ def forward(params, a, keep=False, exact=False):
     return out
 
 
-def loss_and_grads(params, a, target, exact=False):
+def loss_and_grads(params, a, target, exact=False, keep=False):
     """MSE loss and float64 gradients (dw, db) per layer. The gradients of the
     four 32 -> 32 layers' pre-activations are rounded to bfloat16 before their
-    weight and input gradients are formed (tensor-core operands on the GPU)."""
+    weight and input gradients are formed (tensor-core operands on the GPU).
+    With keep=True also returns, per layer, the two operands of its weight
+    gradient (layer input, output gradient), as the sums used them."""
     rnd = (lambda v: np.asarray(v, np.float64)) if exact else (lambda v: bf16(np.asarray(v, np.float32)))
     f32 = (lambda v: np.asarray(v, np.float64)) if exact else (lambda v: np.asarray(v, np.float32))
     out, (a16, ws, h, masks) = forward(params, a, keep=True, exact=exact)
@@ -133,13 +135,19 @@ def loss_and_grads(params, a, target, exact=False):
     loss = float(np.mean(diff ** 2))
     g_out = (2.0 / n) * diff
     grads = [None] * 6
+    operands = [None] * 6
     g6 = f32(g_out[..., None])
     grads[5] = conv_wgrad(h[4], g6, exact=exact)
+    operands[5] = (h[4], g6)
     g_h = conv_dgrad(g6, ws[5], exact=exact)
     for k in range(4, 0, -1):
         g_z = rnd(np.where(masks[k], g_h, 0.0))
         grads[k] = conv_wgrad(h[k - 1], g_z, exact=exact)
+        operands[k] = (h[k - 1], g_z)
         g_h = g_h + conv_dgrad(g_z, ws[k], exact=exact)
     g_z1 = f32(np.where(masks[0], g_h, 0.0))
     grads[0] = conv_wgrad(a16, g_z1, exact=exact)
+    operands[0] = (a16, g_z1)
+    if keep:
+        return loss, grads, operands
     return loss, grads

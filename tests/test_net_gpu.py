@@ -154,3 +154,70 @@ def test_bounded_wait_runs_out_and_the_next_call_matches_the_oracle(case):
     assert L.tsp_device_status(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(code)) == 0
     assert code.value == 0
 
+
+
+@pytest.fixture(scope="module")
+def c5_case():
+    """The warm-start workload's grid (64 x 48 x 96), batch 2, with the oracle's
+    forward pass and gradients (float64 sums; several seconds of CPU time)."""
+    shape, B = (64, 48, 96), 2
+    params = _params(3)
+    rng = synth.SplitMix64(4)
+    a = np.abs(rng.normal(B * int(np.prod(shape)))).reshape(B, *shape).astype(np.float32)
+    t = np.abs(rng.normal(B * int(np.prod(shape)))).reshape(B, *shape).astype(np.float32)
+    net = WarmStartNet(shape, max_batch=B)
+    net.set_params(_flat(params))
+    out = net.forward(torch.tensor(a, device=DEV)).cpu().numpy()
+    acts = [net.activation(k, B) for k in range(5)]
+    loss = net.loss_grad(torch.tensor(a, device=DEV), torch.tensor(t, device=DEV))
+    grads = _unflat(net.get_grads())
+    ref, (a16, ws, h, masks) = onet.forward(params, a, keep=True)
+    ref_loss, ref_grads, operands = onet.loss_and_grads(params, a, t, keep=True)
+    return shape, B, params, a, t, out, acts, loss, grads, ref, a16, ws, h, operands, ref_loss, ref_grads
+
+
+def test_c5_shape_outputs_and_activations_elementwise(c5_case):
+    """4096 sampled output positions element by element: |out - ref| within
+    2^-7 of S = sum |w6| |h5| over the output's receptive inputs (two bfloat16
+    ulps of every input of the output layer) plus float32 rounding; the five
+    activations at the same positions by the two-ulp rule of the smaller
+    shapes."""
+    shape, B, params, a, t, out, acts, loss, grads, ref, a16, ws, h, operands, ref_loss, ref_grads = c5_case
+    S = onet.conv_fwd(np.abs(h[4]), np.abs(ws[5]), np.zeros(1, np.float32))[..., 0]
+    idx = synth.SplitMix64(5).integers(0, out.size - 1, 4096)
+    o, r, sv = out.reshape(-1)[idx], ref.reshape(-1)[idx], S.reshape(-1)[idx]
+    bound = 2.0 ** -7 * sv + 2.0 ** -20 * (np.abs(r) + sv)
+    err = np.abs(o - r)
+    print(f"c5 outputs: worst err / bound {np.max(err / bound):.3f}, median {np.median(err / bound):.3e}")
+    assert np.all(err <= bound), (np.flatnonzero(err > bound)[:5], np.max(err / bound))
+    vox = idx  # flat (b, r, e, a) positions
+    for k in range(5):
+        hg = acts[k].reshape(-1, 32)[vox]
+        hr = np.asarray(h[k]).reshape(-1, 32)[vox]
+        diff = np.abs(hg - hr)
+        far = np.mean(diff > np.maximum(np.abs(hr), 1e-30) * 2.0 ** -6 + 1e-6)
+        print(f"c5 h{k + 1}: beyond 2 ulps {far:.2e}")
+        assert far <= 1e-3, (k, far)
+
+
+def test_c5_shape_gradients_elementwise(c5_case):
+    """Every weight and bias gradient entry of all six layers element by
+    element: |g - ref| within 2^-6 of the entry's absolute sum G =
+    sum_v |gz[v]| |h[v + d]| over the oracle's own operands (bfloat16
+    operands: a term whose two factors each sit up to two ulps, 2^-7, from
+    the oracle's moves by up to 2^-6 of its magnitude), plus 1e-4 of the
+    largest entry of the layer. The loss within 1e-3."""
+    shape, B, params, a, t, out, acts, loss, grads, ref, a16, ws, h, operands, ref_loss, ref_grads = c5_case
+    assert abs(loss - ref_loss) <= 1e-3 * ref_loss
+    for k in range(6):
+        x_in, g_z = operands[k]
+        mags = onet.conv_wgrad(np.abs(np.asarray(x_in, np.float32)), np.abs(np.asarray(g_z, np.float32)))
+        for which in range(2):
+            gg = grads[k][which].astype(np.float64).reshape(-1)
+            rr = np.asarray(ref_grads[k][which], np.float64).reshape(-1)
+            G = np.asarray(mags[which], np.float64).reshape(-1)
+            bound = 2.0 ** -6 * G + 1e-4 * np.max(np.abs(rr))
+            err = np.abs(gg - rr)
+            print(f"c5 layer {k + 1} {'wb'[which]}: {err.size} entries, worst err / bound {np.max(err / bound):.3f}, "
+                  f"median {np.median(err / bound):.2e}, worst err / G {np.max(err[G > 0] / G[G > 0]):.2e}")
+            assert np.all(err <= bound), (k, which, np.max(err / bound))
