@@ -114,9 +114,12 @@ __device__ __forceinline__ void trace_any(const TGrid& G, const InstDesc& d, int
   else trace_tile<GEOM_RAYS>(G, d, t, op, L);
 }
 
-// Persistent traversal stage over all instances.
-__global__ void __launch_bounds__(512) batch_trace_kernel(const InstDesc* __restrict__ insts, int n_inst,
-                                                          int64_t total_items, unsigned long long* counter, int stage,
+// Persistent traversal stage over all instances, one kernel per stage (each
+// holds one per-segment operation, so the walk's registers are those of that
+// operation alone).
+template <int stage>
+__global__ void __launch_bounds__(512, 1) batch_trace_kernel(const InstDesc* __restrict__ insts, int n_inst,
+                                                          int64_t total_items, unsigned long long* counter,
                                                           BatchPtrs P, int list_off, int ccap) {
   // shared memory: the current instance's grid table, then from word list_off
   // (the largest table) each thread's cone-crossing list of ccap entries
@@ -142,22 +145,22 @@ __global__ void __launch_bounds__(512) batch_trace_kernel(const InstDesc* __rest
     }
     const TGrid G = tgrid_from_smem(d.gd, smem);
     const int64_t t = item - d.item0;
-    if (stage == ST_PATHLEN) {
+    if constexpr (stage == ST_PATHLEN) {
       BPathLen op;
       op.R = P.R + d.ray0;
       trace_any(G, d, t, op, L);
-    } else if (stage == ST_UNIT) {
+    } else if constexpr (stage == ST_UNIT) {
       BUnit op;
       op.C = P.C + d.vox0;
       trace_any(G, d, t, op, L);
-    } else if (stage == ST_RESID) {
+    } else if constexpr (stage == ST_RESID) {
       BResid op;
       op.x = d.x;
       op.y = d.y;
       op.R = P.R + d.ray0;
       op.r = P.r + d.ray0;
       trace_any(G, d, t, op, L);
-    } else if (d.scatter) {
+    } else if (d.scatter) {  // ST_SCATTER, per instance: warp-aggregated or one atomic per segment
       AggScatterOp<1> op;
       op.y = P.r + d.ray0;
       op.g = P.g + d.vox0;
@@ -222,7 +225,8 @@ struct tsp_batch_s {
   int64_t total_items = 0, total_rays = 0, total_vox = 0;
   int block = 128;
   int max_words = 0;
-  int grid_trace = 152, grid_vox = 608;  // persistent grid sizes (resident blocks x SMs)
+  int grid_stage[4] = {152, 152, 152, 152};  // persistent grid per traversal stage (resident blocks x SMs)
+  int grid_vox = 608;
   int device = 0;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
@@ -252,18 +256,22 @@ tsp_status enqueue_batch(tsp_batch b, int n_iter, int flags, void* ws, cudaStrea
   const int n_ctr = counters_for(n_iter);
   const int ccap = cone_cap(b->block);
   const size_t smem = sizeof(float) * (size_t(b->max_words) + size_t(ccap) * size_t(b->block));
-  const int grid_trace = b->grid_trace, grid_vox = b->grid_vox;
+  const int grid_vox = b->grid_vox;
   const int nonneg = flags & TSP_SIRT_NONNEG;
   int c = 0;
   TSP_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long) * size_t(n_ctr), st));
   TSP_CUDA(cudaMemsetAsync(P.C, 0, sizeof(float) * size_t(b->total_vox), st));
   TSP_CUDA(cudaMemsetAsync(P.g, 0, sizeof(float) * size_t(b->total_vox), st));
-  batch_trace_kernel<<<grid_trace, b->block, smem, st>>>(b->d, b->n, b->total_items, ctr + c++, ST_PATHLEN, P, b->max_words, ccap);
-  batch_trace_kernel<<<grid_trace, b->block, smem, st>>>(b->d, b->n, b->total_items, ctr + c++, ST_UNIT, P, b->max_words, ccap);
+  batch_trace_kernel<ST_PATHLEN><<<b->grid_stage[ST_PATHLEN], b->block, smem, st>>>(b->d, b->n, b->total_items,
+                                                                                    ctr + c++, P, b->max_words, ccap);
+  batch_trace_kernel<ST_UNIT><<<b->grid_stage[ST_UNIT], b->block, smem, st>>>(b->d, b->n, b->total_items, ctr + c++,
+                                                                              P, b->max_words, ccap);
   batch_voxel_kernel<<<grid_vox, 256, 0, st>>>(b->d, b->n, b->total_vox, ctr + c++, 0, 0, P);
   for (int it = 0; it < n_iter; ++it) {
-    batch_trace_kernel<<<grid_trace, b->block, smem, st>>>(b->d, b->n, b->total_items, ctr + c++, ST_RESID, P, b->max_words, ccap);
-    batch_trace_kernel<<<grid_trace, b->block, smem, st>>>(b->d, b->n, b->total_items, ctr + c++, ST_SCATTER, P, b->max_words, ccap);
+    batch_trace_kernel<ST_RESID><<<b->grid_stage[ST_RESID], b->block, smem, st>>>(b->d, b->n, b->total_items,
+                                                                                  ctr + c++, P, b->max_words, ccap);
+    batch_trace_kernel<ST_SCATTER><<<b->grid_stage[ST_SCATTER], b->block, smem, st>>>(b->d, b->n, b->total_items,
+                                                                                      ctr + c++, P, b->max_words, ccap);
     batch_voxel_kernel<<<grid_vox, 256, 0, st>>>(b->d, b->n, b->total_vox, ctr + c++, 1, nonneg, P);
   }
   TSP_CUDA(cudaGetLastError());
@@ -351,11 +359,18 @@ extern "C" tsp_status tsp_batch_create(const tsp_batch_item* items, int n_items,
     delete b;
     return fail(TSP_ENOTSUP, "tsp_batch_create: grid tables and cone lists exceed a block's shared memory");
   }
-  allow_smem(batch_trace_kernel, smem);
-  int sms = 152, per_sm = 1;
+  int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_trace_kernel, b->block, smem);
-  b->grid_trace = std::max(1, per_sm) * sms;
+  auto persistent_grid = [&](auto kernel) {
+    allow_smem(kernel, smem);
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, b->block, smem);
+    return std::max(1, per_sm) * sms;
+  };
+  b->grid_stage[ST_PATHLEN] = persistent_grid(batch_trace_kernel<ST_PATHLEN>);
+  b->grid_stage[ST_UNIT] = persistent_grid(batch_trace_kernel<ST_UNIT>);
+  b->grid_stage[ST_RESID] = persistent_grid(batch_trace_kernel<ST_RESID>);
+  b->grid_stage[ST_SCATTER] = persistent_grid(batch_trace_kernel<ST_SCATTER>);
   b->grid_vox = 4 * sms;
   *out = b;
   return TSP_OK;

@@ -123,7 +123,7 @@ __device__ __forceinline__ bool ray_of_thread(const GeomArgs& ga, int tw, int64_
 // Shared memory: the grid table, then each thread's cone-crossing list of
 // ccap entries (thread i's entry j at word words + j * blockDim + i).
 template <int GK, class Op>
-__global__ void __launch_bounds__(512) trace_kernel(GridDesc gd, GeomArgs ga, Op op, int tw, int ccap) {
+__global__ void __launch_bounds__(512, 1) trace_kernel(GridDesc gd, GeomArgs ga, Op op, int tw, int ccap) {
   extern __shared__ float smem[];
   load_table(gd, smem);
   const TGrid G = tgrid_from_smem(gd, smem);
