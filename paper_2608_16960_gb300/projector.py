@@ -169,15 +169,23 @@ def _launch_ptr(launch):
     return ctypes.byref(tsp_launch(*launch))
 
 
-def tsp_forward(grid: Grid, geom: Geometry, rho: torch.Tensor, launch=None) -> torch.Tensor:
+def tsp_forward(grid: Grid, geom: Geometry, rho: torch.Tensor, launch=None,
+                out: torch.Tensor | None = None) -> torch.Tensor:
     """y = F rho (Eq. 5). rho: (N_r, N_e, N_a) or (B, N_r, N_e, N_a) CUDA float32.
-    Returns y shaped like the detector: (B?,) + det_shape."""
+    Returns y shaped like the detector: (B?,) + det_shape, written into `out`
+    (contiguous float32 on rho's device, B x the detector's size) if given."""
     _require_cuda(rho, "rho")
     batched = rho.dim() == 4
     if tuple(rho.shape[-3:]) != grid.shape or rho.dim() not in (3, 4):
         raise ValueError(f"rho shape {tuple(rho.shape)} does not match grid {grid.shape}")
     B = rho.shape[0] if batched else 1
-    y = torch.empty((B,) + geom.det_shape, device=rho.device, dtype=torch.float32)
+    if out is None:
+        y = torch.empty((B,) + geom.det_shape, device=rho.device, dtype=torch.float32)
+    else:
+        _require_cuda(out, "out")
+        if out.numel() != B * geom.n_rays or not out.is_contiguous() or out.device != rho.device:
+            raise ValueError("out must be a contiguous float32 tensor of the detector's size on rho's device")
+        y = out.view((B,) + geom.det_shape)
     L = _lib.load()
     check(L.tsp_forward_ex(grid.handle, geom.handle, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                            B, _launch_ptr(launch), _stream(rho)), "tsp_forward")

@@ -277,6 +277,17 @@ def test_paper_scale_adjoint_identity(paper_scale):
         assert abs(lhs - rhs) <= 1e-5 * abs(lhs), (lhs, rhs)
 
 
+def test_forward_into_a_caller_buffer(tiny):
+    wl, grid, geom, st, di = tiny
+    rho = torch.tensor(wl.rho, device=DEV)
+    out = torch.full(geom.det_shape, -1.0, device=DEV)
+    y = tsp_forward(grid, geom, rho, out=out)
+    assert y.data_ptr() == out.data_ptr()
+    assert torch.equal(out, tsp_forward(grid, geom, rho))
+    with pytest.raises(ValueError):
+        tsp_forward(grid, geom, rho, out=torch.empty(7, device=DEV))
+
+
 def test_batched_equals_single(tiny):
     wl, grid, geom, st, di = tiny
     B = 11  # more than one chunk of 8
