@@ -386,3 +386,72 @@ def test_rays_through_the_axis_in_a_half_plane():
            if min(abs(y[i] - c[i]) for c in cands) > 1e-4 * max(max(abs(c[i]) for c in cands), 1e-2 * big)]
     assert not bad, (bad[:5], y[bad[:5]])
     assert tsp_device_status() == 0
+
+
+def test_lines_passing_just_off_the_axis():
+    """The device build on lines passing 1e-7 .. 1e-3 from the z axis, from
+    horizontal to within 1e-3 of vertical, starting 2 to 100 grid radii away
+    (the host build's set, tests/test_host_walk.py): the parity rule, plus,
+    for the few rays outside it, float32 crossing position over the sine of
+    the grazing angle at each crossing (a line nearly parallel to a
+    half-plane far from the axis)."""
+    from _util import K_POS, U32, _crossing_gain
+    e = synth.grid_edges(20, 15, 30)
+    grid = Grid.from_edges(e)
+    rho = synth.uniform_volume(e.shape, 6, 0.1, 1.0)
+    R = float(e.r[-1])
+    rng = np.random.default_rng(7)
+    rays = []
+    for S in (2.0, 10.0, 100.0):
+        for nxy in (1.0, 0.1, 0.01, 1e-3):
+            for dist in (1e-7, 1e-6, 1e-5, 1e-4, 1e-3):
+                for _ in range(25):
+                    a = rng.uniform(0, 2 * np.pi)
+                    u = np.array([np.cos(a), np.sin(a), 0.0])
+                    w = np.array([-np.sin(a), np.cos(a), 0.0])
+                    n = nxy * u + np.array([0.0, 0.0, np.sqrt(1.0 - nxy * nxy) * rng.choice([-1.0, 1.0])])
+                    p0 = dist * w + np.array([0.0, 0.0, rng.uniform(-0.5, 0.5) * R])
+                    rays.append((p0 - S * R * n, n))
+    s64 = np.array([a for a, _ in rays])
+    d64 = np.array([b for _, b in rays])
+    geom, st, di = rays_geom(s64.T, d64.T)
+    y = tsp_forward(grid, geom, torch.tensor(rho, device=DEV)).cpu().numpy().reshape(-1)
+    ref = oracle.forward(e, st.T, di.T, rho)
+    big = np.max(np.abs(ref))
+    err = np.abs(y - ref)
+    plain = 1e-4 * np.maximum(np.abs(ref), 1e-2 * big)
+    over = np.flatnonzero(err > plain)
+    for i in over:
+        x, d = st.T[i], di.T[i]
+        n = d / np.linalg.norm(d)
+        vox, l0, ln = oracle.ray_pieces(e, x, d)
+        g = _crossing_gain(e, x[None, :] + np.concatenate([l0, l0 + ln])[:, None] * n[None, :], n, R)
+        allow = float(rho.max()) * K_POS * U32 * R * g.sum()
+        assert err[i] <= plain[i] + allow, (i, y[i], ref[i], allow)
+    assert len(over) <= 0.01 * len(rays), len(over)
+    assert tsp_device_status() == 0
+
+
+def test_grid_whose_table_exceeds_48_kb_of_shared_memory():
+    """1024 x 1024 x 512 voxels (2.1 GB volume): the grid table (36 KB) and
+    the per-thread cone lists need more than the default 48 KB of dynamic
+    shared memory per block, which the launch opts into. Forward on a 64 x 64
+    cone view against the oracle on every 7th ray; the adjoint identity."""
+    e = synth.grid_edges(1024, 1024, 512)
+    grid = Grid.from_edges(e)
+    rng = synth.SplitMix64(91)
+    # a separable volume built from seeded 1-D profiles (keeps the host copy cheap)
+    fr, fe, fa = (rng.uniform(n, 0.2, 1.0).astype(np.float32) for n in e.shape)
+    rho = (fr[:, None, None] * fe[None, :, None] + fa[None, None, :]).astype(np.float32)
+    geom = Geometry.cone(np.array([[60.0, 5.0, 3.0]]), (64, 64), 30.0)
+    y = tsp_forward(grid, geom, torch.tensor(rho, device=DEV)).cpu().numpy().reshape(-1)
+    st, di = oracle.cone_rays(np.array([[60.0, 5.0, 3.0]]), 64, 64, 30.0)
+    idx = np.arange(0, len(st), 7)
+    ref = oracle.forward(e, st[idx], di[idx], rho)
+    parity(y[idx], ref, what="1024^3 grid forward")
+    yv = torch.tensor(synth.uniform_volume(geom.det_shape, 92), device=DEV)
+    x = torch.tensor(rho, device=DEV)
+    lhs = torch.dot(tsp_forward(grid, geom, x).double().ravel(), yv.double().ravel()).item()
+    rhs = torch.dot(x.double().ravel(), tsp_adjoint(grid, geom, yv).double().ravel()).item()
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs), (lhs, rhs)
+    assert tsp_device_status() == 0
