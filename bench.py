@@ -366,15 +366,32 @@ def run_ours(args):
         d_ys = [torch.empty(g.det_shape, device="cuda") for g in geoms]
         d_gs = [torch.empty(grid.shape, device="cuda") for _ in geoms]
 
+        # a second stream carries the copies that need not wait: the adjoint
+        # inputs go up while the forward runs, the detector values come back
+        # while the adjoint runs
+        side = torch.cuda.Stream()
+
         def e2e_step():
+            main = torch.cuda.current_stream()
             d_rho.copy_(h_rho, non_blocking=True)
-            for d, h in zip(d_ws, h_ws):
-                d.copy_(h, non_blocking=True)
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                for d, h in zip(d_ws, h_ws):
+                    d.copy_(h, non_blocking=True)
             for i, g in enumerate(geoms):
-                h_ys[i].copy_(tsp_forward(grid, g, d_rho, out=d_ys[i]), non_blocking=True)
+                tsp_forward(grid, g, d_rho, out=d_ys[i])
+            y_done = main.record_event()
+            main.wait_stream(side)
             for i, g in enumerate(geoms):
-                h_gs[i].copy_(tsp_adjoint(grid, g, d_ws[i], out=d_gs[i]), non_blocking=True)
-            torch.cuda.current_stream().synchronize()
+                tsp_adjoint(grid, g, d_ws[i], out=d_gs[i])
+            with torch.cuda.stream(side):
+                side.wait_event(y_done)
+                for h, d in zip(h_ys, d_ys):
+                    h.copy_(d, non_blocking=True)
+            for h, d in zip(h_gs, d_gs):
+                h.copy_(d, non_blocking=True)
+            main.wait_stream(side)
+            main.synchronize()
 
         for _ in range(2):
             e2e_step()

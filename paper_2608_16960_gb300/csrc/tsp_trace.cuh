@@ -42,6 +42,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace tsp {
 
 // Explicitly rounded arithmetic: the device build uses the round-to-nearest
@@ -392,7 +394,7 @@ struct op_has_gap {
   static constexpr bool value = false;
 };
 template <class Op>
-struct op_has_gap<Op, decltype(void(static_cast<Op*>(nullptr)->gap()))> {
+struct op_has_gap<Op, decltype(void(std::declval<Op&>().gap()))> {
   static constexpr bool value = true;
 };
 
