@@ -36,7 +36,7 @@ def outside_rays(n, seed, radius=60.0, aim=25.0):
 
 
 # --------------------------------------------------------------------------
-# closed forms (Sec. 5.1: unit-sphere test; BASELINE closed forms)
+# closed forms (Sec. 5.1: the unit-sphere test; chords of balls and shells)
 # --------------------------------------------------------------------------
 
 def test_uniform_unit_ball_chord():
