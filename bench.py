@@ -886,11 +886,14 @@ def _error_curve(ws, y, truth, x0, cap):
     return (torch.stack(errs) / tn).cpu().numpy()
 
 
-def _timed_region(fn, flush, reps=3):
+def _timed_region(fn, flush, reps=3, warmup=1):
     """Median over reps of fn's device time (CUDA events on the current stream),
-    L2 flushed before each."""
+    L2 flushed before each, after warmup untimed runs."""
     import torch
 
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
         flush.zero_()
@@ -998,7 +1001,7 @@ def warmstart_leg(args, n_train, n_eval, n_eval_low, flush):
             "train": {"samples": n_train, "seconds": t_train, "loss_first": float(np.mean(losses[:20])),
                       "loss_last": float(np.mean(losses[-20:])), "noise_frac": 0.01},
             "config": {"workload": "grid 64x48x96, 48 cone views 256^2 (50 deg), network trained at 1% noise",
-                       "launch_fwd_adj": tuned, "timing": "CUDA events, median of 3, L2 flushed before each",
+                       "launch_fwd_adj": tuned, "timing": "CUDA events, one untimed run then the median of 3, L2 flushed before each",
                        "sirt_weights": "computed once per geometry, outside the timed regions",
                        "sirt_projections": "on-the-fly traversal" if args.no_segments else "stored segment lists"}}
 
