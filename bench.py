@@ -224,7 +224,21 @@ def cpu_baseline(wl, target_s=15.0):
             break
     which = "every ray" if stride == 1 else f"every {ordinal(stride)} ray"
     return {"value": n / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{which} of each view set ({n} rays), forward + adjoint, FP64, {dt:.1f} s"}
+            "sample": f"{which} of each view set ({n} rays), forward + adjoint, FP64, {dt:.1f} s",
+            "segments_per_ray": oracle_segments_per_ray(wl)}
+
+
+def oracle_segments_per_ray(wl, stride=419):
+    """Mean valid segments per ray counted by the oracle (Eq. 4's pieces, with
+    the pieces of one voxel that the definition splits at the closest
+    approaches joined) on every stride-th ray of each view set."""
+    import oracle
+    st, di = oracle_sample(wl, stride)
+    total = 0
+    for x, d in zip(st, di):
+        vox, _ = oracle.ray_segments(wl.edges, x, d)
+        total += int(len(vox) - np.count_nonzero(vox[1:] == vox[:-1])) if len(vox) else 0
+    return {"value": total / len(st), "sample": f"every {ordinal(stride)} ray of each view set ({len(st)} rays)"}
 
 
 # ---------------------------------------------------------------------------

@@ -17,6 +17,7 @@ def _fake_oracle(monkeypatch, per_ray_s, overhead_s, calls):
         calls.append(stride)
         return n, overhead_s + n * per_ray_s
     monkeypatch.setattr(bench, "time_oracle", fake)
+    monkeypatch.setattr(bench, "oracle_segments_per_ray", lambda wl: {"value": 0.0, "sample": ""})
     m = types.ModuleType("oracle")
     m.threads = lambda: 16
     monkeypatch.setitem(sys.modules, "oracle", m)
