@@ -196,13 +196,13 @@ def oracle_sample(wl, stride):
     return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
 
 
-def time_oracle(wl, stride):
+def time_oracle(wl, stride, n_threads=0):
     import oracle
     st, di = oracle_sample(wl, stride)
     yv = np.ones(len(st))
     t = time.perf_counter()
-    oracle.forward(wl.edges, st, di, wl.rho)
-    oracle.adjoint(wl.edges, st, di, yv)
+    oracle.forward(wl.edges, st, di, wl.rho, n_threads=n_threads)
+    oracle.adjoint(wl.edges, st, di, yv, n_threads=n_threads)
     dt = time.perf_counter() - t
     return len(st), dt
 
@@ -225,7 +225,14 @@ def cpu_baseline(wl, target_s=15.0):
     which = "every ray" if stride == 1 else f"every {ordinal(stride)} ray"
     return {"value": n / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
             "sample": f"{which} of each view set ({n} rays), forward + adjoint, FP64, {dt:.1f} s",
-            "segments_per_ray": oracle_segments_per_ray(wl)}
+            "segments_per_ray": oracle_segments_per_ray(wl), "single_core": oracle_single_core(wl)}
+
+
+def oracle_single_core(wl, stride=97):
+    """The same oracle on one host core, every stride-th ray (a few seconds)."""
+    n, dt = time_oracle(wl, stride, n_threads=1)
+    return {"value": n / dt, "unit": UNIT, "cores": 1,
+            "sample": f"every {ordinal(stride)} ray of each view set ({n} rays), forward + adjoint, FP64, {dt:.1f} s"}
 
 
 def oracle_segments_per_ray(wl, stride=419):

@@ -12,12 +12,13 @@ def test_ordinal():
 
 
 def _fake_oracle(monkeypatch, per_ray_s, overhead_s, calls):
-    def fake(wl, stride):
+    def fake(wl, stride, n_threads=0):
         n = 4194304 // stride
         calls.append(stride)
         return n, overhead_s + n * per_ray_s
     monkeypatch.setattr(bench, "time_oracle", fake)
     monkeypatch.setattr(bench, "oracle_segments_per_ray", lambda wl: {"value": 0.0, "sample": ""})
+    monkeypatch.setattr(bench, "oracle_single_core", lambda wl: {"value": 0.0, "sample": ""})
     m = types.ModuleType("oracle")
     m.threads = lambda: 16
     monkeypatch.setitem(sys.modules, "oracle", m)
