@@ -87,7 +87,8 @@ def parse():
     ap.add_argument("--no-dynamic", action="store_true", help="skip the dynamic-object leg")
     ap.add_argument("--views", type=int, default=0,
                     help="paper-scale workload: keep only the first N views of each set (small profiling case)")
-    ap.add_argument("--workload", choices=["paper_scale", "batched", "differentiation", "warmstart", "retrieval"],
+    ap.add_argument("--workload", choices=["paper_scale", "batched", "differentiation", "warmstart", "retrieval",
+                                           "table3"],
                     default="paper_scale",
                     help="batched: 64 uneven SIRT reconstructions in one captured graph (not the headline metric)")
     ap.add_argument("--iters", type=int, default=50, help="SIRT iterations of the batched workload")
@@ -1047,6 +1048,73 @@ def run_warmstart(args):
     emit(out)
 
 
+def run_table3(args):
+    """The paper's Table 3 shapes (Sec. 5.2): one 256^2 cone view on a 100^3
+    grid, one 512^2 view on 50^3, thirty 64^2 views on 50^3 (radius 60, 30 deg).
+    Per shape: the stored lists' build (the paper's precompute, steps 1-3), F
+    and F^T from the lists (the paper's raytrace, step 4, and its adjoint),
+    and F and F^T on the fly. CUDA events, L2 flushed before each timed run,
+    median over args.steps after args.warmup runs."""
+    import torch
+
+    from paper_2608_16960_gb300 import workloads
+    from paper_2608_16960_gb300.projector import Geometry, Grid, Segments, tsp_adjoint, tsp_forward
+
+    torch.cuda.set_device(0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+
+    def med(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    rows = []
+    sampler = ClockSampler(0)
+    sampler.start()
+    for row in range(3):
+        wl = workloads.table3(row)
+        v = wl.views[0]
+        grid = Grid.from_edges(wl.edges)
+        geom = Geometry.cone(v.pos, v.shape, v.fov_deg)
+        rho = torch.tensor(wl.rho, device="cuda")
+        yv = torch.ones(geom.det_shape, device="cuda")
+        y_out = torch.empty(geom.det_shape, device="cuda")
+        g_out = torch.empty(grid.shape, device="cuda")
+        holder = []
+
+        def build():
+            holder.clear()
+            holder.append(Segments(grid, geom, transpose=True))
+
+        build_ms = med(build)
+        segs = holder[0]
+        rows.append({"grid": list(wl.edges.shape), "views": int(len(v.pos)), "detector": list(v.shape),
+                     "rays": int(geom.n_rays), "segments": int(segs.info()[1]),
+                     "lists_build_ms": build_ms,
+                     "lists_forward_ms": med(lambda: segs.forward(rho)),
+                     "lists_adjoint_ms": med(lambda: segs.adjoint(yv)),
+                     "forward_ms": med(lambda: tsp_forward(grid, geom, rho, out=y_out)),
+                     "adjoint_ms": med(lambda: tsp_adjoint(grid, geom, yv, out=g_out))})
+        del holder[:]
+        torch.cuda.empty_cache()
+    clocks = sampler.stop()
+    out = {"metric": "Table 3 shapes: precompute and raytrace times", "unit": "ms", "higher_is_better": False,
+           "dtype": "f32", "data": "synthetic", "steps": args.steps, "warmup": max(3, args.warmup),
+           "value": rows[0]["lists_forward_ms"], "rows": rows, "clocks": clocks,
+           "config": {"workload": "Table 3 shapes (Sec. 5.2): 1x256^2 on 100^3, 1x512^2 on 50^3, 30x64^2 on 50^3",
+                      "timing": "CUDA events, median, L2 flushed before each run"}}
+    emit(out)
+
+
 def main():
     global _LOG
     args = parse()
@@ -1061,6 +1129,8 @@ def main():
         run_retrieval(args)
     elif args.workload == "warmstart":
         run_warmstart(args)
+    elif args.workload == "table3":
+        run_table3(args)
     else:
         run_ours(args)
 
