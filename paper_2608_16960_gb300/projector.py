@@ -480,23 +480,47 @@ class DynamicProjectorFn(torch.autograd.Function):
         return tsp_adjoint_dynamic(ctx.grid, ctx.geom, gy.contiguous()), None, None
 
 
+class ListProjectorFn(torch.autograd.Function):
+    """Autograd function over stored segment lists: forward = the lists' F,
+    backward = their F^T (the voxel-major gather when the lists were
+    transposed), for repeated projections through one geometry."""
+
+    @staticmethod
+    def forward(ctx, rho, segments):
+        ctx.segments = segments
+        return segments.forward(rho)
+
+    @staticmethod
+    def backward(ctx, gy):
+        return ctx.segments.adjoint(gy.contiguous()), None
+
+
 class Operator:
     """Operator(grid, geom): callable F with autograd (Sec. 4.4, Listing 6).
     Called with a 3D object it projects it through every view; a 4D object
     is a batch of independent objects, or, with dynamic=True, a dynamic
-    object whose k-th volume is seen by the k-th view (Sec. 4.4)."""
+    object whose k-th volume is seen by the k-th view (Sec. 4.4). With
+    segments (a Segments of the same grid and geometry) F and F^T run from
+    the stored lists instead of re-tracing every ray."""
 
-    def __init__(self, grid: Grid, geom: Geometry, launch=None, dynamic: bool = False):
+    def __init__(self, grid: Grid, geom: Geometry, launch=None, dynamic: bool = False, segments=None):
+        if segments is not None and (dynamic or segments.grid is not grid or segments.geom is not geom):
+            raise ValueError("segments must belong to this grid and geometry (and the operator be static)")
         self.grid, self.geom, self.launch, self.dynamic = grid, geom, launch, dynamic
+        self.segments = segments
 
     def __call__(self, rho: torch.Tensor) -> torch.Tensor:
         if self.dynamic and rho.dim() == 4:
             return DynamicProjectorFn.apply(rho, self.grid, self.geom)
+        if self.segments is not None:
+            return ListProjectorFn.apply(rho, self.segments)
         return ProjectorFn.apply(rho, self.grid, self.geom, self.launch)
 
     def T(self, y: torch.Tensor) -> torch.Tensor:
         if self.dynamic:
             return tsp_adjoint_dynamic(self.grid, self.geom, y)
+        if self.segments is not None:
+            return self.segments.adjoint(y)
         return tsp_adjoint(self.grid, self.geom, y, launch=self.launch)
 
 

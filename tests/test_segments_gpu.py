@@ -14,7 +14,7 @@ import torch
 import oracle
 from paper_2608_16960_gb300 import synth, workloads
 from paper_2608_16960_gb300._lib import TspError
-from paper_2608_16960_gb300.projector import (Geometry, Grid, Segments, tsp_adjoint, tsp_count_segments,
+from paper_2608_16960_gb300.projector import (Geometry, Grid, Operator, Segments, tsp_adjoint, tsp_count_segments,
                                               tsp_device_status, tsp_forward)
 
 from _util import oracle_rays, parity
@@ -367,4 +367,28 @@ def test_chunked_sirt_finishes_the_chunk_and_retries_after_out_of_memory():
     assert runs[0][0] == 1 and runs[1][0] == 2
     for a, b in zip(runs[0][1], runs[1][1]):
         assert torch.equal(a, b)
+    assert tsp_device_status() == 0
+
+
+def test_operator_over_lists_differentiates_like_the_oracle():
+    """Operator(grid, geom, segments=...) takes F and F^T from the stored
+    lists: the forward matches the oracle's and the gradient of
+    <F rho, w> is the oracle's F^T w (per voxel 1e-4 with the floor)."""
+    wl = workloads.tiny()
+    grid = Grid.from_edges(wl.edges)
+    v = wl.views[0]
+    geom = Geometry.cone(v.pos, v.shape, v.fov_deg)
+    segs = Segments(grid, geom, transpose=True)
+    op = Operator(grid, geom, segments=segs)
+    rho = torch.tensor(wl.rho, device=DEV, requires_grad=True)
+    y = op(rho)
+    w = torch.tensor(synth.uniform_volume(geom.det_shape, 17), device=DEV)
+    (y * w).sum().backward()
+    st, di = oracle_rays(v)
+    parity(y.detach().cpu().numpy(), oracle.forward(wl.edges, st, di, wl.rho), what="list operator forward")
+    parity(rho.grad.cpu().numpy(), oracle.adjoint(wl.edges, st, di, w.cpu().numpy().reshape(-1).astype(np.float64)),
+           what="list operator gradient")
+    assert torch.equal(op.T(w), segs.adjoint(w))
+    with pytest.raises(ValueError):
+        Operator(grid, Geometry.cone(v.pos, v.shape, v.fov_deg), segments=segs)
     assert tsp_device_status() == 0
