@@ -1070,7 +1070,7 @@ def run_table3(args):
     import torch
 
     from paper_2608_16960_gb300 import workloads
-    from paper_2608_16960_gb300.projector import Geometry, Grid, Segments, tsp_adjoint, tsp_forward
+    from paper_2608_16960_gb300.projector import Geometry, Grid, Segments, tsp_adjoint, tsp_autotune, tsp_forward
 
     torch.cuda.set_device(0)
     flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
@@ -1097,6 +1097,7 @@ def run_table3(args):
         v = wl.views[0]
         grid = Grid.from_edges(wl.edges)
         geom = Geometry.cone(v.pos, v.shape, v.fov_deg)
+        tuned = tsp_autotune(grid, geom)  # set-up: launch knobs and scatter strategy for this size class
         rho = torch.tensor(wl.rho, device="cuda")
         yv = torch.ones(geom.det_shape, device="cuda")
         y_out = torch.empty(geom.det_shape, device="cuda")
@@ -1110,6 +1111,7 @@ def run_table3(args):
         build_ms = med(build)
         segs = holder[0]
         rows.append({"grid": list(wl.edges.shape), "views": int(len(v.pos)), "detector": list(v.shape),
+                     "launch_fwd_adj": tuned,
                      "rays": int(geom.n_rays), "segments": int(segs.info()[1]),
                      "lists_build_ms": build_ms,
                      "lists_forward_ms": med(lambda: segs.forward(rho)),
