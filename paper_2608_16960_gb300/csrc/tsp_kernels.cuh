@@ -224,7 +224,7 @@ struct GatherOp {
   __device__ __forceinline__ void operator()(int v, float dl) {
 #pragma unroll
     for (int b = 0; b < NB; ++b)
-      if (b < nb) acc[b] = fmaf(__ldg(rho + b * V + v), dl, acc[b]);
+      if (NB == 1 || b < nb) acc[b] = fmaf(__ldg(rho + b * V + v), dl, acc[b]);
   }
   __device__ __forceinline__ void end(int64_t ray) {
 #pragma unroll
@@ -251,6 +251,10 @@ struct ScatterOp {
     return any;
   }
   __device__ __forceinline__ void operator()(int v, float dl) {
+    if (NB == 1) {  // begin() skipped a ray whose value is zero
+      atomicAdd(g + v, __fmul_rn(w[0], dl));
+      return;
+    }
 #pragma unroll
     for (int b = 0; b < NB; ++b)
       if (b < nb && w[b] != 0.0f) atomicAdd(g + b * V + v, __fmul_rn(w[b], dl));

@@ -238,7 +238,8 @@ struct RayState {
   int th_mode;   // 0 walk, 1 no crossings, 2 one jump pending (line through the origin)
   int ie_jump;   // th_mode 2: the polar region after the jump
   int cn, ci;    // crossings in the cone list, index of the next one
-  unsigned long long cmask;  // bit i: crossing i of the list raises the polar index (else lowers it)
+  int cturn;     // crossings (counted from the list's first entry) before the polar direction turns
+  int cdir;      // +1: the polar index rises at crossings before the turn, -1: it falls
   bool cmore;    // the list filled up: more crossings may follow
   float tgen;    // the last crossing produced (each is clamped to it)
   float th_sg, th_fe, th_te;
@@ -346,9 +347,11 @@ struct ConeList {
   int stride, cap;
 };
 
+// theta(t) along a line is unimodal, so the polar index moves one way until
+// the extremum and the other way after it: the list keeps the first
+// direction and the number of crossings before the turn.
 TSP_HD void cone_fill(const TGrid& G, RayState& s, const ConeList& L) {
-  int n = 0;
-  unsigned long long mask = 0ull;
+  int n = 0, turn = L.cap, d0 = 0;
   float prev = s.tgen, first = INFINITY;
 #pragma unroll 1
   for (; n < L.cap; ++n) {
@@ -357,14 +360,19 @@ TSP_HD void cone_fill(const TGrid& G, RayState& s, const ConeList& L) {
     if (!theta_gen(G, s, t, dir)) break;
     t = fmaxf(t, prev);
     prev = t;
-    if (n == 0) first = t;
+    if (n == 0) {
+      first = t;
+      d0 = dir;
+    } else if (dir != d0 && turn == L.cap) {
+      turn = n;
+    }
     L.t[n * L.stride] = t;
-    mask |= (unsigned long long)(dir > 0) << n;
   }
   s.cmore = n == L.cap;
   s.cn = n;
   s.ci = 0;
-  s.cmask = mask;
+  s.cturn = turn;
+  s.cdir = d0;
   s.tgen = prev;
   s.tth = first;
 }
@@ -562,7 +570,8 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
   s.gie = s.ie;
   s.tgen = tcur;
   s.cn = s.ci = 0;
-  s.cmask = 0ull;
+  s.cturn = 0;
+  s.cdir = 1;
   s.cmore = false;
   if (s.th_mode == 2) {
     s.tth = 0.0f;
@@ -591,7 +600,7 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
       if constexpr (op_has_gap<Op>::value) op.gap();
     }
     tcur = tn;
-    if (s.tr <= s.tth && s.tr <= s.tph) {
+    if (s.tr == tn) {  // the smallest (ties go to the sphere, then the cone)
       s.ir = s.ir_next;
       if (s.ir >= G.Nr) return true;  // left through the outer sphere
       radial_next(G, s);
@@ -602,7 +611,7 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
         s.th_mode = 1;
         s.tth = INFINITY;
       } else {
-        s.ie += ((s.cmask >> s.ci) & 1ull) ? 1 : -1;
+        s.ie += s.ci < s.cturn ? s.cdir : -s.cdir;
         if (++s.ci < s.cn) s.tth = L.t[s.ci * L.stride];
         else if (s.cmore) cone_fill(G, s, L);
         else s.tth = INFINITY;
