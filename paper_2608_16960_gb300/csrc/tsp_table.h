@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <vector>
 
 #include "tsp_internal.h"
@@ -48,11 +49,14 @@ inline void build_grid_table(const double* r_edges, int n_r_edges, const double*
   }
   g->M = int(planes.size());
   g->pa0 = float(planes[0]);
-  g->words = 2 * (Nr + 1) + 5 * (Ne + 1) + 4 * g->M;
+  g->words = 2 * (Nr + 2) + 5 * (Ne + 1) + 4 * g->M;
   std::vector<float>& table = *table_out;
   table.assign(size_t(g->words), 0.0f);
-  float* R2 = table.data();
-  float* R2L = R2 + (Nr + 1);
+  // R2 and R2L each start with an entry for k = -1 (the hole inside the
+  // innermost sphere: no crossing), so that R_k^2 - b^2 needs no range test
+  table[0] = -std::numeric_limits<float>::infinity();
+  float* R2 = table.data() + 1;
+  float* R2L = R2 + (Nr + 1) + 1;
   float* C = R2L + (Nr + 1);
   float* S2 = C + (Ne + 1);
   float* S2L = S2 + (Ne + 1);

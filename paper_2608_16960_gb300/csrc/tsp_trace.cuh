@@ -83,8 +83,8 @@ __device__ __forceinline__ float sqrt_approx_(float x) {
 
 // Grid tables as seen by a kernel (pointers into shared memory).
 struct TGrid {
-  const float* R2;  // [Nr+1] squared sphere radii (high part)
-  const float* R2L; // [Nr+1] low part: R_k^2 = R2 + R2L to ~2^-48
+  const float* R2;  // [Nr+1] squared sphere radii (high part); R2[-1] = -inf
+  const float* R2L; // [Nr+1] low part: R_k^2 = R2 + R2L to ~2^-48; R2L[-1] = 0
   const float* C;   // [Ne+1] cos(theta_k), decreasing
   const float* S2;  // [Ne+1] sin^2(theta_k), high part
   const float* S2L; // [Ne+1] low part
@@ -100,7 +100,7 @@ struct TGrid {
 
 // Device-side description of a grid's table in global memory.
 struct GridDesc {
-  const float* table;  // R2 | R2L | C | S2 | S2L | K2 | K2L | PC | PS | PA | SEC (int bits)
+  const float* table;  // -inf R2 | 0 R2L | C | S2 | S2L | K2 | K2L | PC | PS | PA | SEC (int bits)
   int Nr, Ne, Na, M;
   int words;           // table length in 32-bit words
   float pa0;
@@ -108,8 +108,8 @@ struct GridDesc {
 
 TSP_HD TGrid tgrid_from_smem(const GridDesc& d, const float* s) {
   TGrid g;
-  g.R2 = s;
-  g.R2L = s + (d.Nr + 1);
+  g.R2 = s + 1;
+  g.R2L = g.R2 + (d.Nr + 1) + 1;
   g.C = g.R2L + (d.Nr + 1);
   g.S2 = g.C + (d.Ne + 1);
   g.S2L = g.S2 + (d.Ne + 1);
@@ -255,15 +255,15 @@ struct RayState {
   float tph;
 };
 
-// R_k^2 - b^2 from the two-part table and impact parameter.
+// R_k^2 - b^2 from the two-part table and impact parameter (-inf for k = -1).
 TSP_HD float sphere_disc(const TGrid& G, const RayState& s, int k) {
   return T_ADD(T_SUB(G.R2[k], s.b2), T_SUB(G.R2L[k], s.b2lo));
 }
 
 TSP_HD void radial_next(const TGrid& G, RayState& s) {
   if (!s.r_out) {
-    const int k = s.ir;  // inner sphere of the current shell
-    const float dk = k >= 0 ? sphere_disc(G, s, k) : -1.0f;
+    const int k = s.ir;  // inner sphere of the current shell (-1 inside the innermost)
+    const float dk = sphere_disc(G, s, k);
     if (dk > 0.0f) {
       s.tr = -T_SQRTA(dk);
       s.ir_next = k - 1;
@@ -271,14 +271,11 @@ TSP_HD void radial_next(const TGrid& G, RayState& s) {
     }
     s.r_out = true;  // passed the closest approach: from now on outward
   }
-  const int k = s.ir + 1;  // outer sphere of the current shell
-  if (k <= G.Nr) {
-    s.tr = T_SQRTA(fmaxf(sphere_disc(G, s, k), 0.0f));
-    s.ir_next = k;
-  } else {
-    s.tr = INFINITY;
-    s.ir_next = s.ir;
-  }
+  // outer sphere of the current shell: k <= N_r, as the walk stops once it
+  // leaves through sphere N_r
+  const int k = s.ir + 1;
+  s.tr = T_SQRTA(fmaxf(sphere_disc(G, s, k), 0.0f));
+  s.ir_next = k;
 }
 
 // W = sqrt(b2 sin^2 theta_k - m_z^2) = sqrt(|m_xy|^2 sin^2 - m_z^2 cos^2) with
