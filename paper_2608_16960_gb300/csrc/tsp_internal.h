@@ -17,7 +17,7 @@ struct tsp_grid_s {
   bool wrap = false;
   float pa0 = 0.0f;
   int words = 0;
-  float* d_table = nullptr;  // R2 | C | PC | PS | PA | SEC
+  float* d_table = nullptr;  // the grid table of tsp_table.h (radii, cones, half-planes, sector maps)
   float* d_centres = nullptr;  // voxel centres: r [Nr] | sin t [Ne] | cos t [Ne] | cos p [Na] | sin p [Na]
   int device = 0;
   std::vector<double> r, th, ph;

@@ -16,7 +16,7 @@ constexpr double kTablePi = 3.14159265358979323846;
 constexpr double kTableTwoPi = 2.0 * kTablePi;
 
 // Shared-memory table of a grid (layout R2 | R2L | C | S2 | S2L | K2 | K2L | PC |
-// PS | PA | SEC; the *L arrays hold the float32 rounding residue of the
+// PS | PA | SEC | SEC'; the *L arrays hold the float32 rounding residue of the
 // preceding high parts, computed in double). Pure host
 // arithmetic: radii squared, cosines of the polar edges, and the azimuth
 // half-planes with their sector-to-voxel map. Fills the grid's dimensions.
@@ -49,7 +49,7 @@ inline void build_grid_table(const double* r_edges, int n_r_edges, const double*
   }
   g->M = int(planes.size());
   g->pa0 = float(planes[0]);
-  g->words = 2 * (Nr + 2) + 5 * (Ne + 1) + 4 * g->M;
+  g->words = 2 * (Nr + 2) + 5 * (Ne + 1) + 5 * g->M;
   std::vector<float>& table = *table_out;
   table.assign(size_t(g->words), 0.0f);
   // R2 and R2L each start with an entry for k = -1 (the hole inside the
@@ -83,6 +83,7 @@ inline void build_grid_table(const double* r_edges, int n_r_edges, const double*
     PS[j] = float(std::sin(planes[j]));
     PA[j] = float(planes[j] - planes[0]);
     SEC[j] = sec[j];
+    SEC[g->M + j] = sec[j == 0 ? g->M - 1 : j - 1];  // the sector clockwise of plane j
   }
 }
 

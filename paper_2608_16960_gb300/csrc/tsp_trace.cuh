@@ -93,14 +93,15 @@ struct TGrid {
   const float* PC;  // [M] cos of half-plane azimuths
   const float* PS;  // [M] sin of half-plane azimuths
   const float* PA;  // [M] half-plane azimuth minus PA0, increasing in [0, 2 pi)
-  const int* SEC;   // [M] azimuth voxel index of the sector counter-clockwise of plane j (-1: outside)
+  const int* SEC;   // [2M] azimuth voxel index (-1: outside) of the sector counter-clockwise of
+                    // plane j at SEC[j], of the sector clockwise of it at SEC[M + j]
   int Nr, Ne, Na, M;
   float pa0;
 };
 
 // Device-side description of a grid's table in global memory.
 struct GridDesc {
-  const float* table;  // -inf R2 | 0 R2L | C | S2 | S2L | K2 | K2L | PC | PS | PA | SEC (int bits)
+  const float* table;  // -inf R2 | 0 R2L | C | S2 | S2L | K2 | K2L | PC | PS | PA | SEC SEC' (int bits)
   int Nr, Ne, Na, M;
   int words;           // table length in 32-bit words
   float pa0;
@@ -245,10 +246,12 @@ struct RayState {
   float th_sg, th_fe, th_te;
   float tth;
   // azimuth
-  int sec, sec_next;
-  int ia;        // azimuth voxel index of sector sec (-1 outside a wedge)
-  int ph_mode;   // 0 walk, 1 no crossings, 2 one jump pending (line meets the z axis)
-  float mz;
+  int ia;        // azimuth voxel index of the current sector (-1 outside a wedge)
+  int pj;        // the half-plane the next azimuth crossing is on
+  int pdj;       // +1: planes are met counter-clockwise (m_z > 0), -1: clockwise
+  int pwrap, pwto;  // pj steps from pwrap to pwto across the start of the table
+  int soff;      // 0 or M: the part of SEC giving the sector beyond plane pj
+  float nxs, nys;   // n_x, n_y times the sign of m_z (0, 0: no crossing ahead)
   float pk;      // m_z / |n_xy|^2
   float ptax;    // t_a: closest approach of the horizontal projection to the z axis
   int pstop;     // half-plane the line heads along (parallel within rounding): never crossed; -1 none
@@ -374,19 +377,16 @@ TSP_HD void cone_fill(const TGrid& G, RayState& s, const ConeList& L) {
   s.tth = first;
 }
 
+// Crossing of half-plane pj, if the line meets it: the sign of m_z is folded
+// into (nxs, nys), so den = sign(m_z) (n_xy x w_j) is negative exactly when
+// the crossing is on the half-plane (Eq. 13), and nw / den equals the
+// unsigned ratio (n_xy . w_j) / (n_xy x w_j) bit for bit.
 TSP_HD void phi_next(const TGrid& G, RayState& s) {
-  if (s.ph_mode != 0) {
-    s.tph = INFINITY;
-    return;
-  }
-  const bool ccw = s.mz > 0.0f;
-  const int j = ccw ? (s.sec + 1 == G.M ? 0 : s.sec + 1) : s.sec;
-  const float pc = G.PC[j], ps = G.PS[j];
-  const float den = fmaf(s.nx, ps, -T_MUL(s.ny, pc));  // n_xy x w_j
-  if ((ccw ? den < 0.0f : den > 0.0f) && j != s.pstop) {
-    const float nw = fmaf(s.nx, pc, T_MUL(s.ny, ps));  // n_xy . w_j
+  const float pc = G.PC[s.pj], ps = G.PS[s.pj];
+  const float den = fmaf(s.nxs, ps, -T_MUL(s.nys, pc));
+  if (den < 0.0f && s.pj != s.pstop) {
+    const float nw = fmaf(s.nxs, pc, T_MUL(s.nys, ps));
     s.tph = fmaf(-s.pk, T_DIV(nw, den), s.ptax);
-    s.sec_next = ccw ? j : (s.sec == 0 ? G.M - 1 : s.sec - 1);
   } else {
     s.tph = INFINITY;
   }
@@ -463,7 +463,7 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
   s.b2nz = T_MUL(s.b2, s.nz);
   // m_z = (q x n)_z: its sign gives the azimuth's direction along the ray (it
   // grows iff m_z > 0, Eq. 13); |m_z| / |n_xy| is the line's distance from the z axis
-  s.mz = mnz.hi;
+  const float mz = mnz.hi;
   s.qx = qxf.hi;
   s.qy = qyf.hi;
   s.qz = qzf.hi;
@@ -511,7 +511,8 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
   }
 
   // azimuth set-up
-  s.sec = classify_sector(G, px, py);
+  int sec = classify_sector(G, px, py);
+  int ph_mode;  // 0 walk, 1 no crossings, 2 one jump (the line meets the z axis)
   float t_ax = INFINITY;
   int sec_ax = 0;
   // Half-plane crossings are measured from t_a, where the line's horizontal
@@ -526,11 +527,11 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
   if (nxy > 0.0f) {
     const ff nn = ff_add(ff_mul(nxf, nxf), ff_mul(nyf, nyf));
     s.ptax = -ff_div(ff_add(ff_mul(qxf, nxf), ff_mul(qyf, nyf)), nn).hi;
-    s.pk = T_DIV(s.mz, nn.hi);
+    s.pk = T_DIV(mz, nn.hi);
   }
   s.pstop = -1;
   if (nxy > 0.0f && fabsf(s.pk) > T_MUL(0x1p-24f, sout)) {
-    s.ph_mode = 0;
+    ph_mode = 0;
     // Half-planes parallel to the line within rounding of n and of the table
     // (|n_xy x w| <= 2^-21 |n_xy|) can only sit at the two ends of the sweep,
     // where their crossing test sees noise. The one the line comes from
@@ -538,11 +539,11 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
     // it there: the walk steps across it at once. The one the line heads
     // along (n_xy . w > 0) is never crossed.
     const float pde = T_MUL(0x1p-21f, T_SQRT(nxy));
-    const bool ccw = s.mz > 0.0f;
-    const int j0 = ccw ? (s.sec + 1 == G.M ? 0 : s.sec + 1) : s.sec;
+    const bool ccw = mz > 0.0f;
+    const int j0 = ccw ? (sec + 1 == G.M ? 0 : sec + 1) : sec;
     if (fabsf(fmaf(s.nx, G.PS[j0], -T_MUL(s.ny, G.PC[j0]))) <= pde &&
         fmaf(s.nx, G.PC[j0], T_MUL(s.ny, G.PS[j0])) < 0.0f)
-      s.sec = ccw ? j0 : (s.sec == 0 ? G.M - 1 : s.sec - 1);
+      sec = ccw ? j0 : (sec == 0 ? G.M - 1 : sec - 1);
     const int se = classify_sector(G, s.nx, s.ny);  // the sector of the direction of travel
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -554,11 +555,11 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
   } else {
     if (nxy > 0.0f) {  // the line meets the z axis: azimuth jumps by pi there
       t_ax = s.ptax;
-      s.ph_mode = t_ax > tcur ? 2 : 1;
+      ph_mode = t_ax > tcur ? 2 : 1;
       sec_ax = classify_sector(G, s.nx, s.ny);
-      if (t_ax <= tcur) s.sec = sec_ax;  // at or past the axis: the direction's azimuth
+      if (t_ax <= tcur) sec = sec_ax;  // at or past the axis: the direction's azimuth
     } else {
-      s.ph_mode = 1;  // vertical line: constant azimuth
+      ph_mode = 1;  // vertical line: constant azimuth
     }
   }
 
@@ -578,15 +579,28 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
   } else {
     s.tth = INFINITY;
   }
-  if (s.ph_mode == 2) {
-    s.tph = t_ax;
-    s.sec_next = sec_ax;
-  } else {
+  s.ia = G.SEC[sec];
+  if (ph_mode == 0) {
+    const bool ccw = mz > 0.0f;
+    s.pdj = ccw ? 1 : -1;
+    s.pwrap = ccw ? G.M - 1 : 0;
+    s.pwto = G.M - 1 - s.pwrap;
+    s.soff = ccw ? 0 : G.M;
+    s.nxs = ccw ? s.nx : -s.nx;
+    s.nys = ccw ? s.ny : -s.ny;
+    s.pj = ccw ? (sec + 1 == G.M ? 0 : sec + 1) : sec;
     phi_next(G, s);
     s.tph = fmaxf(s.tph, tcur);
+  } else {  // no half-plane crossing, or the one jump to the sector of sec_ax
+    s.pdj = 1;
+    s.pwrap = G.M - 1;
+    s.pwto = 0;
+    s.soff = 0;
+    s.nxs = s.nys = 0.0f;
+    s.pj = ph_mode == 2 ? sec_ax : 0;
+    s.tph = ph_mode == 2 ? t_ax : INFINITY;
   }
 
-  s.ia = G.SEC[s.sec];
   const int cap = 2 * (G.Nr + G.Ne + 2) + G.M + 8;
 #pragma unroll 1
   for (int it = 0; it < cap; ++it) {
@@ -614,9 +628,8 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
         else s.tth = INFINITY;
       }
     } else {
-      s.sec = s.sec_next;
-      s.ia = G.SEC[s.sec];
-      if (s.ph_mode == 2) s.ph_mode = 1;
+      s.ia = G.SEC[s.pj + s.soff];
+      s.pj = s.pj == s.pwrap ? s.pwto : s.pj + s.pdj;
       phi_next(G, s);
       s.tph = fmaxf(s.tph, tcur);
     }
