@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <limits>
 #include <vector>
 
@@ -15,8 +16,8 @@ namespace tsp {
 constexpr double kTablePi = 3.14159265358979323846;
 constexpr double kTableTwoPi = 2.0 * kTablePi;
 
-// Shared-memory table of a grid (layout R2 | R2L | C | S2 | S2L | K2 | K2L | PC |
-// PS | PA | SEC | SEC'; the *L arrays hold the float32 rounding residue of the
+// Shared-memory table of a grid (layout PR | RR | C | S2 | S2L | K2 | K2L | PA;
+// the *L arrays hold the float32 rounding residue of the
 // preceding high parts, computed in double). Pure host
 // arithmetic: radii squared, cosines of the polar edges, and the azimuth
 // half-planes with their sector-to-voxel map. Fills the grid's dimensions.
@@ -49,28 +50,45 @@ inline void build_grid_table(const double* r_edges, int n_r_edges, const double*
   }
   g->M = int(planes.size());
   g->pa0 = float(planes[0]);
-  g->words = 2 * (Nr + 2) + 5 * (Ne + 1) + 5 * g->M;
+  const int M = g->M;
+  g->words = 8 * M + 2 * (Nr + 2) + 5 * (Ne + 1) + M;
   std::vector<float>& table = *table_out;
   table.assign(size_t(g->words), 0.0f);
-  // R2 and R2L each start with an entry for k = -1 (the hole inside the
-  // innermost sphere: no crossing), so that R_k^2 - b^2 needs no range test
-  table[0] = -std::numeric_limits<float>::infinity();
-  float* R2 = table.data() + 1;
-  float* R2L = R2 + (Nr + 1) + 1;
-  float* C = R2L + (Nr + 1);
+  // Half-plane records first (16-byte aligned): record j < M serves a line
+  // whose azimuth grows, record M + j one whose azimuth falls. Each holds
+  // plane j's (cos, sin), the voxel index of the sector beyond it in that
+  // direction and the record of the plane after it.
+  float* PR = table.data();
+  auto put_int = [](float* dst, int v) { std::memcpy(dst, &v, sizeof v); };
+  for (int j = 0; j < M; ++j) {
+    const float c = float(std::cos(planes[j])), sn = float(std::sin(planes[j]));
+    const int jp = j + 1 == M ? 0 : j + 1, jm = j == 0 ? M - 1 : j - 1;
+    float* up = PR + 4 * j;
+    float* dn = PR + 4 * (M + j);
+    up[0] = dn[0] = c;
+    up[1] = dn[1] = sn;
+    put_int(up + 2, sec[j]);
+    put_int(up + 3, jp);
+    put_int(dn + 2, sec[jm]);
+    put_int(dn + 3, M + jm);
+  }
+  // Squared radii as (high, low) pairs, starting with a pair for k = -1 (the
+  // hole inside the innermost sphere: no crossing), so that R_k^2 - b^2 needs
+  // no range test
+  float* RR = table.data() + 8 * M + 2;
+  RR[-2] = -std::numeric_limits<float>::infinity();
+  RR[-1] = 0.0f;
+  float* C = RR + 2 * (Nr + 1);
   float* S2 = C + (Ne + 1);
   float* S2L = S2 + (Ne + 1);
   float* K2 = S2L + (Ne + 1);
   float* K2L = K2 + (Ne + 1);
-  float* PC = K2L + (Ne + 1);
-  float* PS = PC + g->M;
-  float* PA = PS + g->M;
-  int* SEC = reinterpret_cast<int*>(PA + g->M);
+  float* PA = K2L + (Ne + 1);
   auto split = [](double v, float* hi, float* lo) {
     *hi = float(v);
     *lo = float(v - double(*hi));
   };
-  for (int k = 0; k <= Nr; ++k) split(r_edges[k] * r_edges[k], &R2[k], &R2L[k]);
+  for (int k = 0; k <= Nr; ++k) split(r_edges[k] * r_edges[k], &RR[2 * k], &RR[2 * k + 1]);
   for (int k = 0; k <= Ne; ++k) {
     const double t = std::min(kTablePi, std::max(0.0, theta_edges[k]));
     const double c = std::cos(t), sn = std::sin(t);
@@ -78,13 +96,7 @@ inline void build_grid_table(const double* r_edges, int n_r_edges, const double*
     split(sn * sn, &S2[k], &S2L[k]);
     split(c * c, &K2[k], &K2L[k]);
   }
-  for (int j = 0; j < g->M; ++j) {
-    PC[j] = float(std::cos(planes[j]));
-    PS[j] = float(std::sin(planes[j]));
-    PA[j] = float(planes[j] - planes[0]);
-    SEC[j] = sec[j];
-    SEC[g->M + j] = sec[j == 0 ? g->M - 1 : j - 1];  // the sector clockwise of plane j
-  }
+  for (int j = 0; j < M; ++j) PA[j] = float(planes[j] - planes[0]);
 }
 
 }  // namespace tsp

@@ -41,6 +41,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <utility>
 
@@ -83,25 +84,25 @@ __device__ __forceinline__ float sqrt_approx_(float x) {
 
 // Grid tables as seen by a kernel (pointers into shared memory).
 struct TGrid {
-  const float* R2;  // [Nr+1] squared sphere radii (high part); R2[-1] = -inf
-  const float* R2L; // [Nr+1] low part: R_k^2 = R2 + R2L to ~2^-48; R2L[-1] = 0
+  const float2* RR; // [Nr+1] squared sphere radii (high, low): R_k^2 = x + y to ~2^-48;
+                    // RR[-1] = (-inf, 0)
   const float* C;   // [Ne+1] cos(theta_k), decreasing
   const float* S2;  // [Ne+1] sin^2(theta_k), high part
   const float* S2L; // [Ne+1] low part
   const float* K2;  // [Ne+1] cos^2(theta_k), high part
   const float* K2L; // [Ne+1] low part
-  const float* PC;  // [M] cos of half-plane azimuths
-  const float* PS;  // [M] sin of half-plane azimuths
+  const float4* PR; // [2M] half-plane records (cos psi_j, sin psi_j, sector beyond, next record)
+                    // as int bits: record j for azimuth growing (the sector
+                    // counter-clockwise of plane j, then record j+1 mod M), record M + j
+                    // for azimuth falling (the sector clockwise of it, then M + (j-1 mod M))
   const float* PA;  // [M] half-plane azimuth minus PA0, increasing in [0, 2 pi)
-  const int* SEC;   // [2M] azimuth voxel index (-1: outside) of the sector counter-clockwise of
-                    // plane j at SEC[j], of the sector clockwise of it at SEC[M + j]
   int Nr, Ne, Na, M;
   float pa0;
 };
 
 // Device-side description of a grid's table in global memory.
 struct GridDesc {
-  const float* table;  // -inf R2 | 0 R2L | C | S2 | S2L | K2 | K2L | PC | PS | PA | SEC SEC' (int bits)
+  const float* table;  // PR | (-inf, 0) RR | C | S2 | S2L | K2 | K2L | PA (16-byte aligned)
   int Nr, Ne, Na, M;
   int words;           // table length in 32-bit words
   float pa0;
@@ -109,17 +110,14 @@ struct GridDesc {
 
 TSP_HD TGrid tgrid_from_smem(const GridDesc& d, const float* s) {
   TGrid g;
-  g.R2 = s + 1;
-  g.R2L = g.R2 + (d.Nr + 1) + 1;
-  g.C = g.R2L + (d.Nr + 1);
+  g.PR = reinterpret_cast<const float4*>(s);
+  g.RR = reinterpret_cast<const float2*>(s + 8 * d.M + 2);
+  g.C = s + 8 * d.M + 2 + 2 * (d.Nr + 1);
   g.S2 = g.C + (d.Ne + 1);
   g.S2L = g.S2 + (d.Ne + 1);
   g.K2 = g.S2L + (d.Ne + 1);
   g.K2L = g.K2 + (d.Ne + 1);
-  g.PC = g.K2L + (d.Ne + 1);
-  g.PS = g.PC + d.M;
-  g.PA = g.PS + d.M;
-  g.SEC = reinterpret_cast<const int*>(g.PA + d.M);
+  g.PA = g.K2L + (d.Ne + 1);
   g.Nr = d.Nr;
   g.Ne = d.Ne;
   g.Na = d.Na;
@@ -138,12 +136,12 @@ __device__ __forceinline__ void load_table(const GridDesc& d, float* s) {
 
 // ---- classification of one point (only at the ray's first in-grid point) ----
 
-// Radial region: number of k with R2[k] <= r2, minus one.
+// Radial region: number of k with R_k^2 (high part) <= r2, minus one.
 TSP_HD int classify_r(const TGrid& G, float r2) {
   int lo = 0, hi = G.Nr + 1;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (G.R2[mid] <= r2) lo = mid + 1;
+    if (G.RR[mid].x <= r2) lo = mid + 1;
     else hi = mid;
   }
   return lo - 1;
@@ -177,6 +175,17 @@ TSP_HD int classify_sector(const TGrid& G, float px, float py) {
 }
 
 // ---- next-crossing rules per family ----
+
+// The int stored in a float's bits (the table's integer fields).
+TSP_HD int bits_i(float f) {
+#if defined(__CUDA_ARCH__)
+  return __float_as_int(f);
+#else
+  int v;
+  memcpy(&v, &f, sizeof v);
+  return v;
+#endif
+}
 
 TSP_HD int imin_(int a, int b) { return a < b ? a : b; }
 
@@ -247,20 +256,20 @@ struct RayState {
   float tth;
   // azimuth
   int ia;        // azimuth voxel index of the current sector (-1 outside a wedge)
-  int pj;        // the half-plane the next azimuth crossing is on
-  int pdj;       // +1: planes are met counter-clockwise (m_z > 0), -1: clockwise
-  int pwrap, pwto;  // pj steps from pwrap to pwto across the start of the table
-  int soff;      // 0 or M: the part of SEC giving the sector beyond plane pj
+  int pj;        // record of the half-plane the next azimuth crossing is on
+  int psec, pnx; // its sector beyond and next record
   float nxs, nys;   // n_x, n_y times the sign of m_z (0, 0: no crossing ahead)
   float pk;      // m_z / |n_xy|^2
   float ptax;    // t_a: closest approach of the horizontal projection to the z axis
-  int pstop;     // half-plane the line heads along (parallel within rounding): never crossed; -1 none
+  int pstop;     // record of the half-plane the line heads along (parallel within rounding):
+                 // never crossed; -1 none
   float tph;
 };
 
 // R_k^2 - b^2 from the two-part table and impact parameter (-inf for k = -1).
 TSP_HD float sphere_disc(const TGrid& G, const RayState& s, int k) {
-  return T_ADD(T_SUB(G.R2[k], s.b2), T_SUB(G.R2L[k], s.b2lo));
+  const float2 r = G.RR[k];
+  return T_ADD(T_SUB(r.x, s.b2), T_SUB(r.y, s.b2lo));
 }
 
 TSP_HD void radial_next(const TGrid& G, RayState& s) {
@@ -382,10 +391,12 @@ TSP_HD void cone_fill(const TGrid& G, RayState& s, const ConeList& L) {
 // the crossing is on the half-plane (Eq. 13), and nw / den equals the
 // unsigned ratio (n_xy . w_j) / (n_xy x w_j) bit for bit.
 TSP_HD void phi_next(const TGrid& G, RayState& s) {
-  const float pc = G.PC[s.pj], ps = G.PS[s.pj];
-  const float den = fmaf(s.nxs, ps, -T_MUL(s.nys, pc));
+  const float4 r = G.PR[s.pj];
+  s.psec = bits_i(r.z);
+  s.pnx = bits_i(r.w);
+  const float den = fmaf(s.nxs, r.y, -T_MUL(s.nys, r.x));
   if (den < 0.0f && s.pj != s.pstop) {
-    const float nw = fmaf(s.nxs, pc, T_MUL(s.nys, ps));
+    const float nw = fmaf(s.nxs, r.x, T_MUL(s.nys, r.y));
     s.tph = fmaf(-s.pk, T_DIV(nw, den), s.ptax);
   } else {
     s.tph = INFINITY;
@@ -541,15 +552,15 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
     const float pde = T_MUL(0x1p-21f, T_SQRT(nxy));
     const bool ccw = mz > 0.0f;
     const int j0 = ccw ? (sec + 1 == G.M ? 0 : sec + 1) : sec;
-    if (fabsf(fmaf(s.nx, G.PS[j0], -T_MUL(s.ny, G.PC[j0]))) <= pde &&
-        fmaf(s.nx, G.PC[j0], T_MUL(s.ny, G.PS[j0])) < 0.0f)
+    if (fabsf(fmaf(s.nx, G.PR[j0].y, -T_MUL(s.ny, G.PR[j0].x))) <= pde &&
+        fmaf(s.nx, G.PR[j0].x, T_MUL(s.ny, G.PR[j0].y)) < 0.0f)
       sec = ccw ? j0 : (sec == 0 ? G.M - 1 : sec - 1);
     const int se = classify_sector(G, s.nx, s.ny);  // the sector of the direction of travel
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int j = e == 0 ? se : (se + 1 == G.M ? 0 : se + 1);
-      if (fabsf(fmaf(s.nx, G.PS[j], -T_MUL(s.ny, G.PC[j]))) <= pde &&
-          fmaf(s.nx, G.PC[j], T_MUL(s.ny, G.PS[j])) > 0.0f)
+      if (fabsf(fmaf(s.nx, G.PR[j].y, -T_MUL(s.ny, G.PR[j].x))) <= pde &&
+          fmaf(s.nx, G.PR[j].x, T_MUL(s.ny, G.PR[j].y)) > 0.0f)
         s.pstop = j;
     }
   } else {
@@ -579,25 +590,20 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
   } else {
     s.tth = INFINITY;
   }
-  s.ia = G.SEC[sec];
+  s.ia = bits_i(G.PR[sec].z);
   if (ph_mode == 0) {
     const bool ccw = mz > 0.0f;
-    s.pdj = ccw ? 1 : -1;
-    s.pwrap = ccw ? G.M - 1 : 0;
-    s.pwto = G.M - 1 - s.pwrap;
-    s.soff = ccw ? 0 : G.M;
     s.nxs = ccw ? s.nx : -s.nx;
     s.nys = ccw ? s.ny : -s.ny;
-    s.pj = ccw ? (sec + 1 == G.M ? 0 : sec + 1) : sec;
+    s.pj = ccw ? (sec + 1 == G.M ? 0 : sec + 1) : G.M + sec;
+    if (s.pstop >= 0 && !ccw) s.pstop += G.M;
     phi_next(G, s);
     s.tph = fmaxf(s.tph, tcur);
   } else {  // no half-plane crossing, or the one jump to the sector of sec_ax
-    s.pdj = 1;
-    s.pwrap = G.M - 1;
-    s.pwto = 0;
-    s.soff = 0;
-    s.nxs = s.nys = 0.0f;
-    s.pj = ph_mode == 2 ? sec_ax : 0;
+    s.nxs = s.nys = 0.0f;  // no crossing after it: den = 0
+    s.pj = 0;
+    s.psec = bits_i(G.PR[sec_ax].z);
+    s.pnx = 0;
     s.tph = ph_mode == 2 ? t_ax : INFINITY;
   }
 
@@ -628,8 +634,8 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
         else s.tth = INFINITY;
       }
     } else {
-      s.ia = G.SEC[s.pj + s.soff];
-      s.pj = s.pj == s.pwrap ? s.pwto : s.pj + s.pdj;
+      s.ia = s.psec;
+      s.pj = s.pnx;
       phi_next(G, s);
       s.tph = fmaxf(s.tph, tcur);
     }
