@@ -245,8 +245,6 @@ struct RayState {
   int ie;
   int gie;       // the cone generator's region (after the last crossing it produced)
   bool th_br2;   // the generator is past the extremum of theta
-  int th_mode;   // 0 walk, 1 no crossings, 2 one jump pending (line through the origin)
-  int ie_jump;   // th_mode 2: the polar region after the jump
   int cn, ci;    // crossings in the cone list, index of the next one
   int cturn;     // crossings (counted from the list's first entry) before the polar direction turns
   int cdir;      // +1: the polar index rises at crossings before the turn, -1: it falls
@@ -500,11 +498,12 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
 
   // polar set-up
   s.ie = classify_theta(G, pz, pn);
+  int th_mode;  // 0 walk, 1 no crossings, 2 one jump (the line passes through the origin)
   if (s.b2 == 0.0f) {              // through the origin: theta jumps there
-    s.th_mode = tcur < 0.0f ? 2 : 1;
+    th_mode = tcur < 0.0f ? 2 : 1;
     if (tcur >= 0.0f) s.ie = classify_theta(G, s.nz, 1.0f);  // at or past the apex: the direction's bin
   } else if (s.qz != 0.0f) {
-    s.th_mode = 0;
+    th_mode = 0;
     s.th_sg = s.qz > 0.0f ? 1.0f : -1.0f;
     // |cos theta| at the extremum: sqrt(|m_xy|^2 / |m|^2)
     const float rho2 = fminf(T_DIV(s.mxy2.hi, T_ADD(s.mxy2.hi, s.mz2.hi)), 1.0f);
@@ -512,13 +511,13 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
     s.th_te = T_DIV(T_MUL(s.b2, s.nz), s.qz);
     s.th_br2 = !(tcur < s.th_te);
   } else if (s.nz != 0.0f) {       // q in the plane z = 0: cos(theta) monotone
-    s.th_mode = 0;
+    th_mode = 0;
     s.th_sg = s.nz > 0.0f ? 1.0f : -1.0f;
     s.th_fe = s.nz;
     s.th_te = INFINITY;
     s.th_br2 = false;
   } else {                         // horizontal line in the plane z = 0
-    s.th_mode = 1;
+    th_mode = 1;
   }
 
   // azimuth set-up
@@ -582,10 +581,13 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
   s.cturn = 0;
   s.cdir = 1;
   s.cmore = false;
-  if (s.th_mode == 2) {
+  if (th_mode == 2) {  // through the origin: one list entry, the jump to the direction's bin
+    L.t[0] = 0.0f;
     s.tth = 0.0f;
-    s.ie_jump = classify_theta(G, s.nz, 1.0f);
-  } else if (s.th_mode == 0) {
+    s.cn = 1;
+    s.cturn = L.cap;
+    s.cdir = classify_theta(G, s.nz, 1.0f) - s.ie;
+  } else if (th_mode == 0) {
     cone_fill(G, s, L);
   } else {
     s.tth = INFINITY;
@@ -623,16 +625,10 @@ TSP_HD bool trace_ray(const TGrid& G, const ff x[3], const ff d_in[3], Op& op, c
       radial_next(G, s);
       s.tr = fmaxf(s.tr, tcur);
     } else if (s.tth <= s.tph) {
-      if (s.th_mode == 2) {  // through the origin: the one jump
-        s.ie = s.ie_jump;
-        s.th_mode = 1;
-        s.tth = INFINITY;
-      } else {
-        s.ie += s.ci < s.cturn ? s.cdir : -s.cdir;
-        if (++s.ci < s.cn) s.tth = L.t[s.ci * L.stride];
-        else if (s.cmore) cone_fill(G, s, L);
-        else s.tth = INFINITY;
-      }
+      s.ie += s.ci < s.cturn ? s.cdir : -s.cdir;
+      if (++s.ci < s.cn) s.tth = L.t[s.ci * L.stride];
+      else if (s.cmore) cone_fill(G, s, L);
+      else s.tth = INFINITY;
     } else {
       s.ia = s.psec;
       s.pj = s.pnx;
