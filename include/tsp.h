@@ -315,6 +315,14 @@ tsp_status tsp_atten_backward(tsp_grid grid, tsp_geom geom, const float* rho, co
 tsp_status tsp_autotune(tsp_grid grid, tsp_geom geom, tsp_launch* fwd, tsp_launch* adj, void* stream);
 /* Cached choice for this size class, or TSP_ENOTSUP if it was never tuned. */
 tsp_status tsp_autotune_lookup(tsp_grid grid, tsp_geom geom, tsp_launch* fwd, tsp_launch* adj);
+/*
+ * Store fwd / adj as the cached choice for this size class, as if tuned (no
+ * timing, nothing launched): pins the knobs of later calls without explicit
+ * ones, for reproducible runs or to select a scatter strategy. Replaces an
+ * earlier choice. TSP_EINVAL for NULL handles or knobs outside the ranges of
+ * tsp_launch.
+ */
+tsp_status tsp_autotune_store(tsp_grid grid, tsp_geom geom, const tsp_launch* fwd, const tsp_launch* adj);
 /* Forget every cached choice. */
 void tsp_autotune_clear(void);
 

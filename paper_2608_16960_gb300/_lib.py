@@ -77,6 +77,7 @@ SIGNATURES = {
     "tsp_autotune": (_I, [_P, _P, _LP, _LP, _P]),
     "tsp_autotune_lookup": (_I, [_P, _P, _LP, _LP]),
     "tsp_autotune_clear": (None, []),
+    "tsp_autotune_store": (_I, [_P, _P, _LP, _LP]),
     "tsp_batch_create": (_I, [ctypes.POINTER(tsp_batch_item), _I, ctypes.POINTER(_P)]),
     "tsp_batch_workspace_bytes": (_I, [_P, _I, ctypes.POINTER(ctypes.c_size_t)]),
     "tsp_batch_sirt": (_I, [_P, _I, _I, _P, ctypes.c_size_t, _P]),

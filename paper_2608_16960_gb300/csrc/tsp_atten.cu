@@ -60,18 +60,21 @@ struct ProductGatherOp {
   __device__ __forceinline__ void end(int64_t ray) { out[ray] = acc; }
 };
 
-// Add x to *p; with AGG the active lanes of the warp that add to the same
-// address first combine their values and one of them adds the sum.
+// Add x to *p; with AGG a lane whose neighbour (lane ^ 1) adds to the same
+// key in this step hands its value over and the pair issues one atomic add.
 template <bool AGG>
 __device__ __forceinline__ void scatter_add(float* p, int key, float x) {
   if (AGG) {
-    cooperative_groups::coalesced_group act = cooperative_groups::coalesced_threads();
-    cooperative_groups::coalesced_group grp = cooperative_groups::labeled_partition(act, key);
-    const float sum = cooperative_groups::reduce(grp, x, cooperative_groups::plus<float>());
-    if (grp.thread_rank() == 0) atomicAdd(p, sum);
-  } else {
-    atomicAdd(p, x);
+    const unsigned m = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int pk = __shfl_xor_sync(m, key, 1);
+    const float px = __shfl_xor_sync(m, x, 1);
+    if (((m >> (lane ^ 1)) & 1u) && pk == key) {
+      if (lane & 1) return;
+      x = __fadd_rn(x, px);
+    }
   }
+  atomicAdd(p, x);
 }
 
 // Adjoint of ProductGatherOp: with w = g_tau1[ray], g_rho[v] += w sigma[v] dl

@@ -154,6 +154,15 @@ extern "C" tsp_status tsp_autotune_lookup(tsp_grid grid, tsp_geom geom, tsp_laun
   return TSP_OK;
 }
 
+extern "C" tsp_status tsp_autotune_store(tsp_grid grid, tsp_geom geom, const tsp_launch* fwd, const tsp_launch* adj) {
+  if (!grid || !geom) return fail(TSP_EINVAL, "tsp_autotune_store: NULL handle");
+  if (!fwd || !adj) return fail(TSP_EINVAL, "tsp_autotune_store: NULL knobs");
+  if (!valid_launch(*fwd) || !valid_launch(*adj)) return fail(TSP_EINVAL, "tsp_autotune_store: invalid launch knobs");
+  std::lock_guard<std::mutex> lock(g_mu);
+  g_cache[key_of(grid, geom)] = std::make_pair(*fwd, *adj);
+  return TSP_OK;
+}
+
 extern "C" void tsp_autotune_clear(void) {
   std::lock_guard<std::mutex> lock(g_mu);
   g_cache.clear();

@@ -11,8 +11,6 @@
 // all of them see bit-identical segments (same code, -fmad=false).
 #pragma once
 
-#include <cooperative_groups.h>
-#include <cooperative_groups/reduce.h>
 
 #include "tsp_internal.h"
 
@@ -262,24 +260,36 @@ struct ScatterOp {
   __device__ __forceinline__ void end(int64_t) {}
 };
 
-// Warp-aggregated scatter: lanes of a warp that hit the same voxel in the same
-// step combine their contributions and issue one atomic add.
+// Warp-aggregated scatter: a lane whose neighbour (lane ^ 1) adds to the same
+// voxel in the same step hands its contribution over, and the pair issues one
+// atomic add. Neighbouring rays of a cone view often sit in the same voxel at
+// the same step; the combine costs two shuffles per segment. (Groups of four,
+// and a full match of equal voxels with a group reduction, cost more in
+// shuffles than they saved in atomics.)
 template <int NB>
 struct AggScatterOp : ScatterOp<NB> {
   __device__ __forceinline__ void operator()(int v, float dl) {
-    cooperative_groups::coalesced_group act = cooperative_groups::coalesced_threads();
-    cooperative_groups::coalesced_group grp = cooperative_groups::labeled_partition(act, v);
+    const unsigned m = __activemask();  // the lanes with a segment in this step
+    const int lane = threadIdx.x & 31;
+    const int pv = __shfl_xor_sync(m, v, 1);
+    const bool pair = ((m >> (lane ^ 1)) & 1u) && pv == v;
+    if (NB == 1) {  // begin() skipped a ray whose value is zero
+      float c = __fmul_rn(this->w[0], dl);
+      const float pc = __shfl_xor_sync(m, c, 1);
+      if (pair) {
+        if (lane & 1) return;
+        c = __fadd_rn(c, pc);
+      }
+      atomicAdd(this->g + v, c);
+      return;
+    }
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-      if (b < this->nb) {
-        const float s = cooperative_groups::reduce(grp, __fmul_rn(this->w[b], dl), cooperative_groups::plus<float>());
-        if (grp.thread_rank() == 0) atomicAdd(this->g + b * this->V + v, s);
-      }
+      float c = __fmul_rn(this->w[b], dl);
+      const float pc = __shfl_xor_sync(m, c, 1);
+      if (pair && !(lane & 1)) c = __fadd_rn(c, pc);
+      if (b < this->nb && !(pair && (lane & 1)) && c != 0.0f) atomicAdd(this->g + b * this->V + v, c);
     }
-  }
-  __device__ __forceinline__ bool begin(int64_t ray) {
-    ScatterOp<NB>::begin(ray);
-    return true;  // every lane takes part in the warp-level combine
   }
 };
 

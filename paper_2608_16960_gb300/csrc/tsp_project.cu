@@ -41,7 +41,8 @@ struct DynGatherOp {
 };
 
 // Adjoint of DynGatherOp: g[view][v] += y dl, one atomic add per segment, or
-// (AGG) one per group of lanes of a warp that hit the same voxel in a step.
+// (AGG) one per pair of neighbouring lanes (lane, lane ^ 1) that hit the same
+// voxel in a step.
 template <bool AGG>
 struct DynScatterOp {
   const float* __restrict__ y;
@@ -52,17 +53,23 @@ struct DynScatterOp {
   __device__ __forceinline__ bool begin(int64_t ray) {
     base = g + (ray / per_view) * V;
     w = __ldg(y + ray);
-    return AGG || w != 0.0f;  // the aggregated form needs every lane in the combine
+    return w != 0.0f;
   }
   __device__ __forceinline__ void operator()(int v, float dl) {
+    float c = __fmul_rn(w, dl);
     if (AGG) {
-      cooperative_groups::coalesced_group act = cooperative_groups::coalesced_threads();
-      cooperative_groups::coalesced_group grp = cooperative_groups::labeled_partition(act, v);
-      const float s = cooperative_groups::reduce(grp, __fmul_rn(w, dl), cooperative_groups::plus<float>());
-      if (grp.thread_rank() == 0) atomicAdd(base + v, s);
-    } else {
-      atomicAdd(base + v, __fmul_rn(w, dl));
+      // the neighbour's voxel index is per view: compare the addresses
+      const unsigned m = __activemask();
+      const int lane = threadIdx.x & 31;
+      float* const a = base + v;
+      const unsigned long long pa = __shfl_xor_sync(m, reinterpret_cast<unsigned long long>(a), 1);
+      const float pc = __shfl_xor_sync(m, c, 1);
+      if (((m >> (lane ^ 1)) & 1u) && pa == reinterpret_cast<unsigned long long>(a)) {
+        if (lane & 1) return;
+        c = __fadd_rn(c, pc);
+      }
     }
+    atomicAdd(base + v, c);
   }
   __device__ __forceinline__ void end(int64_t) {}
 };

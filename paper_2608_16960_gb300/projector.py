@@ -259,6 +259,14 @@ def tsp_autotune_clear():
     _lib.load().tsp_autotune_clear()
 
 
+def tsp_autotune_store(grid: Grid, geom: Geometry, fwd, adj):
+    """Pin (block, tile, scatter) knobs for this size class as if tuned: later
+    calls without explicit knobs use them."""
+    f, a = tsp_launch(*fwd), tsp_launch(*adj)
+    check(_lib.load().tsp_autotune_store(grid.handle, geom.handle, ctypes.byref(f), ctypes.byref(a)),
+          "tsp_autotune_store")
+
+
 def tsp_count_segments(grid: Grid, geom: Geometry) -> torch.Tensor:
     """Valid segments per ray (int32, det_shape)."""
     L = _lib.load()

@@ -65,6 +65,7 @@ def test_null_arguments_rejected():
     n = ctypes.c_int64()
     assert L.tsp_geom_num_rays(None, ctypes.byref(n)) == 1
     assert L.tsp_geom_cone(0, None, None, None, 4, 4, 30.0, 30.0, None) == 1
+    assert L.tsp_autotune_store(None, None, None, None) == 1
 
 
 def test_stall_hook_rejects_bad_budgets():

@@ -17,7 +17,7 @@ from paper_2608_16960_gb300.projector import (AttenuatedOperator, Geometry, Grid
                                               optical_depth, optical_depth_adjoint, sunward_geometry, sunward_rays,
                                               tsp_device_status, tsp_forward)
 
-from _util import oracle_rays, parity
+from _util import oracle_rays, parity, pinned_scatter
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
@@ -82,24 +82,28 @@ def test_no_absorption_is_the_plain_projector(case):
     assert np.max(np.abs(y - y0)) <= 1e-6 * np.max(np.abs(y0))
 
 
-def test_backward_parity(case):
+@pytest.mark.parametrize("strategy", [0, 1], ids=["atomic", "warp-aggregated"])
+def test_backward_parity(case, strategy):
     wl, grid, geom, st, di, rho, sigma, sun = case
     tau1 = (0.5 * synth.uniform_volume(wl.edges.shape, 5)).astype(np.float32)
     gy = synth.SplitMix64(12).uniform(st.shape[0], -1.0, 1.0).astype(np.float32)
     t = [torch.tensor(a, device=DEV) for a in (rho, sigma, tau1)]
     y = atten_forward(grid, geom, *t)
-    g = atten_backward(grid, geom, *t, y, torch.tensor(gy, device=DEV).view_as(y))
+    with pinned_scatter([(grid, geom)], strategy):
+        g = atten_backward(grid, geom, *t, y, torch.tensor(gy, device=DEV).view_as(y))
     ref = atten.backward(wl.edges, st, di, rho, sigma, tau1, gy.astype(np.float64))
     for name, a, b in zip(("g_rho", "g_sigma", "g_tau1"), g, ref):
         grad_parity(a.cpu().numpy(), b, name)
     assert tsp_device_status() == 0
 
 
-def test_optical_depth_adjoint_parity(case):
+@pytest.mark.parametrize("strategy", [0, 1], ids=["atomic", "warp-aggregated"])
+def test_optical_depth_adjoint_parity(case, strategy):
     wl, grid, geom, st, di, rho, sigma, sun = case
     gt = synth.uniform_volume(wl.edges.shape, 19).astype(np.float32) - 0.5
-    g_rho, g_sig = optical_depth_adjoint(grid, sun, torch.tensor(rho, device=DEV), torch.tensor(sigma, device=DEV),
-                                         torch.tensor(gt, device=DEV))
+    with pinned_scatter([(grid, sun)], strategy):
+        g_rho, g_sig = optical_depth_adjoint(grid, sun, torch.tensor(rho, device=DEV),
+                                             torch.tensor(sigma, device=DEV), torch.tensor(gt, device=DEV))
     s, d = atten.sunward_rays(wl.edges, SUN)  # the oracle's own FP64 rays
     r_rho, r_sig = atten.optical_depth_backward(wl.edges, rho, sigma, s, d, gt)
     grad_parity(g_rho.cpu().numpy(), r_rho, "g_rho (tau_1)")

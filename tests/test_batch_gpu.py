@@ -24,7 +24,7 @@ from paper_2608_16960_gb300._lib import TspError
 from paper_2608_16960_gb300.projector import (Batch, Geometry, Grid, tsp_autotune, tsp_autotune_clear,
                                               tsp_device_status, tsp_forward, tsp_sirt)
 
-from _util import oracle_rays, parity, rays_near, sirt_parity, voxel_ball
+from _util import oracle_rays, parity, pinned_scatter, rays_near, sirt_parity, voxel_ball
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
@@ -110,6 +110,19 @@ def test_batch_matches_oracle_sirt(oracle_instances, nonneg):
     torch.cuda.synchronize()
     for i, it in enumerate(oracle_instances):
         _check_oracle_sirt(xs[i], it, 4, nonneg, f"batch instance {i} vs oracle")
+    assert tsp_device_status() == 0
+
+
+def test_batch_aggregated_scatter_matches_oracle_sirt(oracle_instances):
+    """Every instance pinned to the adjoint's neighbouring-lane combine (the
+    per-instance scatter strategy is read when the batch is created)."""
+    xs = [torch.zeros(it[0].shape, device=DEV) for it in oracle_instances]
+    with pinned_scatter([(it[0], it[1]) for it in oracle_instances], 1):
+        b = Batch([(g, geo, y, x) for (g, geo, y, *_), x in zip(oracle_instances, xs)])
+        b.sirt(4)
+        torch.cuda.synchronize()
+    for i, it in enumerate(oracle_instances):
+        _check_oracle_sirt(xs[i], it, 4, False, f"batch instance {i} (aggregated scatter) vs oracle")
     assert tsp_device_status() == 0
 
 

@@ -12,7 +12,7 @@ from paper_2608_16960_gb300 import synth, workloads
 from paper_2608_16960_gb300.projector import (Geometry, Grid, Operator, tsp_adjoint_dynamic, tsp_device_status,
                                               tsp_forward, tsp_forward_dynamic)
 
-from _util import oracle_rays, parity
+from _util import oracle_rays, parity, pinned_scatter
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
@@ -43,10 +43,12 @@ def test_forward_parity(case):
     assert tsp_device_status() == 0
 
 
-def test_adjoint_parity_and_identity(case):
+@pytest.mark.parametrize("strategy", [0, 1], ids=["atomic", "warp-aggregated"])
+def test_adjoint_parity_and_identity(case, strategy):
     wl, grid, geom, st, di, rho = case
     yv = synth.uniform_volume((NV, H, W), 3).astype(np.float32)
-    g = tsp_adjoint_dynamic(grid, geom, torch.tensor(yv, device=DEV)).cpu().numpy()
+    with pinned_scatter([(grid, geom)], strategy):
+        g = tsp_adjoint_dynamic(grid, geom, torch.tensor(yv, device=DEV)).cpu().numpy()
     ref = oracle.adjoint_dynamic(wl.edges, st, di, yv, NV)
     assert np.linalg.norm(g - ref) <= 2e-4 * np.linalg.norm(ref)
     y = tsp_forward_dynamic(grid, geom, torch.tensor(rho, device=DEV)).cpu().numpy().astype(np.float64)

@@ -302,6 +302,20 @@ def test_batched_equals_single(tiny):
         assert torch.allclose(gb[b], gs, rtol=1e-5, atol=1e-6)
 
 
+@pytest.mark.parametrize("strategy", [0, 1], ids=["atomic", "warp-aggregated"])
+def test_batched_adjoint_parity(tiny, strategy):
+    """F^T of a batch of 3 and of 11 (one chunk of 8 plus 3) against the
+    oracle per item, for both scatter strategies."""
+    wl, grid, geom, st, di = tiny
+    for B in (3, 11):
+        ys = np.stack([synth.uniform_volume(geom.det_shape, 110 + b) for b in range(B)]).astype(np.float32)
+        gb = tsp_adjoint(grid, geom, torch.tensor(ys, device=DEV), launch=(128, 8, strategy)).cpu().numpy()
+        for b in range(B):
+            ref = oracle.adjoint(wl.edges, st, di, ys[b].reshape(-1).astype(np.float64))
+            parity(gb[b], ref, what=f"batched adjoint {b} of {B}, strategy {strategy}")
+    assert tsp_device_status() == 0
+
+
 def test_launch_variants_bit_identical_forward(tiny):
     wl, grid, geom, st, di = tiny
     rho = torch.tensor(wl.rho, device=DEV)

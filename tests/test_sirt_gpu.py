@@ -8,7 +8,7 @@ from oracle import sirt as osirt
 from paper_2608_16960_gb300 import synth, workloads
 from paper_2608_16960_gb300.projector import Geometry, Grid, sirt_workspace, tsp_device_status, tsp_forward, tsp_sirt
 
-from _util import oracle_rays, parity
+from _util import oracle_rays, parity, pinned_scatter
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda"
@@ -33,6 +33,18 @@ def test_sirt_matches_oracle(tiny, n_iter, nonneg):
     tsp_sirt(grid, geom, yt, x, n_iter, nonneg=nonneg)
     ref = osirt.sirt(wl.edges, st, di, y.astype(np.float32), np.zeros(wl.edges.shape), n_iter, nonneg=nonneg)
     parity(x.cpu().numpy(), ref, what=f"sirt {n_iter}")
+    assert tsp_device_status() == 0
+
+
+def test_sirt_aggregated_scatter_matches_oracle(tiny):
+    """SIRT with the adjoint's neighbouring lanes combined before the atomic add."""
+    wl, grid, geom, st, di, y = tiny
+    x = torch.zeros(grid.shape, device=DEV)
+    yt = torch.tensor(y.astype(np.float32).reshape(geom.det_shape), device=DEV)
+    with pinned_scatter([(grid, geom)], 1):
+        tsp_sirt(grid, geom, yt, x, 5)
+    ref = osirt.sirt(wl.edges, st, di, y.astype(np.float32), np.zeros(wl.edges.shape), 5)
+    parity(x.cpu().numpy(), ref, what="sirt, aggregated scatter")
     assert tsp_device_status() == 0
 
 
