@@ -44,20 +44,24 @@ struct RunJoin {
 };
 
 // y_1[ray] = sum sigma[v] rho[v] dl over the sunward ray of each voxel
-// (tau_1 = F_1(sigma rho); the product is formed per segment).
+// (tau_1 = F_1(sigma rho); the product is formed per segment). Each
+// segment's loads are used at the next segment, as in DelayedSum.
 struct ProductGatherOp {
   const float* __restrict__ rho;
   const float* __restrict__ sigma;
   float* __restrict__ out;
-  float acc;
+  float acc, ps, pr, pdl;
   __device__ __forceinline__ bool begin(int64_t) {
-    acc = 0.0f;
+    acc = ps = pr = pdl = 0.0f;
     return true;
   }
   __device__ __forceinline__ void operator()(int v, float dl) {
-    acc = fmaf(__fmul_rn(__ldg(sigma + v), __ldg(rho + v)), dl, acc);
+    acc = fmaf(__fmul_rn(ps, pr), pdl, acc);
+    ps = __ldg(sigma + v);
+    pr = __ldg(rho + v);
+    pdl = dl;
   }
-  __device__ __forceinline__ void end(int64_t ray) { out[ray] = acc; }
+  __device__ __forceinline__ void end(int64_t ray) { out[ray] = fmaf(__fmul_rn(ps, pr), pdl, acc); }
 };
 
 // Add x to *p; with AGG a lane whose neighbour (lane ^ 1) adds to the same

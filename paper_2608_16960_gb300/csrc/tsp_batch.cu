@@ -72,13 +72,15 @@ struct BResid {
   const float* y;
   const float* R;
   float* r;
-  float acc;
+  DelayedSum sum;
   __device__ __forceinline__ bool begin(int64_t) {
-    acc = 0.0f;
+    sum.reset();
     return true;
   }
-  __device__ __forceinline__ void operator()(int v, float dl) { acc = fmaf(__ldg(x + v), dl, acc); }
-  __device__ __forceinline__ void end(int64_t ray) { r[ray] = __fmul_rn(__ldg(R + ray), __fsub_rn(__ldg(y + ray), acc)); }
+  __device__ __forceinline__ void operator()(int v, float dl) { sum.add(x + v, dl); }
+  __device__ __forceinline__ void end(int64_t ray) {
+    r[ray] = __fmul_rn(__ldg(R + ray), __fsub_rn(__ldg(y + ray), sum.total()));
+  }
 };
 
 template <int GK, class Op>

@@ -206,6 +206,24 @@ inline tsp_status check_trace_args(tsp_grid grid, tsp_geom geom, const void* a, 
 
 // ---- per-segment operations shared across translation units ----
 
+// A line integral accumulated one segment behind the walk: the value loaded
+// for a segment is added when the next segment (or the end of the ray) comes,
+// so the load's latency overlaps the walk's next step instead of stalling the
+// multiply-add. The terms are added in the same order, fma(value, length,
+// sum) per segment, so the result is the same bit for bit. The previous
+// term's multiply-add is issued before the new load (measured: the other
+// order, the load first, ran the forward 17% slower).
+struct DelayedSum {
+  float acc, pv, pdl;
+  __device__ __forceinline__ void reset() { acc = pv = pdl = 0.0f; }
+  __device__ __forceinline__ void add(const float* p, float dl) {
+    acc = fmaf(pv, pdl, acc);
+    pv = __ldg(p);
+    pdl = dl;
+  }
+  __device__ __forceinline__ float total() const { return fmaf(pv, pdl, acc); }
+};
+
 // y[b] = sum rho[b][v] dl  (Eq. 5), optionally followed by an epilogue.
 template <int NB>
 struct GatherOp {
@@ -214,17 +232,27 @@ struct GatherOp {
   int64_t V, n_rays;
   int nb;
   float acc[NB];
+  DelayedSum one;  // NB == 1
   __device__ __forceinline__ bool begin(int64_t) {
+    one.reset();
 #pragma unroll
     for (int b = 0; b < NB; ++b) acc[b] = 0.0f;
     return true;
   }
   __device__ __forceinline__ void operator()(int v, float dl) {
+    if (NB == 1) {
+      one.add(rho + v, dl);
+      return;
+    }
 #pragma unroll
     for (int b = 0; b < NB; ++b)
-      if (NB == 1 || b < nb) acc[b] = fmaf(__ldg(rho + b * V + v), dl, acc[b]);
+      if (b < nb) acc[b] = fmaf(__ldg(rho + b * V + v), dl, acc[b]);
   }
   __device__ __forceinline__ void end(int64_t ray) {
+    if (NB == 1) {
+      y[ray] = one.total();
+      return;
+    }
 #pragma unroll
     for (int b = 0; b < NB; ++b)
       if (b < nb) y[b * n_rays + ray] = acc[b];

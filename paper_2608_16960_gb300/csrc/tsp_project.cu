@@ -30,14 +30,14 @@ struct DynGatherOp {
   float* __restrict__ y;
   int64_t V, per_view;
   const float* base;
-  float acc;
+  DelayedSum sum;
   __device__ __forceinline__ bool begin(int64_t ray) {
     base = rho + (ray / per_view) * V;
-    acc = 0.0f;
+    sum.reset();
     return true;
   }
-  __device__ __forceinline__ void operator()(int v, float dl) { acc = fmaf(__ldg(base + v), dl, acc); }
-  __device__ __forceinline__ void end(int64_t ray) { y[ray] = acc; }
+  __device__ __forceinline__ void operator()(int v, float dl) { sum.add(base + v, dl); }
+  __device__ __forceinline__ void end(int64_t ray) { y[ray] = sum.total(); }
 };
 
 // Adjoint of DynGatherOp: g[view][v] += y dl, one atomic add per segment, or

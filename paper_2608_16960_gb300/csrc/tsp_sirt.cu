@@ -38,14 +38,14 @@ struct ResidualOp {
   const float* __restrict__ y;
   const float* __restrict__ R;
   float* __restrict__ r;
-  float acc;
+  DelayedSum sum;
   __device__ __forceinline__ bool begin(int64_t) {
-    acc = 0.0f;
+    sum.reset();
     return true;
   }
-  __device__ __forceinline__ void operator()(int v, float dl) { acc = fmaf(__ldg(x + v), dl, acc); }
+  __device__ __forceinline__ void operator()(int v, float dl) { sum.add(x + v, dl); }
   __device__ __forceinline__ void end(int64_t ray) {
-    r[ray] = __fmul_rn(__ldg(R + ray), __fsub_rn(__ldg(y + ray), acc));
+    r[ray] = __fmul_rn(__ldg(R + ray), __fsub_rn(__ldg(y + ray), sum.total()));
   }
 };
 

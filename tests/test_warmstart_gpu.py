@@ -83,24 +83,39 @@ def test_training_improves_on_the_input(ws):
     assert np.mean(gains) > 0, gains
 
 
-def test_captured_warm_start_equals_the_launches(ws):
+def test_captured_warm_start_equals_the_launches():
     """The warm start replayed as a captured CUDA graph gives the eager
-    launches' result (to float32 summation order: this pipeline
-    back-projects with atomic adds, so even two replays may differ in the
-    last bits), and is captured again after the weights change (one
-    training step)."""
-    close = lambda u, v: float((u - v).abs().max()) <= 1e-4 * float(v.abs().max())
+    launches' result bit for bit, and is captured again after the weights
+    change (one training step). From stored segment lists every sum of the
+    pipeline has a fixed order, so the two must agree exactly."""
+    e = synth.grid_edges(12, 10, 32)
+    w = WarmStart(e, synth.circular_orbit(12, 60.0, incline_deg=35.0), 32, 50.0, max_batch=4, use_lists=True)
+    rho = w.phantoms([4242])
+    y = w.measure(rho, [4242])[0]
+    a = w.warm_start(y)
+    assert torch.equal(a, w._warm_start_launches(y))
+    assert torch.equal(w.warm_start(y), a)  # replay with the same input
+    y2 = w.measure(w.phantoms([4243]), [4243])[0]
+    assert torch.equal(w.warm_start(y2), w._warm_start_launches(y2))  # new input, same graph
+    w.train(4, batch=4, lr=1e-3, seed0=77)
+    b = w.warm_start(y)
+    assert torch.equal(b, w._warm_start_launches(y))  # new weights: captured again
+    assert not torch.equal(b, a)  # (a stale graph would repeat a)
+
+
+def test_captured_warm_start_on_the_fly(ws):
+    """The same with the on-the-fly back-projection, whose atomic adds sum in
+    a varying order: two eager runs of the pipeline differ by a few float32
+    ulps in the network's input, which the bf16 activations can round apart
+    (measured up to 3.5e-4 of the largest output between two eager runs after
+    a training step). Graph and launches agree to 2e-3 of the largest value."""
+    close = lambda u, v: float((u - v).abs().max()) <= 2e-3 * float(v.abs().max())
     rho = ws.phantoms([4242])
     y = ws.measure(rho, [4242])[0]
     a = ws.warm_start(y)
     assert close(a, ws._warm_start_launches(y))
-    assert close(ws.warm_start(y), a)  # replay with the same input
-    y2 = ws.measure(ws.phantoms([4243]), [4243])[0]
-    assert close(ws.warm_start(y2), ws._warm_start_launches(y2))  # new input, same graph
     ws.train(4, batch=4, lr=1e-3, seed0=77)
-    b = ws.warm_start(y)
-    assert close(b, ws._warm_start_launches(y))  # new weights: captured again
-    assert not close(b, a)
+    assert close(ws.warm_start(y), ws._warm_start_launches(y))
 
 
 def test_list_weights_match_traversal_weights_and_repeat():
