@@ -47,12 +47,13 @@ STREAM_DRAM_BYTES_PER_ENTRY = 8.38
 # (add, exponential counted as one, multiply, fma).
 ATTEN_EXTRA_OPS = 6.0
 # DRAM bytes (read + write) per launch of the on-the-fly traversal, from ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on the 8 + 8-view case, mean
-# of the cone and parallel launches: the volume and the grid table are read
-# once and the detector values stay in L2, so the figure does not grow with
-# the views (2.74 MB at 2 views, 2.77 MB at 8 for the cone forward). None
-# once the kernel changes after the capture.
-TRACE_DRAM_BYTES = {"forward": 0.5 * (2769920 + 2962944), "adjoint": 0.5 * (4854784 + 5058560)}
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the 8 + 8-view case with
+# the tuned launches pinned, mean of the cone and parallel launches (the cone
+# adjoint with neighbouring lanes combined): the volume and the grid table
+# are read once and the detector values stay in L2, so the figure does not
+# grow with the views (2.74 MB at 2 views, 2.77 MB at 8 for the cone
+# forward). None once the kernel changes after the capture.
+TRACE_DRAM_BYTES = {"forward": 0.5 * (2771712 + 2930176), "adjoint": 0.5 * (4858368 + 5026560)}
 
 
 _LOG = ""
@@ -108,6 +109,11 @@ def parse():
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start leg")
     ap.add_argument("--no-autotune", action="store_true",
                     help="paper-scale workload: default launch knobs instead of the autotuner's (profiling captures)")
+    ap.add_argument("--pin-launches", default="",
+                    help="paper-scale workload: launch knobs per view kind instead of the autotuner's, as a run "
+                         "prints them in config.launch_fwd_adj (JSON, e.g. "
+                         "'{\"cone\": [[128, 8, 0], [128, 16, 1]], \"parallel\": [[128, 8, 0], [128, 8, 0]]}'); "
+                         "profiling captures of the tuned kernels without the autotuner's launches")
     ap.add_argument("--target", type=float, default=0.01, help="warm start: relative error target")
     ap.add_argument("--log", default="", help="also append the JSON line to this file (JSONL)")
     ap.add_argument("--ws-lr", type=float, default=2e-3, help="warm start: peak Adam step size (cosine decay)")
@@ -320,10 +326,18 @@ def run_ours(args):
     ws = [torch.tensor(synth.uniform_volume(g.det_shape, 100 + i), device="cuda") for i, g in enumerate(geoms)]
     gs = [torch.empty(grid.shape, device="cuda") for _ in geoms]
     n_rays = sum(g.n_rays for g in geoms)
-    from paper_2608_16960_gb300.projector import tsp_autotune
+    from paper_2608_16960_gb300.projector import tsp_autotune, tsp_autotune_store
     # setup, outside the timed region (skipped for profiling captures, which
-    # then run the default launch knobs)
-    tuned = [None if args.no_autotune else tsp_autotune(grid, g) for g in geoms]
+    # then run the default or the pinned launch knobs)
+    if args.pin_launches:
+        pins = json.loads(args.pin_launches)
+        tuned = []
+        for v, g in zip(wl.views, geoms):
+            f, a = (tuple(int(k) for k in knobs) for knobs in pins[v.kind])
+            tsp_autotune_store(grid, g, f, a)
+            tuned.append((f, a))
+    else:
+        tuned = [None if args.no_autotune else tsp_autotune(grid, g) for g in geoms]
     segs = [int(tsp_count_segments(grid, g).sum().item()) for g in geoms]
     n_segs = sum(segs)
     flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")  # 256 MB > 129 MB L2
@@ -462,7 +476,9 @@ def run_ours(args):
     l2_gbs = ((4.0 if dom == "forward" else 8.0) * seg_per_launch + 4.0 * n_dom_rays) / t_dom_launch / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Tops/s", "frac": achieved / peak_ops,
                 "traffic": TRACE_DRAM_BYTES[dom] if not args.views else None,
-                "kernel": "trace_kernel<GatherOp> (F)" if dom == "forward" else "trace_kernel<ScatterOp> (F^T)",
+                "kernel": "trace_kernel<GatherOp> (F)" if dom == "forward" else
+                          "trace_kernel<" + " / ".join(sorted({"AggScatterOp" if t and t[1][2] == 1 else "ScatterOp"
+                                                              for t in tuned})) + "> (F^T)",
                 "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz",
                 "ops_per_segment": OPS_PER_SEGMENT,
                 "l2_gbs": l2_gbs,
