@@ -1,5 +1,6 @@
-"""Host logic of bench.py that needs no GPU: the wording of the oracle sample
-and the calibration of the CPU baseline's stride toward its time target."""
+"""Host logic of bench.py that needs no GPU: the wording of the oracle sample,
+the calibration of the CPU baseline's stride toward its time target and the
+parsing of pinned launch knobs."""
 import sys
 import types
 
@@ -57,3 +58,14 @@ def test_emit_appends_jsonl(monkeypatch, capsys):
     os.remove(log)
     assert [json.loads(x)["value"] for x in lines] == [1.0, 2.0]
     assert capsys.readouterr().out.splitlines() == lines
+
+
+def test_pinned_launches_parse_the_printed_form():
+    import pytest
+    spec = '{"cone": [[128, 8, 0], [128, 16, 1]], "parallel": [[128, 8, 0], [128, 8, 0]]}'
+    assert bench.pinned_launches(spec, ["cone", "parallel"]) == [((128, 8, 0), (128, 16, 1)),
+                                                                  ((128, 8, 0), (128, 8, 0))]
+    with pytest.raises(SystemExit):
+        bench.pinned_launches('{"cone": [[128, 8, 0], [128, 8, 1]]}', ["cone", "parallel"])
+    with pytest.raises(SystemExit):
+        bench.pinned_launches('{"cone": [[128, 8], [128, 8, 1]]}', ["cone"])
