@@ -16,8 +16,7 @@ namespace tsp {
 constexpr double kTablePi = 3.14159265358979323846;
 constexpr double kTableTwoPi = 2.0 * kTablePi;
 
-// Shared-memory table of a grid (layout PR | RR | C | S2 | S2L | K2 | K2L | PA;
-// the *L arrays hold the float32 rounding residue of the
+// Shared-memory table of a grid (layout PR | CR | RR | S2L | K2L | PA; the *L arrays hold the float32 rounding residue of the
 // preceding high parts, computed in double). Pure host
 // arithmetic: radii squared, cosines of the polar edges, and the azimuth
 // half-planes with their sector-to-voxel map. Fills the grid's dimensions.
@@ -51,7 +50,7 @@ inline void build_grid_table(const double* r_edges, int n_r_edges, const double*
   g->M = int(planes.size());
   g->pa0 = float(planes[0]);
   const int M = g->M;
-  g->words = 8 * M + 2 * (Nr + 2) + 5 * (Ne + 1) + M;
+  g->words = 8 * M + 4 * (Ne + 3) + 2 * (Nr + 2) + 2 * (Ne + 1) + M;
   std::vector<float>& table = *table_out;
   table.assign(size_t(g->words), 0.0f);
   // Half-plane records first (16-byte aligned): record j < M serves a line
@@ -72,17 +71,20 @@ inline void build_grid_table(const double* r_edges, int n_r_edges, const double*
     put_int(dn + 2, sec[jm]);
     put_int(dn + 3, M + jm);
   }
+  // Cone records (cos theta_k, sin^2 theta_k, cos^2 theta_k, 0), k = 0..N_e,
+  // between records for k = -1 (cos = +inf) and k = N_e + 1 (cos = -inf) that
+  // end a cone run without a range test
+  float* CR = table.data() + 8 * M + 4;
+  CR[-4] = std::numeric_limits<float>::infinity();
+  CR[4 * (Ne + 1)] = -std::numeric_limits<float>::infinity();
   // Squared radii as (high, low) pairs, starting with a pair for k = -1 (the
   // hole inside the innermost sphere: no crossing), so that R_k^2 - b^2 needs
   // no range test
-  float* RR = table.data() + 8 * M + 2;
+  float* RR = CR + 4 * (Ne + 2) + 2;
   RR[-2] = -std::numeric_limits<float>::infinity();
   RR[-1] = 0.0f;
-  float* C = RR + 2 * (Nr + 1);
-  float* S2 = C + (Ne + 1);
-  float* S2L = S2 + (Ne + 1);
-  float* K2 = S2L + (Ne + 1);
-  float* K2L = K2 + (Ne + 1);
+  float* S2L = RR + 2 * (Nr + 1);  // low parts of sin^2 and cos^2
+  float* K2L = S2L + (Ne + 1);
   float* PA = K2L + (Ne + 1);
   auto split = [](double v, float* hi, float* lo) {
     *hi = float(v);
@@ -92,9 +94,9 @@ inline void build_grid_table(const double* r_edges, int n_r_edges, const double*
   for (int k = 0; k <= Ne; ++k) {
     const double t = std::min(kTablePi, std::max(0.0, theta_edges[k]));
     const double c = std::cos(t), sn = std::sin(t);
-    C[k] = float(c);
-    split(sn * sn, &S2[k], &S2L[k]);
-    split(c * c, &K2[k], &K2L[k]);
+    CR[4 * k] = float(c);
+    split(sn * sn, &CR[4 * k + 1], &S2L[k]);
+    split(c * c, &CR[4 * k + 2], &K2L[k]);
   }
   for (int j = 0; j < M; ++j) PA[j] = float(planes[j] - planes[0]);
 }

@@ -86,11 +86,10 @@ __device__ __forceinline__ float sqrt_approx_(float x) {
 struct TGrid {
   const float2* RR; // [Nr+1] squared sphere radii (high, low): R_k^2 = x + y to ~2^-48;
                     // RR[-1] = (-inf, 0)
-  const float* C;   // [Ne+1] cos(theta_k), decreasing
-  const float* S2;  // [Ne+1] sin^2(theta_k), high part
-  const float* S2L; // [Ne+1] low part
-  const float* K2;  // [Ne+1] cos^2(theta_k), high part
-  const float* K2L; // [Ne+1] low part
+  const float4* CR; // [Ne+1] (cos theta_k decreasing, sin^2 and cos^2 theta_k high parts, 0);
+                    // CR[-1].x = +inf, CR[Ne+1].x = -inf
+  const float* S2L; // [Ne+1] low part of sin^2(theta_k)
+  const float* K2L; // [Ne+1] low part of cos^2(theta_k)
   const float4* PR; // [2M] half-plane records (cos psi_j, sin psi_j, sector beyond, next record)
                     // as int bits: record j for azimuth growing (the sector
                     // counter-clockwise of plane j, then record j+1 mod M), record M + j
@@ -102,7 +101,7 @@ struct TGrid {
 
 // Device-side description of a grid's table in global memory.
 struct GridDesc {
-  const float* table;  // PR | (-inf, 0) RR | C | S2 | S2L | K2 | K2L | PA (16-byte aligned)
+  const float* table;  // PR | CR | (-inf, 0) RR | S2L | K2L | PA (16-byte aligned)
   int Nr, Ne, Na, M;
   int words;           // table length in 32-bit words
   float pa0;
@@ -111,12 +110,10 @@ struct GridDesc {
 TSP_HD TGrid tgrid_from_smem(const GridDesc& d, const float* s) {
   TGrid g;
   g.PR = reinterpret_cast<const float4*>(s);
-  g.RR = reinterpret_cast<const float2*>(s + 8 * d.M + 2);
-  g.C = s + 8 * d.M + 2 + 2 * (d.Nr + 1);
-  g.S2 = g.C + (d.Ne + 1);
-  g.S2L = g.S2 + (d.Ne + 1);
-  g.K2 = g.S2L + (d.Ne + 1);
-  g.K2L = g.K2 + (d.Ne + 1);
+  g.RR = reinterpret_cast<const float2*>(s + 8 * d.M + 4 * (d.Ne + 3) + 2);
+  g.CR = reinterpret_cast<const float4*>(s + 8 * d.M + 4);
+  g.S2L = s + 8 * d.M + 4 * (d.Ne + 3) + 2 + 2 * (d.Nr + 1);
+  g.K2L = g.S2L + (d.Ne + 1);
   g.PA = g.K2L + (d.Ne + 1);
   g.Nr = d.Nr;
   g.Ne = d.Ne;
@@ -153,7 +150,7 @@ TSP_HD int classify_theta(const TGrid& G, float pz, float pn) {
   int lo = 0, hi = G.Ne + 1;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (G.C[mid] * pn >= pz) lo = mid + 1;
+    if (G.CR[mid].x * pn >= pz) lo = mid + 1;
     else hi = mid;
   }
   return lo - 1;
@@ -290,15 +287,15 @@ TSP_HD void radial_next(const TGrid& G, RayState& s) {
 
 // W = sqrt(b2 sin^2 theta_k - m_z^2) = sqrt(|m_xy|^2 sin^2 - m_z^2 cos^2) with
 // m = q x n, the difference taken in float-float (it cancels at tangency).
-TSP_HD float cone_w(const TGrid& G, const RayState& s, int k) {
+TSP_HD float cone_w(const TGrid& G, const RayState& s, int k, const float4& cr) {
   // Far from tangency (the difference keeps at least a quarter of its terms'
   // magnitude) float32 already gives W to about an ulp.
-  const float a0 = T_MUL(s.mxy2.hi, G.S2[k]);
-  const float b0 = T_MUL(s.mz2.hi, G.K2[k]);
+  const float a0 = T_MUL(s.mxy2.hi, cr.y);
+  const float b0 = T_MUL(s.mz2.hi, cr.z);
   const float w2f = T_SUB(a0, b0);
   if (w2f >= T_MUL(0.25f, T_ADD(a0, b0))) return T_SQRTA(w2f);
-  const ff a = ff_mul(s.mxy2, ff{G.S2[k], G.S2L[k]});
-  const ff b = ff_mul(s.mz2, ff{G.K2[k], G.K2L[k]});
+  const ff a = ff_mul(s.mxy2, ff{cr.y, G.S2L[k]});
+  const ff b = ff_mul(s.mz2, ff{cr.z, G.K2L[k]});
   const float w2 = T_ADD(T_SUB(a.hi, b.hi), T_SUB(a.lo, b.lo));
   return T_SQRTA(fmaxf(w2, 0.0f));
 }
@@ -313,9 +310,10 @@ TSP_HD bool theta_gen(const TGrid& G, RayState& s, float& t, int& dir) {
     const float lim = s.th_br2 ? s.nz : s.th_fe;
     if (dec) {  // theta decreasing: next is the cone at the region's small-theta side
       const int k = s.gie;
-      if (k >= 0 && G.C[k] < lim) {
-        const float c = G.C[k];
-        const float W = cone_w(G, s, k);
+      const float4 cr = G.CR[k];
+      if (cr.x < lim) {  // (+inf at k = -1)
+        const float c = cr.x;
+        const float W = cone_w(G, s, k, cr);
         const float num = fmaf(-s.qz, W, T_MUL(s.b2nz, c));
         const float den = fmaf(s.nz, W, T_MUL(s.qz, c));
         t = den > 0.0f ? T_DIV(num, den) : (s.th_br2 ? INFINITY : -INFINITY);
@@ -325,9 +323,10 @@ TSP_HD bool theta_gen(const TGrid& G, RayState& s, float& t, int& dir) {
       }
     } else {  // theta increasing: next is the cone at the region's large-theta side
       const int k = s.gie + 1;
-      if (k <= G.Ne && G.C[k] > lim) {
-        const float c = G.C[k];
-        const float W = cone_w(G, s, k);
+      const float4 cr = G.CR[k];
+      if (cr.x > lim) {  // (-inf at k = N_e + 1)
+        const float c = cr.x;
+        const float W = cone_w(G, s, k, cr);
         const float num = fmaf(s.qz, W, T_MUL(s.b2nz, c));
         const float den = fmaf(-s.nz, W, T_MUL(s.qz, c));
         t = den > 0.0f ? T_DIV(num, den) : (s.th_br2 ? INFINITY : -INFINITY);
