@@ -135,9 +135,12 @@ extern "C" tsp_status tsp_grid_create(const double* r_edges, int n_r_edges, cons
   g->ph.assign(phi_edges, phi_edges + n_phi_edges);
   std::vector<float> table;
   tsp::build_grid_table(r_edges, n_r_edges, theta_edges, n_theta_edges, phi_edges, n_phi_edges, &table, g);
-  if (g->words > 12288) {  // kernels stage the table in at most 48 KB of shared memory
+  // Kernels stage the table in shared memory beside the cone lists (24 KB a
+  // block): at most 227 KB a block on this GPU. The grid limits keep the table
+  // under 107 KB, so this only guards the layout's arithmetic.
+  if (g->words > (232448 - 24576 - 4096) / 4) {
     delete g;
-    return fail(TSP_ENOTSUP, "tsp_grid_create: boundary tables exceed 48 KB (too many edges)");
+    return fail(TSP_ENOTSUP, "tsp_grid_create: boundary tables exceed the shared memory of a block (too many edges)");
   }
   // voxel centres at the arithmetic midpoints of the edges (for phantoms and models)
   std::vector<float> centres(size_t(Nr + 2 * Ne + 2 * Na));

@@ -121,7 +121,7 @@ __device__ __forceinline__ bool ray_of_thread(const GeomArgs& ga, int tw, int64_
 // Shared memory: the grid table, then each thread's cone-crossing list of
 // ccap entries (thread i's entry j at word words + j * blockDim + i).
 template <int GK, class Op>
-__global__ void __launch_bounds__(512, 1) trace_kernel(GridDesc gd, GeomArgs ga, Op op, int tw, int ccap) {
+__device__ __forceinline__ void trace_body(const GridDesc& gd, const GeomArgs& ga, Op& op, int tw, int ccap) {
   extern __shared__ float smem[];
   load_table(gd, smem);
   const TGrid G = tgrid_from_smem(gd, smem);
@@ -133,6 +133,29 @@ __global__ void __launch_bounds__(512, 1) trace_kernel(GridDesc gd, GeomArgs ga,
   if (!trace_ray(G, x, d, op, L)) atomicOr(&g_tsp_error_word, 1);
   op.end(ray);
 }
+
+template <int GK, class Op>
+__global__ void __launch_bounds__(512, 1) trace_kernel(GridDesc gd, GeomArgs ga, Op op, int tw, int ccap) {
+  trace_body<GK>(gd, ga, op, tw, ccap);
+}
+
+// The same for ops that declare `static constexpr bool cap_registers = true`:
+// at most 72 registers a thread, the count that keeps 7 blocks of 128
+// threads on an SM (the gather's compiler-chosen allocation otherwise grows
+// past it and costs a block).
+template <int GK, class Op>
+__global__ void __maxnreg__(72) trace_kernel_r72(GridDesc gd, GeomArgs ga, Op op, int tw, int ccap) {
+  trace_body<GK>(gd, ga, op, tw, ccap);
+}
+
+template <class Op, class = void>
+struct op_caps_registers {
+  static constexpr bool value = false;
+};
+template <class Op>
+struct op_caps_registers<Op, decltype(void(Op::cap_registers))> {
+  static constexpr bool value = Op::cap_registers;
+};
 
 // Cone-crossing list entries per thread: 48 up to 128 threads per block
 // (24 KB per block; one ray in two hundred at the paper-scale workload has
@@ -174,15 +197,18 @@ void launch_trace(const tsp_grid_s* grid, const tsp_geom_s* geom, const tsp_laun
   const LaunchShape s = shape_for(grid, geom, l);
   const GridDesc gd = grid->desc();
   const GeomArgs ga = geom_args(geom);
-  if (geom->kind == GEOM_CONE) {
-    allow_smem(trace_kernel<GEOM_CONE, Op>, s.smem);
-    trace_kernel<GEOM_CONE, Op><<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w, s.ccap);
-  } else if (geom->kind == GEOM_PARALLEL) {
-    allow_smem(trace_kernel<GEOM_PARALLEL, Op>, s.smem);
-    trace_kernel<GEOM_PARALLEL, Op><<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w, s.ccap);
+  auto go = [&](auto kernel) {
+    allow_smem(kernel, s.smem);
+    kernel<<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w, s.ccap);
+  };
+  if constexpr (op_caps_registers<Op>::value) {
+    if (geom->kind == GEOM_CONE) go(trace_kernel_r72<GEOM_CONE, Op>);
+    else if (geom->kind == GEOM_PARALLEL) go(trace_kernel_r72<GEOM_PARALLEL, Op>);
+    else go(trace_kernel_r72<GEOM_RAYS, Op>);
   } else {
-    allow_smem(trace_kernel<GEOM_RAYS, Op>, s.smem);
-    trace_kernel<GEOM_RAYS, Op><<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w, s.ccap);
+    if (geom->kind == GEOM_CONE) go(trace_kernel<GEOM_CONE, Op>);
+    else if (geom->kind == GEOM_PARALLEL) go(trace_kernel<GEOM_PARALLEL, Op>);
+    else go(trace_kernel<GEOM_RAYS, Op>);
   }
 }
 
@@ -227,6 +253,7 @@ struct DelayedSum {
 // y[b] = sum rho[b][v] dl  (Eq. 5), optionally followed by an epilogue.
 template <int NB>
 struct GatherOp {
+  static constexpr bool cap_registers = NB == 1;  // (the batched forms would spill under the cap)
   const float* __restrict__ rho;
   float* __restrict__ y;
   int64_t V, n_rays;

@@ -300,47 +300,6 @@ TSP_HD float cone_w(const TGrid& G, const RayState& s, int k, const float4& cr) 
   return T_SQRTA(fmaxf(w2, 0.0f));
 }
 
-// Next crossing of the cone family after the generator's region s.gie (in
-// its phase s.th_br2): t before clamping and the direction (+1: theta grows,
-// the polar index goes up; -1: it goes down). False when none is left.
-TSP_HD bool theta_gen(const TGrid& G, RayState& s, float& t, int& dir) {
-#pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) {
-    const bool dec = s.th_br2 ? (s.th_sg < 0.0f) : (s.th_sg > 0.0f);
-    const float lim = s.th_br2 ? s.nz : s.th_fe;
-    if (dec) {  // theta decreasing: next is the cone at the region's small-theta side
-      const int k = s.gie;
-      const float4 cr = G.CR[k];
-      if (cr.x < lim) {  // (+inf at k = -1)
-        const float c = cr.x;
-        const float W = cone_w(G, s, k, cr);
-        const float num = fmaf(-s.qz, W, T_MUL(s.b2nz, c));
-        const float den = fmaf(s.nz, W, T_MUL(s.qz, c));
-        t = den > 0.0f ? T_DIV(num, den) : (s.th_br2 ? INFINITY : -INFINITY);
-        dir = -1;
-        s.gie = k - 1;
-        return t < INFINITY;
-      }
-    } else {  // theta increasing: next is the cone at the region's large-theta side
-      const int k = s.gie + 1;
-      const float4 cr = G.CR[k];
-      if (cr.x > lim) {  // (-inf at k = N_e + 1)
-        const float c = cr.x;
-        const float W = cone_w(G, s, k, cr);
-        const float num = fmaf(s.qz, W, T_MUL(s.b2nz, c));
-        const float den = fmaf(-s.nz, W, T_MUL(s.qz, c));
-        t = den > 0.0f ? T_DIV(num, den) : (s.th_br2 ? INFINITY : -INFINITY);
-        dir = 1;
-        s.gie = k;
-        return t < INFINITY;
-      }
-    }
-    if (s.th_br2) break;
-    s.th_br2 = true;  // no more crossings before the extremum: continue past it
-  }
-  return false;
-}
-
 // Cone crossings are produced ahead of the walk, up to L.cap at a time, into
 // a per-ray list (shared memory on the device: entry i at t[i * stride]).
 // Every lane of a warp fills its list in the same loop, so the crossing
@@ -354,33 +313,59 @@ struct ConeList {
 };
 
 // theta(t) along a line is unimodal, so the polar index moves one way until
-// the extremum and the other way after it: the list keeps the first
-// direction and the number of crossings before the turn.
+// the extremum (phase s.th_br2 false) and the other way after it (true). The
+// fill runs the phases in turn from the generator's region s.gie: the next
+// cone is the region's small-theta side (k = gie) while theta decreases, its
+// large-theta side (k = gie + 1) while it increases, as long as that cone is
+// reached before the phase's limit on cos theta (the +-inf records end the
+// run at the axis). The list keeps the direction of the phase it started in
+// and the number of crossings made in it (after them the direction is
+// reversed). A crossing at t = +inf ends the sequence.
 TSP_HD void cone_fill(const TGrid& G, RayState& s, const ConeList& L) {
-  int n = 0, turn = L.cap, d0 = 0;
-  float prev = s.tgen, first = INFINITY;
+  int n = 0, n0 = 0, d0 = 0;
+  float prev = s.tgen;
+  bool more = true;
 #pragma unroll 1
-  for (; n < L.cap; ++n) {
-    float t;
-    int dir;
-    if (!theta_gen(G, s, t, dir)) break;
-    t = fmaxf(t, prev);
-    prev = t;
-    if (n == 0) {
-      first = t;
-      d0 = dir;
-    } else if (dir != d0 && turn == L.cap) {
-      turn = n;
+  for (int phase = 0; phase < 2; ++phase) {
+    const bool dec = s.th_br2 ? (s.th_sg < 0.0f) : (s.th_sg > 0.0f);
+    const float lim = s.th_br2 ? s.nz : s.th_fe;
+    // the cone test c < lim (decreasing) or c > lim (increasing) as one
+    // compare, and the root's signs, of the phase
+    const float csg = dec ? 1.0f : -1.0f, lims = dec ? lim : -lim;
+    const float qzs = dec ? -s.qz : s.qz, nzs = dec ? s.nz : -s.nz;
+    const float tden = s.th_br2 ? INFINITY : -INFINITY;  // a non-positive denominator
+    const int koff = dec ? 0 : 1, kstep = dec ? -1 : 1;
+    if (phase == 0) d0 = kstep;
+#pragma unroll 1
+    for (; n < L.cap; ++n) {
+      const int k = s.gie + koff;
+      const float4 cr = G.CR[k];
+      if (!(T_MUL(csg, cr.x) < lims)) break;
+      const float c = cr.x;
+      const float W = cone_w(G, s, k, cr);
+      const float num = fmaf(qzs, W, T_MUL(s.b2nz, c));
+      const float den = fmaf(nzs, W, T_MUL(s.qz, c));
+      float t = den > 0.0f ? T_DIV(num, den) : tden;
+      s.gie += kstep;
+      if (!(t < INFINITY)) {
+        more = false;
+        break;
+      }
+      t = fmaxf(t, prev);
+      prev = t;
+      L.t[n * L.stride] = t;
     }
-    L.t[n * L.stride] = t;
+    if (phase == 0) n0 = n;
+    if (n == L.cap || !more || s.th_br2) break;
+    s.th_br2 = true;  // no more crossings before the extremum: continue past it
   }
   s.cmore = n == L.cap;
   s.cn = n;
   s.ci = 0;
-  s.cturn = turn;
+  s.cturn = n0;
   s.cdir = d0;
   s.tgen = prev;
-  s.tth = first;
+  s.tth = n > 0 ? L.t[0] : INFINITY;
 }
 
 // Crossing of half-plane pj, if the line meets it: the sign of m_z is folded

@@ -447,7 +447,7 @@ def test_lines_passing_just_off_the_axis():
 
 
 def test_grid_whose_table_exceeds_48_kb_of_shared_memory():
-    """1024 x 1024 x 512 voxels (2.1 GB volume): the grid table (36 KB) and
+    """1024 x 1024 x 512 voxels (2.1 GB volume): the grid table (51 KB) and
     the per-thread cone lists need more than the default 48 KB of dynamic
     shared memory per block, which the launch opts into. Forward on a 64 x 64
     cone view against the oracle on every 7th ray; the adjoint identity."""
