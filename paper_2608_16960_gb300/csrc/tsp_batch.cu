@@ -118,9 +118,11 @@ __device__ __forceinline__ void trace_any(const TGrid& G, const InstDesc& d, int
 
 // Persistent traversal stage over all instances, one kernel per stage (each
 // holds one per-segment operation, so the walk's registers are those of that
-// operation alone).
+// operation alone). At most 72 registers a thread, which keeps 7 blocks of
+// 128 threads per SM: the compiler's own choice, 92-109, allows 4 (measured:
+// the 64-instance schedule 14.4 s uncapped, 13.2 s capped).
 template <int stage>
-__global__ void __launch_bounds__(512, 1) batch_trace_kernel(const InstDesc* __restrict__ insts, int n_inst,
+__global__ void __maxnreg__(72) batch_trace_kernel(const InstDesc* __restrict__ insts, int n_inst,
                                                           int64_t total_items, unsigned long long* counter,
                                                           BatchPtrs P, int list_off, int ccap) {
   // shared memory: the current instance's grid table, then from word list_off

@@ -134,27 +134,32 @@ __device__ __forceinline__ void trace_body(const GridDesc& gd, const GeomArgs& g
   op.end(ray);
 }
 
+// At most 72 registers a thread: 7 blocks of 128 threads per SM. Left to
+// the compiler most per-segment operations take 75-90 and lose one to three
+// blocks (measured: the single-volume gather 3.9% faster capped, the batch
+// stages 9%), without spilling under the cap.
 template <int GK, class Op>
-__global__ void __launch_bounds__(512, 1) trace_kernel(GridDesc gd, GeomArgs ga, Op op, int tw, int ccap) {
+__global__ void __maxnreg__(72) trace_kernel(GridDesc gd, GeomArgs ga, Op op, int tw, int ccap) {
   trace_body<GK>(gd, ga, op, tw, ccap);
 }
 
-// The same for ops that declare `static constexpr bool cap_registers = true`:
-// at most 72 registers a thread, the count that keeps 7 blocks of 128
-// threads on an SM (the gather's compiler-chosen allocation otherwise grows
-// past it and costs a block).
+// Ops that declare `static constexpr bool wide_registers = true` keep the
+// compiler's allocation: the scatters, which fit in 72 registers anyway and
+// ran 2% slower under the cap's allocation, the 8-volume gather, which would
+// spill, and the attenuated projection's operations (8% slower capped; the
+// dynamic gather, by contrast, 15% faster).
 template <int GK, class Op>
-__global__ void __maxnreg__(72) trace_kernel_r72(GridDesc gd, GeomArgs ga, Op op, int tw, int ccap) {
+__global__ void __launch_bounds__(512, 1) trace_kernel_wide(GridDesc gd, GeomArgs ga, Op op, int tw, int ccap) {
   trace_body<GK>(gd, ga, op, tw, ccap);
 }
 
 template <class Op, class = void>
-struct op_caps_registers {
+struct op_wide_registers {
   static constexpr bool value = false;
 };
 template <class Op>
-struct op_caps_registers<Op, decltype(void(Op::cap_registers))> {
-  static constexpr bool value = Op::cap_registers;
+struct op_wide_registers<Op, decltype(void(Op::wide_registers))> {
+  static constexpr bool value = Op::wide_registers;
 };
 
 // Cone-crossing list entries per thread: 48 up to 128 threads per block
@@ -201,10 +206,10 @@ void launch_trace(const tsp_grid_s* grid, const tsp_geom_s* geom, const tsp_laun
     allow_smem(kernel, s.smem);
     kernel<<<s.grid, s.block, s.smem, st>>>(gd, ga, op, l.warp_tile_w, s.ccap);
   };
-  if constexpr (op_caps_registers<Op>::value) {
-    if (geom->kind == GEOM_CONE) go(trace_kernel_r72<GEOM_CONE, Op>);
-    else if (geom->kind == GEOM_PARALLEL) go(trace_kernel_r72<GEOM_PARALLEL, Op>);
-    else go(trace_kernel_r72<GEOM_RAYS, Op>);
+  if constexpr (op_wide_registers<Op>::value) {
+    if (geom->kind == GEOM_CONE) go(trace_kernel_wide<GEOM_CONE, Op>);
+    else if (geom->kind == GEOM_PARALLEL) go(trace_kernel_wide<GEOM_PARALLEL, Op>);
+    else go(trace_kernel_wide<GEOM_RAYS, Op>);
   } else {
     if (geom->kind == GEOM_CONE) go(trace_kernel<GEOM_CONE, Op>);
     else if (geom->kind == GEOM_PARALLEL) go(trace_kernel<GEOM_PARALLEL, Op>);
@@ -253,7 +258,7 @@ struct DelayedSum {
 // y[b] = sum rho[b][v] dl  (Eq. 5), optionally followed by an epilogue.
 template <int NB>
 struct GatherOp {
-  static constexpr bool cap_registers = NB == 1;  // (the batched forms would spill under the cap)
+  static constexpr bool wide_registers = NB == 8;
   const float* __restrict__ rho;
   float* __restrict__ y;
   int64_t V, n_rays;
@@ -289,6 +294,7 @@ struct GatherOp {
 // g[b][v] += w[b] dl with one atomic add per segment (adjoint of Eq. 5).
 template <int NB>
 struct ScatterOp {
+  static constexpr bool wide_registers = NB < 8;
   const float* __restrict__ y;
   float* __restrict__ g;
   int64_t V, n_rays;
@@ -323,6 +329,7 @@ struct ScatterOp {
 // shuffles than they saved in atomics.)
 template <int NB>
 struct AggScatterOp : ScatterOp<NB> {
+  static constexpr bool wide_registers = NB < 4;
   __device__ __forceinline__ void operator()(int v, float dl) {
     const unsigned m = __activemask();  // the lanes with a segment in this step
     const int lane = threadIdx.x & 31;

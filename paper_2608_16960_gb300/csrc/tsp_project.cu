@@ -45,6 +45,7 @@ struct DynGatherOp {
 // voxel in a step.
 template <bool AGG>
 struct DynScatterOp {
+  static constexpr bool wide_registers = true;
   const float* __restrict__ y;
   float* __restrict__ g;
   int64_t V, per_view;

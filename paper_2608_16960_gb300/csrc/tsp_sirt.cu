@@ -26,6 +26,7 @@ struct PathLenOp {
 
 // c[v] += dl for every segment of every ray (F^T 1).
 struct UnitScatterOp {
+  static constexpr bool wide_registers = true;
   float* __restrict__ c;
   __device__ __forceinline__ bool begin(int64_t) { return true; }
   __device__ __forceinline__ void operator()(int v, float dl) { atomicAdd(c + v, dl); }
