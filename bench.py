@@ -53,7 +53,7 @@ ATTEN_EXTRA_OPS = 6.0
 # are read once and the detector values stay in L2, so the figure does not
 # grow with the views (2.74 MB at 2 views, 2.77 MB at 8 for the cone
 # forward). None once the kernel changes after the capture.
-TRACE_DRAM_BYTES = {"forward": 0.5 * (2771712 + 2930176), "adjoint": 0.5 * (4858368 + 5026560)}
+TRACE_DRAM_BYTES = {"forward": 0.5 * (2770432 + 2927872), "adjoint": 0.5 * (4897536 + 5024256)}
 
 
 _LOG = ""
