@@ -66,3 +66,36 @@ extern "C" int host_walk_list(const double* r, int nr, const double* th, int nt,
   }
   return bad;
 }
+
+// The boundary table of a grid as the kernels stage it in shared memory:
+// copies up to cap words to out, and writes the table's length, M and the
+// word offsets of its parts (half-plane records, cone records, radius pairs,
+// low parts of sin^2 and cos^2, plane angles) as read through TGrid to
+// info[0..7]. Returns the length in words, -1 for a grid with no cells.
+extern "C" int host_table(const double* r, int nr, const double* th, int nt, const double* ph, int np, float* out,
+                          int cap, int* info) {
+  if (nr < 2 || nt < 2 || np < 2) return -1;
+  tsp_grid_s g;
+  std::vector<float> table;
+  tsp::build_grid_table(r, nr, th, nt, ph, np, &table, &g);
+  tsp::GridDesc gd;
+  gd.table = nullptr;
+  gd.Nr = g.Nr;
+  gd.Ne = g.Ne;
+  gd.Na = g.Na;
+  gd.M = g.M;
+  gd.words = g.words;
+  gd.pa0 = g.pa0;
+  const tsp::TGrid G = tsp::tgrid_from_smem(gd, table.data());
+  const float* base = table.data();
+  info[0] = g.words;
+  info[1] = g.M;
+  info[2] = int(reinterpret_cast<const float*>(G.PR) - base);
+  info[3] = int(reinterpret_cast<const float*>(G.CR) - base);
+  info[4] = int(reinterpret_cast<const float*>(G.RR) - base);
+  info[5] = int(G.S2L - base);
+  info[6] = int(G.K2L - base);
+  info[7] = int(G.PA - base);
+  for (int i = 0; i < g.words && i < cap; ++i) out[i] = table[size_t(i)];
+  return g.words;
+}

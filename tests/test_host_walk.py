@@ -55,6 +55,8 @@ def _lib():
                             P]
     L.host_walk_list.restype = ctypes.c_int
     L.host_walk_list.argtypes = L.host_walk.argtypes + [ctypes.c_int]
+    L.host_table.restype = ctypes.c_int
+    L.host_table.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_int, P]
     return L
 
 
@@ -352,3 +354,75 @@ def test_cone_list_refills_give_the_same_segments(lib):
         m = np.arange(v0.shape[1])[None, :] < c0[:, None]
         assert np.array_equal(np.where(m, v0, 0), np.where(m, v1, 0)), ccap
         assert np.array_equal(np.where(m, l0, 0).view(np.uint32), np.where(m, l1, 0).view(np.uint32)), ccap
+
+
+def _table(edges):
+    L = _lib()
+    r, t, p = [np.ascontiguousarray(a, np.float64) for a in (edges.r, edges.theta, edges.phi)]
+    out = np.zeros(200000, np.float32)
+    info = np.zeros(8, np.int32)
+    n = L.host_table(r.ctypes.data, len(r), t.ctypes.data, len(t), p.ctypes.data, len(p), out.ctypes.data, len(out),
+                     info.ctypes.data)
+    assert 0 < n <= len(out)
+    return out[:n], info
+
+
+@pytest.mark.parametrize("kind", ["paper", "wedge", "virtual", "offset"])
+def test_table_layout(kind):
+    """The boundary table the kernels read (the layout of tsp_table.h as seen
+    through TGrid): 16-byte half-plane records per direction of travel with
+    the next record's index and the sector beyond, cone records between
+    +-inf sentinels, (high, low) squared radii after (-inf, 0), every part
+    aligned for its vector loads, every sector narrower than pi/2."""
+    if kind == "paper":
+        e = synth.grid_edges(100, 60, 120)
+    elif kind == "wedge":
+        e = synth.GridEdges(np.linspace(1.0, 2.0, 11), np.linspace(0.3, 2.0, 18), np.linspace(0.2, 2.5, 21))
+    elif kind == "virtual":  # three wide sectors, split by virtual planes
+        e = synth.GridEdges(np.array([0.0, 1.0, 2.0]), np.array([0.0, 1.0, np.pi]), np.linspace(0.0, 2 * np.pi, 4))
+    else:
+        e = synth.GridEdges(np.array([1.0, 3.0]), np.array([0.2, 1.5, 2.9]), np.linspace(-2.0, -2.0 + 2 * np.pi, 9))
+    T, info = _table(e)
+    words, M, pr, cr, rr, s2l, k2l, pa = (int(v) for v in info)
+    Nr, Ne, Na = len(e.r) - 1, len(e.theta) - 1, len(e.phi) - 1
+    bits = T.view(np.int32)
+    # parts in order, contiguous, aligned for float4 / float2 loads
+    assert pr == 0 and cr == 8 * M + 4 and cr % 4 == 0
+    assert rr == cr + 4 * (Ne + 2) + 2 and rr % 2 == 0
+    assert s2l == rr + 2 * (Nr + 1) and k2l == s2l + Ne + 1 and pa == k2l + Ne + 1 and words == pa + M
+    # half-plane records: same plane in both directions, unit (cos, sin),
+    # next record one plane on, sector beyond = the neighbouring sector
+    ang = T[pa:pa + M].astype(np.float64)
+    assert ang[0] == 0.0 and np.all(np.diff(ang) > 0) and ang[-1] < 2 * np.pi
+    gaps = np.diff(np.concatenate([ang, [2 * np.pi]]))
+    assert np.all(gaps < 0.5 * np.pi + 1e-6), gaps.max()
+    wrap = abs((e.phi[-1] - e.phi[0]) - 2 * np.pi) <= 1e-9
+    for j in range(M):
+        up, dn = T[4 * j:4 * j + 4], T[4 * (M + j):4 * (M + j) + 4]
+        assert up[0] == dn[0] and up[1] == dn[1]
+        assert abs(float(up[0]) ** 2 + float(up[1]) ** 2 - 1.0) < 1e-6
+        assert abs(np.angle(complex(up[0], up[1]) / complex(T[4 * 0], T[4 * 0 + 1])) % (2 * np.pi)
+                   - ang[j] % (2 * np.pi)) < 1e-5 or abs(ang[j]) < 1e-6
+        assert bits[4 * j + 3] == (j + 1) % M
+        assert bits[4 * (M + j) + 3] == M + (j - 1) % M
+        assert bits[4 * (M + j) + 2] == bits[4 * ((j - 1) % M) + 2]
+        sec = bits[4 * j + 2]
+        assert -1 <= sec < Na
+    secs = bits[2:4 * M:4]
+    assert set(secs.tolist()) - {-1} == set(range(Na))  # every azimuth voxel has a sector
+    assert (-1 in secs.tolist()) == (not wrap)  # a wedge has its gap sector
+    # cone records between +inf and -inf, (cos, sin^2, cos^2 high parts, 0)
+    C = T[cr - 4:cr + 4 * (Ne + 2)].reshape(Ne + 3, 4)
+    assert C[0, 0] == np.inf and C[-1, 0] == -np.inf
+    th = np.clip(e.theta, 0.0, np.pi)
+    assert np.array_equal(C[1:-1, 0], np.cos(th).astype(np.float32))
+    assert np.all(np.diff(C[1:-1, 0]) < 0)
+    s2 = C[1:-1, 1].astype(np.float64) + T[s2l:s2l + Ne + 1].astype(np.float64)
+    k2 = C[1:-1, 2].astype(np.float64) + T[k2l:k2l + Ne + 1].astype(np.float64)
+    assert np.allclose(s2, np.sin(th) ** 2, rtol=1e-13, atol=1e-15)
+    assert np.allclose(k2, np.cos(th) ** 2, rtol=1e-13, atol=1e-15)
+    assert np.all(C[:, 3] == 0.0)
+    # squared radii as (high, low) pairs after (-inf, 0)
+    R = T[rr - 2:rr + 2 * (Nr + 1)].reshape(Nr + 2, 2)
+    assert R[0, 0] == -np.inf and R[0, 1] == 0.0
+    assert np.allclose(R[1:, 0].astype(np.float64) + R[1:, 1].astype(np.float64), e.r ** 2, rtol=1e-13, atol=0)
