@@ -109,7 +109,9 @@ void tsp_geom_destroy(tsp_geom geom);
 typedef struct {
   int block_threads;   /* threads per block: 64, 128, 256 or 512 */
   int warp_tile_w;     /* detector pixels per warp along a row: 4, 8, 16 or 32 */
-  int scatter;         /* adjoint: 0 = one atomic add per segment, 1 = warp-aggregated */
+  int scatter;         /* adjoint: 0 = one atomic add per segment, 1 = warp-aggregated: a lane
+                          and its neighbour (lane ^ 1) on the same voxel in the same step add
+                          their sum with one atomic */
 } tsp_launch;
 
 /*
