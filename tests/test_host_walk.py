@@ -149,6 +149,10 @@ def test_degenerate_rays(lib):
         on_surface.append((2 * R * u + rng.uniform(-R, R) * np.array([0.0, 0.0, 1.0]), -u + np.array([0, 0, 0.1]),
                            np.array([-np.sin(p), np.cos(p), 0.0])))
     plain.append((np.array([0.0, 0.0, 2.0 * R]), np.array([0.0, 0.0, -1.0])))          # along the axis
+    for _ in range(12):  # exactly through the origin (b = 0 in float-float: the start a power-of-two
+        v = rng.normal(size=3).astype(np.float32)  # multiple of the direction), from outside, and from
+        for sc in (-32.0, -0.25, 0.25):  # just before and just after the origin
+            plain.append((np.float32(sc) * v, v))
     st = np.array([a for a, _ in plain], np.float32)
     di = np.array([b for _, b in plain], np.float32)
     y = forward(lib, e, st, di, rho)
