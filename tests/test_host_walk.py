@@ -153,6 +153,9 @@ def test_degenerate_rays(lib):
         v = rng.normal(size=3).astype(np.float32)  # multiple of the direction), from outside, and from
         for sc in (-32.0, -0.25, 0.25):  # just before and just after the origin
             plain.append((np.float32(sc) * v, v))
+        # exactly meeting the z axis (m_z = 0): the azimuth jumps by pi there
+        a3 = (rng.uniform(-1, 1, size=3) * [2.0 * R, 2.0 * R, R]).astype(np.float32)
+        plain.append((a3, np.array([-a3[0], -a3[1], rng.uniform(-R, R)], np.float32)))
     st = np.array([a for a, _ in plain], np.float32)
     di = np.array([b for _, b in plain], np.float32)
     y = forward(lib, e, st, di, rho)
